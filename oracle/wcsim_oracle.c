@@ -1,0 +1,342 @@
+/*
+ * FP64 CPU oracle for the per-depo stages of the LArTPC signal simulation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the CUDA path is
+ * checked against.  It shares no code, header or table with the CUDA library, and only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ *
+ * What it computes (paper Sec. 2.1.1: "rasterization" and "scatter adding"; Fig. 2: drift
+ * and diffusion of the electron clouds; Sec. 3.3.1 and Table 1: fluctuation with a
+ * Box-Muller normal):
+ *
+ *   a1  drift:      t_a = t + t_d,  Q' = Q exp(-t_d / tau),
+ *                   sigma_T = sqrt(2 D_T t_d) [mm],  sigma_t = sqrt(2 D_L t_d) / v [us]
+ *   a2  rasterize:  per axis, the bins meeting [mu - n sigma, mu + n sigma] (whole bins),
+ *                   weight w_k = Phi((e_{k+1}-mu)/sigma) - Phi((e_k-mu)/sigma); patch =
+ *                   Q' w^p (x) w^t
+ *   a2f fluctuate:  x_b = max(0, mu_b + sqrt(mu_b (1 - mu_b/Q')) z_b), z_b standard normal
+ *                   from Philox4x32-10 (Salmon et al., SC'11) and Box-Muller
+ *   a3  scatter:    S[r][k] += x_b, in depo order, in double precision
+ *   a7  adjoint:    per-depo gradients of L given dL/dS, with the window held fixed
+ *
+ * The paper states none of the formulas above; the readings used are:
+ *   - which bins a depo covers is an integer decision.  It is taken in the precision the
+ *     CUDA kernel uses (position in FP64 bin units, half-width n*sigma/bin in FP32), so that
+ *     both sides pick the same bins; everything else here is FP64;
+ *   - sigma == 0 (in that FP32 decision) puts all of an axis' weight into the single bin;
+ *   - no renormalisation after truncation;
+ *   - Philox counter = (tick k, row r, depo id, plane id), key = (seed lo, seed hi);
+ *     u = (x + 0.5) 2^-32;  z = sqrt(-2 ln u1) cos(2 pi u2).
+ *
+ * Build: cc -O2 -ffp-contract=off -fPIC -shared wcsim_oracle.c -lm
+ * (no FMA contraction: the bin decision must be evaluated operation by operation).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#define OG_PI 3.14159265358979323846
+#define OG_SQRT2 1.41421356237309504880
+
+typedef struct {
+    int32_t n_wires, n_imp, n_ticks, pad_;
+    double pitch_mm, p0_mm, tick_us, t0_us;
+} og_geom;
+
+typedef struct {
+    double v_mm_per_us, DL_cm2_s, DT_cm2_s, lifetime_us, nsigma;
+    int32_t fluctuate;
+    uint32_t plane_id;
+    uint64_t seed;
+} og_params;
+
+/* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random numbers: as
+ * easy as 1, 2, 3").  Round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2,
+ * c' = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key is bumped by the Weyl
+ * constants after every round. */
+void og_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Box-Muller (Box & Muller 1958) on the first two Philox words, in FP64. */
+double og_normal(uint32_t x0, uint32_t x1)
+{
+    const double two_m32 = 1.0 / 4294967296.0;
+    double u1 = ((double)x0 + 0.5) * two_m32;
+    double u2 = ((double)x1 + 0.5) * two_m32;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * OG_PI * u2);
+}
+
+/* Per-call constants of the bin decision, formed the same way for every depo. */
+typedef struct {
+    double inv_dp, inv_dt;          /* 1/(pitch/n_imp), 1/tick, FP64 */
+    float two_dt_f, two_dl_f, inv_v_f, nsig_f, inv_dp_f, inv_dt_f;
+} og_consts;
+
+static og_consts make_consts(const og_geom* g, const og_params* pr)
+{
+    og_consts c;
+    double dp = g->pitch_mm / (double)g->n_imp;
+    c.inv_dp = 1.0 / dp;
+    c.inv_dt = 1.0 / g->tick_us;
+    c.two_dt_f = (float)(2.0 * (pr->DT_cm2_s * 1e-4));
+    c.two_dl_f = (float)(2.0 * (pr->DL_cm2_s * 1e-4));
+    c.inv_v_f = (float)(1.0 / pr->v_mm_per_us);
+    c.nsig_f = (float)pr->nsigma;
+    c.inv_dp_f = (float)c.inv_dp;
+    c.inv_dt_f = (float)c.inv_dt;
+    return c;
+}
+
+/* One axis of the bin decision.  x: depo position in bin units (FP64), hw: half-width
+ * n*sigma/bin (FP32).  Returns 0 if no bin of [0, n) is covered. */
+static int axis_window(double x, float hw, int64_t n, int64_t* lo, int64_t* hi)
+{
+    if (!(x > -1e12 && x < 1e12)) return 0;       /* also rejects NaN */
+    double i0 = floor(x);
+    float frac = (float)(x - i0);
+    float a = frac - hw;
+    float b = frac + hw;
+    double l = i0 + floor((double)a);
+    double h = i0 + floor((double)b);
+    if (l < 0.0) l = 0.0;
+    if (h > (double)(n - 1)) h = (double)(n - 1);
+    if (l > h) return 0;
+    *lo = (int64_t)l;
+    *hi = (int64_t)h;
+    return 1;
+}
+
+/* Everything the oracle derives for one depo (drift, window, FP64 sigmas). */
+typedef struct {
+    int ok;                        /* 0: contributes nothing */
+    int64_t r_lo, r_hi, k_lo, k_hi;
+    double mu_p, mu_t;             /* pitch position [mm] and arrival time [us] */
+    double sig_p, sig_t;           /* FP64 sigma_T [mm], sigma_t [us] */
+    int delta_p, delta_t;          /* sigma == 0 in the FP32 decision */
+    double qatt;                   /* attenuated charge Q' */
+    double att;                    /* exp(-t_d / tau) */
+} og_depo;
+
+static og_depo drift_and_window(const og_geom* g, const og_params* pr, const og_consts* c,
+                                double p, double t, double td, float q)
+{
+    og_depo d;
+    d.ok = 0;
+    if (!(td >= 0.0) || !isfinite(p) || !isfinite(t) || !isfinite(td) || !(q >= 0.0f)
+        || !isfinite(q))
+        return d;
+    /* a1: drift */
+    d.mu_p = p;
+    d.mu_t = t + td;
+    d.att = exp(-td / pr->lifetime_us);
+    d.qatt = (double)q * d.att;
+    if (!(d.qatt > 0.0)) return d;
+    d.sig_p = sqrt(2.0 * (pr->DT_cm2_s * 1e-4) * td);
+    d.sig_t = sqrt(2.0 * (pr->DL_cm2_s * 1e-4) * td) / pr->v_mm_per_us;
+    /* the bin decision, in the kernel's precision */
+    float td_f = (float)td;
+    float sp_f = sqrtf(c->two_dt_f * td_f);
+    float st_f = sqrtf(c->two_dl_f * td_f) * c->inv_v_f;
+    float hw_p = (c->nsig_f * sp_f) * c->inv_dp_f;
+    float hw_t = (c->nsig_f * st_f) * c->inv_dt_f;
+    d.delta_p = (sp_f == 0.0f);
+    d.delta_t = (st_f == 0.0f);
+    double xp = (p - g->p0_mm) * c->inv_dp;
+    double xt = (d.mu_t - g->t0_us) * c->inv_dt;
+    int64_t nrows = (int64_t)g->n_wires * g->n_imp;
+    if (!axis_window(xp, hw_p, nrows, &d.r_lo, &d.r_hi)) return d;
+    if (!axis_window(xt, hw_t, g->n_ticks, &d.k_lo, &d.k_hi)) return d;
+    d.ok = 1;
+    return d;
+}
+
+/* Phi(b') - Phi(a') for a' = ua*sqrt(2), b' = ub*sqrt(2), with the erfc forms in the tails
+ * so that far-tail bins keep their relative precision. */
+static double gauss_mass(double ua, double ub)
+{
+    if (ua >= 0.0) return 0.5 * (erfc(ua) - erfc(ub));
+    if (ub <= 0.0) return 0.5 * (erfc(-ub) - erfc(-ua));
+    return 0.5 * (erf(ub) - erf(ua));
+}
+
+/* 1D weights of bins lo..hi: w[i] for bin lo+i, origin/bin in physical units. */
+static void axis_weights(double mu, double sig, int delta, double origin, double bin,
+                         int64_t lo, int64_t hi, double* w)
+{
+    int64_t n = hi - lo + 1;
+    if (delta) {
+        /* sigma == 0: the whole charge sits in the one bin of the window */
+        for (int64_t i = 0; i < n; ++i) w[i] = (i == 0) ? 1.0 : 0.0;
+        return;
+    }
+    double s = 1.0 / (OG_SQRT2 * sig);
+    for (int64_t i = 0; i < n; ++i) {
+        double ea = (origin + (double)(lo + i) * bin) - mu;
+        double eb = (origin + (double)(lo + i + 1) * bin) - mu;
+        w[i] = gauss_mass(ea * s, eb * s);
+    }
+}
+
+/* dw/dmu and dw/dsigma of the same bins (window held fixed). */
+static void axis_weight_derivs(double mu, double sig, int delta, double origin, double bin,
+                               int64_t lo, int64_t hi, double* dmu, double* dsig)
+{
+    int64_t n = hi - lo + 1;
+    if (delta) {
+        for (int64_t i = 0; i < n; ++i) { dmu[i] = 0.0; dsig[i] = 0.0; }
+        return;
+    }
+    const double inv_sqrt_2pi = 0.39894228040143267794;
+    for (int64_t i = 0; i < n; ++i) {
+        double a = ((origin + (double)(lo + i) * bin) - mu) / sig;
+        double b = ((origin + (double)(lo + i + 1) * bin) - mu) / sig;
+        double pa = inv_sqrt_2pi * exp(-0.5 * a * a);
+        double pb = inv_sqrt_2pi * exp(-0.5 * b * b);
+        dmu[i] = -(pb - pa) / sig;
+        dsig[i] = -(b * pb - a * pa) / sig;
+    }
+}
+
+#define OG_MAXB 4096
+
+/* Bins each depo covers: out[4*i + (0..3)] = r_lo, r_hi, k_lo, k_hi, or -1s if none. */
+void og_windows(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                const double* t, const double* td, const float* q, int64_t* out)
+{
+    og_consts c = make_consts(g, pr);
+    for (int64_t i = 0; i < n; ++i) {
+        og_depo d = drift_and_window(g, pr, &c, p[i], t[i], td[i], q[i]);
+        if (d.ok) {
+            out[4 * i + 0] = d.r_lo; out[4 * i + 1] = d.r_hi;
+            out[4 * i + 2] = d.k_lo; out[4 * i + 3] = d.k_hi;
+        } else {
+            out[4 * i + 0] = out[4 * i + 1] = out[4 * i + 2] = out[4 * i + 3] = -1;
+        }
+    }
+}
+
+/* 1D weights of one depo along both axes (for the closed-form tests).  wp/wt receive
+ * r_hi-r_lo+1 and k_hi-k_lo+1 values; returns 0 if the depo covers nothing. */
+int og_depo_weights(const og_geom* g, const og_params* pr, double p, double t, double td,
+                    float q, double* qatt, double* wp, double* wt)
+{
+    og_consts c = make_consts(g, pr);
+    og_depo d = drift_and_window(g, pr, &c, p, t, td, q);
+    if (!d.ok) return 0;
+    double dp = g->pitch_mm / (double)g->n_imp;
+    axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
+    axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
+    *qatt = d.qatt;
+    return 1;
+}
+
+/* a1-a3 (+a2f): accumulate every depo's patch into grid[n_rows][n_ticks] (FP64). */
+int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                 const double* t, const double* td, const float* q, const uint32_t* id,
+                 double* grid)
+{
+    static double wp[OG_MAXB], wt[OG_MAXB];
+    og_consts c = make_consts(g, pr);
+    double dp = g->pitch_mm / (double)g->n_imp;
+    const int64_t nt = g->n_ticks;
+    const uint32_t key[2] = {(uint32_t)pr->seed, (uint32_t)(pr->seed >> 32)};
+    for (int64_t i = 0; i < n; ++i) {
+        og_depo d = drift_and_window(g, pr, &c, p[i], t[i], td[i], q[i]);
+        if (!d.ok) continue;
+        if (d.r_hi - d.r_lo + 1 > OG_MAXB || d.k_hi - d.k_lo + 1 > OG_MAXB) return -1;
+        axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
+        axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
+        for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
+            double* row = grid + r * nt;
+            for (int64_t k = d.k_lo; k <= d.k_hi; ++k) {
+                double mean = d.qatt * wp[r - d.r_lo] * wt[k - d.k_lo];
+                double val = mean;
+                if (pr->fluctuate) {
+                    /* normal approximation to Binomial(Q', mean/Q') */
+                    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)r, id[i], pr->plane_id};
+                    uint32_t x[4];
+                    og_philox4x32_10(ctr, key, x);
+                    double z = og_normal(x[0], x[1]);
+                    double var = mean * (1.0 - mean / d.qatt);
+                    if (var < 0.0) var = 0.0;
+                    val = mean + sqrt(var) * z;
+                    if (val < 0.0) val = 0.0;
+                }
+                row[k] += val;
+            }
+        }
+    }
+    return 0;
+}
+
+/* a7, per-depo part: given dS = dL/dS (FP64 grid), the gradients of L with respect to
+ * each depo's charge Q, pitch position p, time t, sigma_L [mm], sigma_T [mm] (mean path,
+ * window fixed), and the sums over depos for D_L, D_T [cm^2/s] and tau [us].
+ * glob[0..2] = dL/dD_L, dL/dD_T, dL/dtau. */
+int og_depo_grads(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                  const double* t, const double* td, const float* q, const double* dS,
+                  double* dq, double* dpos, double* dt, double* dsl, double* dst,
+                  double* glob)
+{
+    static double wp[OG_MAXB], wt[OG_MAXB], dwp_mu[OG_MAXB], dwp_s[OG_MAXB],
+        dwt_mu[OG_MAXB], dwt_s[OG_MAXB];
+    og_consts c = make_consts(g, pr);
+    double dpitch = g->pitch_mm / (double)g->n_imp;
+    const int64_t nt = g->n_ticks;
+    glob[0] = glob[1] = glob[2] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        dq[i] = dpos[i] = dt[i] = dsl[i] = dst[i] = 0.0;
+        og_depo d = drift_and_window(g, pr, &c, p[i], t[i], td[i], q[i]);
+        if (!d.ok) continue;
+        if (d.r_hi - d.r_lo + 1 > OG_MAXB || d.k_hi - d.k_lo + 1 > OG_MAXB) return -1;
+        axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dpitch, d.r_lo, d.r_hi, wp);
+        axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
+        axis_weight_derivs(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dpitch, d.r_lo, d.r_hi,
+                           dwp_mu, dwp_s);
+        axis_weight_derivs(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo,
+                           d.k_hi, dwt_mu, dwt_s);
+        double a_q = 0.0, a_pm = 0.0, a_ps = 0.0, a_tm = 0.0, a_ts = 0.0;
+        for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
+            const double* row = dS + r * nt;
+            int64_t ir = r - d.r_lo;
+            for (int64_t k = d.k_lo; k <= d.k_hi; ++k) {
+                int64_t ik = k - d.k_lo;
+                double s = row[k];
+                a_q += s * wp[ir] * wt[ik];
+                a_pm += s * dwp_mu[ir] * wt[ik];
+                a_ps += s * dwp_s[ir] * wt[ik];
+                a_tm += s * wp[ir] * dwt_mu[ik];
+                a_ts += s * wp[ir] * dwt_s[ik];
+            }
+        }
+        double dqatt = a_q;                         /* dL/dQ' */
+        dq[i] = dqatt * d.att;                      /* Q' = Q exp(-t_d/tau) */
+        dpos[i] = d.qatt * a_pm;                    /* mu_p = p */
+        dt[i] = d.qatt * a_tm;                      /* t_a = t + t_d */
+        dst[i] = d.qatt * a_ps;                     /* sigma_T [mm] */
+        double dsig_t = d.qatt * a_ts;              /* sigma_t [us] */
+        dsl[i] = dsig_t / pr->v_mm_per_us;          /* sigma_t = sigma_L / v */
+        /* sigma = sqrt(2 D t_d): dsigma/dD = sigma / (2 D) */
+        if (pr->DL_cm2_s > 0.0) glob[0] += dsl[i] * (d.sig_t * pr->v_mm_per_us) / (2.0 * pr->DL_cm2_s);
+        if (pr->DT_cm2_s > 0.0) glob[1] += dst[i] * d.sig_p / (2.0 * pr->DT_cm2_s);
+        /* dQ'/dtau = Q' t_d / tau^2 */
+        glob[2] += dqatt * d.qatt * td[i] / (pr->lifetime_us * pr->lifetime_us);
+    }
+    return 0;
+}

@@ -1,0 +1,424 @@
+"""Pins of the FP64 oracle to things other than itself (CPU only).
+
+Each test ties one stage of the oracle to a closed form, an invariant, brute force on tiny
+inputs or an independent library routine, so that a dropped term, a wrong sign, index or
+transposed operand in the oracle fails here.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2104_08265_gb300 import synth as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = json.load(open(os.path.join(HERE, "golden", "hand_values.json")))
+
+
+def one(p, t, td, q=1000.0, idx=0):
+    return S.Depos(p=np.array([p], float), t=np.array([t], float), td=np.array([td], float),
+                   q=np.array([q], np.float32), id=np.array([idx], np.uint32))
+
+
+def fine_geom(n_wires=40, n_imp=10, pitch=1.0, n_ticks=400, tick=0.05):
+    return S.Geometry(n_wires=n_wires, n_imp=n_imp, n_ticks=n_ticks, pitch_mm=pitch,
+                      tick_us=tick)
+
+
+# ------------------------------------------------------------------ a1: drift
+def test_drift_sigma_and_attenuation_hand_values():
+    """Binned second moments reproduce the hand-computed sigmas (Sheppard: +h^2/12)."""
+    g = fine_geom()
+    prm = S.DriftParams(DT_cm2_s=GOLD["sigma_T_mm"]["D_cm2_s"],
+                        DL_cm2_s=GOLD["sigma_t_us"]["D_cm2_s"],
+                        v_mm_per_us=GOLD["sigma_t_us"]["v_mm_per_us"],
+                        lifetime_us=GOLD["attenuation"]["lifetime_us"], nsigma=9.0)
+    td = GOLD["sigma_T_mm"]["t_drift_us"]
+    p, t = 20.013, -490.0
+    qa, wp, wt = O.depo_weights(g, prm, p, t, td, 1000.0)
+    assert qa == pytest.approx(1000.0 * GOLD["attenuation"]["value"], rel=1e-14)
+    win = O.windows(g, prm, one(p, t, td))[0]
+    dp = g.pitch_mm / g.n_imp
+    cp = g.p0_mm + (np.arange(win[0], win[1] + 1) + 0.5) * dp
+    ct = g.t0_us + (np.arange(win[2], win[3] + 1) + 0.5) * g.tick_us
+    for w, c, mu, h, sig in ((wp, cp, p, dp, GOLD["sigma_T_mm"]["value"]),
+                             (wt, ct, t + td, g.tick_us, GOLD["sigma_t_us"]["value"])):
+        assert w.sum() == pytest.approx(1.0, abs=1e-13)
+        m1 = (w * c).sum()
+        var = (w * (c - m1) ** 2).sum()
+        assert m1 == pytest.approx(mu, abs=1e-9)
+        assert var == pytest.approx(sig * sig + h * h / 12.0, rel=1e-9)
+
+
+def test_point_depo_bins_hand_values():
+    g = S.Geometry(n_wires=128, n_imp=10, n_ticks=1024, pitch_mm=3.0)
+    prm = S.DriftParams()
+    for c in GOLD["point_bins"]["cases"]:
+        w = O.windows(g, prm, one(c["p_mm"], c["t_us"], 0.0))[0]
+        assert (w[0], w[1], w[2], w[3]) == (c["row"], c["row"], c["tick"], c["tick"])
+
+
+# ------------------------------------------------------------------ a2: weights
+def test_weights_telescope_to_attenuated_charge():
+    """Untruncated patch (n_sigma = 8) sums to Q' (erf telescoping)."""
+    g = S.Geometry(n_wires=128, n_imp=10, n_ticks=1024, pitch_mm=3.0)
+    prm = S.DriftParams(nsigma=8.0)
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        p = rng.uniform(100, 280); td = rng.uniform(1, 500); t = rng.uniform(0, 10)
+        qa, wp, wt = O.depo_weights(g, prm, p, t, td, 5000.0)
+        tot = qa * wp.sum() * wt.sum()
+        assert tot == pytest.approx(5000.0 * math.exp(-td / prm.lifetime_us), rel=1e-14)
+
+
+def test_weights_match_midpoint_quadrature():
+    """Each bin weight equals the Gaussian integral over the bin (no erf involved)."""
+    g = S.Geometry(n_wires=128, n_imp=10, n_ticks=1024, pitch_mm=3.0)
+    prm = S.DriftParams(nsigma=4.0)
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        p = rng.uniform(100, 280); td = rng.uniform(20, 500)
+        qa, wp, wt = O.depo_weights(g, prm, p, 0.0, td, 1000.0)
+        sig = math.sqrt(2 * prm.DT_cm2_s * 1e-4 * td)
+        w = O.windows(g, prm, one(p, 0.0, td))[0]
+        dp = g.pitch_mm / g.n_imp
+        for i, r in enumerate(range(w[0], w[1] + 1)):
+            x = g.p0_mm + (r + (np.arange(4000) + 0.5) / 4000) * dp
+            quad = (np.exp(-0.5 * ((x - p) / sig) ** 2) / (sig * math.sqrt(2 * math.pi))).sum() * dp / 4000
+            assert wp[i] == pytest.approx(quad, rel=2e-7, abs=1e-15)
+
+
+def test_far_tail_weights_keep_relative_precision():
+    """Bins far in one tail: erfc form, compare with log-space quadrature."""
+    g = fine_geom(n_wires=400, pitch=1.0, n_imp=10)
+    prm = S.DriftParams(nsigma=9.0, DT_cm2_s=8.8)
+    p, td = 200.0, 100.0
+    qa, wp, wt = O.depo_weights(g, prm, p, -90.0, td, 1.0)
+    sig = math.sqrt(2 * 8.8e-4 * td)
+    w = O.windows(g, prm, one(p, -90.0, td))[0]
+    dp = 0.1
+    i = len(wp) - 2             # one of the outermost bins, ~8.5 sigma out
+    r = w[0] + i
+    x = g.p0_mm + (r + (np.arange(20000) + 0.5) / 20000) * dp
+    quad = (np.exp(-0.5 * ((x - p) / sig) ** 2) / (sig * math.sqrt(2 * math.pi))).sum() * dp / 20000
+    assert wp[i] < 1e-12
+    assert wp[i] == pytest.approx(quad, rel=1e-6)
+
+
+def test_windows_match_bruteforce_enumeration():
+    """Window = exactly the bins whose [e_k, e_k+1) meets [mu - n s, mu + n s]."""
+    g = S.Geometry(n_wires=32, n_imp=10, n_ticks=256, pitch_mm=3.0)
+    prm = S.DriftParams()
+    rng = np.random.default_rng(7)
+    n = 400
+    d = S.Depos(p=rng.uniform(-5, 101, n), t=rng.uniform(-10, 10, n),
+                td=rng.uniform(0, 120, n), q=np.full(n, 100.0, np.float32),
+                id=np.arange(n, dtype=np.uint32))
+    d.td[:20] = 0.0                              # point depos
+    got = O.windows(g, prm, d)
+    dp = Fraction(g.pitch_mm) / g.n_imp
+    checked = 0
+    for i in range(n):
+        for axis in (0, 1):
+            if axis == 0:
+                mu = Fraction(d.p[i]); sig = math.sqrt(2 * prm.DT_cm2_s * 1e-4 * d.td[i])
+                org, h, N = Fraction(g.p0_mm), dp, g.n_rows
+            else:
+                mu = Fraction(d.t[i]) + Fraction(d.td[i])
+                sig = math.sqrt(2 * prm.DL_cm2_s * 1e-4 * d.td[i]) / prm.v_mm_per_us
+                org, h, N = Fraction(g.t0_us), Fraction(g.tick_us), g.n_ticks
+            half = Fraction(prm.nsigma) * Fraction(sig)
+            a, b = mu - half, mu + half
+            ks = [k for k in range(N) if org + k * h <= b and org + (k + 1) * h > a]
+            lo, hi = got[i][2 * axis], got[i][2 * axis + 1]
+            if not ks:
+                # off-grid on this axis: the whole depo must be reported empty
+                assert lo == -1
+                continue
+            if lo == -1:
+                # empty because of the other axis
+                continue
+            # ties within rounding of an edge may go either way
+            tie = min(abs(float((a - org) / h) - round(float((a - org) / h))),
+                      abs(float((b - org) / h) - round(float((b - org) / h))))
+            if tie < 1e-5:
+                continue
+            assert (lo, hi) == (ks[0], ks[-1]), (i, axis)
+            checked += 1
+    assert checked > 600
+
+
+# ------------------------------------------------------------------ a3: scatter
+def test_scatter_places_outer_product_at_window():
+    g = S.Geometry(n_wires=16, n_imp=10, n_ticks=128, pitch_mm=3.0)
+    prm = S.DriftParams()
+    d = one(24.1, 10.0, 40.0, q=2000.0)
+    grid = O.rasterize(g, prm, d)
+    qa, wp, wt = O.depo_weights(g, prm, 24.1, 10.0, 40.0, 2000.0)
+    w = O.windows(g, prm, d)[0]
+    ref = np.zeros_like(grid)
+    ref[w[0]:w[1] + 1, w[2]:w[3] + 1] = np.outer(qa * wp, wt)
+    assert np.allclose(grid, ref, rtol=1e-15, atol=0)
+    assert np.count_nonzero(grid) == np.count_nonzero(ref)
+
+
+def test_offgrid_depos_drop_bins_not_wrap():
+    g = S.Geometry(n_wires=8, n_imp=10, n_ticks=64, pitch_mm=3.0)
+    prm = S.DriftParams()
+    d = one(0.2, -199.9, 200.0, q=1000.0)         # near the (0, 0) corner: clipped
+    grid = O.rasterize(g, prm, d)
+    full = O.depo_weights(S.Geometry(n_wires=8, n_imp=10, n_ticks=64, pitch_mm=3.0,
+                                     p0_mm=-12.0, t0_us=-8.0), prm, 0.2, -199.9, 200.0, 1000.0)
+    assert 0 < grid.sum() < full[0] * full[1].sum() * full[2].sum()
+    assert grid[-1, :].sum() == 0 and grid[:, -1].sum() == 0
+    far = one(1e6, 0.0, 10.0)
+    assert O.rasterize(g, prm, far).sum() == 0.0
+
+
+# ------------------------------------------------------------------ a4-a6: convolution
+def direct_circular(Sj_list, rj_list, n_fw, n_ft, n_w, n_t):
+    """M[w][k] = Re sum_j sum_{w',k'} r_j[(w-w') mod n_fw][(k-k') mod n_ft] S_j[w'][k']."""
+    M = np.zeros((n_w, n_t), complex)
+    for Sj, rj in zip(Sj_list, rj_list):
+        for w in range(n_w):
+            for k in range(n_t):
+                acc = 0j
+                for w2 in range(Sj.shape[0]):
+                    for k2 in range(Sj.shape[1]):
+                        if Sj[w2, k2] != 0:
+                            acc += rj[(w - w2) % n_fw, (k - k2) % n_ft] * Sj[w2, k2]
+                M[w, k] += acc
+    return M.real
+
+
+@pytest.mark.parametrize("pad", [(0, 0), (3, 11)])
+@pytest.mark.parametrize("hermitian", [True, False])
+def test_convolve_matches_direct_circular_sum(pad, hermitian):
+    rng = np.random.default_rng(11)
+    g = S.Geometry(n_wires=6, n_imp=2, n_ticks=30, pitch_mm=3.0)
+    n_fw, n_ft = g.n_wires + pad[0], g.n_ticks + pad[1]
+    grid = rng.normal(size=(g.n_rows, g.n_ticks))
+    grid[rng.uniform(size=grid.shape) < 0.5] = 0.0
+    if hermitian:
+        r = rng.normal(size=(g.n_imp, n_fw, n_ft)).astype(complex)
+    else:
+        r = rng.normal(size=(g.n_imp, n_fw, n_ft)) + 1j * rng.normal(size=(g.n_imp, n_fw, n_ft))
+    R = np.stack([np.fft.fft2(r[j]) for j in range(g.n_imp)])
+    got = O.convolve(g, R, grid)
+    Sj = [grid[j::g.n_imp] for j in range(g.n_imp)]
+    ref = direct_circular(Sj, list(r), n_fw, n_ft, g.n_wires, g.n_ticks)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_point_depo_reproduces_shifted_response():
+    """sigma = 0 depo at row (w0, j0), tick k0: M = Q' R_j0 shifted by (w0, k0)."""
+    g = S.Geometry(n_wires=24, n_imp=10, n_ticks=256, pitch_mm=3.0)
+    prm = S.DriftParams()
+    rng = np.random.default_rng(12)
+    r = np.zeros((g.n_imp, g.n_wires, g.n_ticks))
+    r[:, :, :40] = rng.normal(size=(g.n_imp, g.n_wires, 40))
+    R = np.stack([np.fft.fft2(r[j]) for j in range(g.n_imp)])
+    w0, j0, k0 = 7, 3, 201
+    p = g.p0_mm + (w0 * g.n_imp + j0 + 0.37) * g.pitch_mm / g.n_imp
+    t = g.t0_us + (k0 + 0.81) * g.tick_us
+    d = one(p, t, 0.0, q=3000.0)
+    M = O.run(g, prm, R, d)
+    ref = 3000.0 * np.roll(np.roll(r[j0], w0, axis=0), k0, axis=1)
+    assert np.allclose(M, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_forward_linearity_and_superposition():
+    wl = S.make_workload("plane128-2k", n_depos=200)
+    g, prm, kind, d = wl.planes[0]
+    R = S.make_response(g, kind)
+    M = O.run(g, prm, R, d)
+    d2 = d.subset(slice(None)); d2.q = (d2.q * 2).astype(np.float32)
+    assert np.allclose(O.run(g, prm, R, d2), 2 * M, rtol=1e-12, atol=1e-9 * np.abs(M).max())
+    A, B = d.subset(slice(0, 77)), d.subset(slice(77, None))
+    MA, MB = O.run(g, prm, R, A), O.run(g, prm, R, B)
+    assert np.allclose(MA + MB, M, rtol=1e-12, atol=1e-11 * np.abs(M).max())
+
+
+# ------------------------------------------------------------------ a2f: fluctuation
+def test_philox_matches_triton_library_implementation():
+    """Oracle Philox4x32-10 vs Triton's philox (run by its CPU interpreter)."""
+    import subprocess, sys
+    code = r'''
+import os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+@triton.jit
+def k(c_ptr, out_ptr, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    c0 = tl.load(c_ptr + i * 4 + 0); c1 = tl.load(c_ptr + i * 4 + 1)
+    c2 = tl.load(c_ptr + i * 4 + 2); c3 = tl.load(c_ptr + i * 4 + 3)
+    a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+    tl.store(out_ptr + i * 4 + 0, a); tl.store(out_ptr + i * 4 + 1, b)
+    tl.store(out_ptr + i * 4 + 2, c); tl.store(out_ptr + i * 4 + 3, d)
+rng = np.random.default_rng(3)
+ctr = rng.integers(0, 2**32, size=(64, 4), dtype=np.uint64).astype(np.uint32)
+ctr[0] = 0; ctr[1] = 0xFFFFFFFF
+seed = int(sys.argv[1])
+out = torch.zeros(64 * 4, dtype=torch.int32)
+k[(1,)](torch.from_numpy(ctr.view(np.int32).reshape(-1).copy()), out, seed, 64)
+np.save(sys.argv[2], np.stack([ctr.reshape(-1), out.numpy().view(np.uint32)]))
+'''
+    pytest.importorskip("triton")
+    import tempfile
+    for seed in (0x5EED0001, 0x123456789ABCDEF0 >> 1):
+        with tempfile.TemporaryDirectory() as td:
+            f = os.path.join(td, "o.npy")
+            rc = subprocess.run([sys.executable, "-c", code, str(seed), f],
+                                capture_output=True, text=True, timeout=600)
+            if rc.returncode != 0:
+                pytest.skip("triton interpreter unavailable: " + rc.stderr[-300:])
+            ctr, out = np.load(f)
+        ctr = ctr.reshape(64, 4); out = out.reshape(64, 4)
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for i in range(64):
+            assert O.philox4x32_10(ctr[i], key) == [int(x) for x in out[i]], i
+
+
+def test_box_muller_normal_distribution():
+    """z from Philox words is standard normal (KS test) and uses both words."""
+    from scipy import stats
+    zs = np.array([O.normal_from_words(*O.philox4x32_10((i, 7, 9, 1), (1, 2))[:2])
+                   for i in range(20000)])
+    assert stats.kstest(zs, "norm").pvalue > 1e-3
+    assert abs(zs.mean()) < 4 / math.sqrt(len(zs))
+    assert abs(zs.var() - 1) < 4 * math.sqrt(2 / len(zs))
+    # u2 -> cos(2 pi u2): quarter-turn values
+    assert O.normal_from_words(2**31, 0) == pytest.approx(math.sqrt(-2 * math.log((2**31 + .5) / 2**32)), rel=1e-12)
+    assert O.normal_from_words(2**31, 2**31) == pytest.approx(-math.sqrt(-2 * math.log((2**31 + .5) / 2**32)), rel=1e-9)
+
+
+def test_fluctuation_mean_and_variance():
+    """Over 2000 seeds each bin has mean mu_b and variance mu_b (1 - mu_b / Q')."""
+    g = S.Geometry(n_wires=4, n_imp=10, n_ticks=48, pitch_mm=3.0)
+    p, t, td, q = 6.05, -50.0, 60.0, 200000.0
+    base = S.DriftParams(fluctuate=0)
+    mean = O.rasterize(g, base, one(p, t, td, q))
+    qa = O.depo_weights(g, base, p, t, td, q)[0]
+    n = 2000
+    acc = np.zeros_like(mean); acc2 = np.zeros_like(mean)
+    for s in range(n):
+        x = O.rasterize(g, S.DriftParams(fluctuate=1, seed=s), one(p, t, td, q))
+        acc += x; acc2 += x * x
+    m = acc / n; v = acc2 / n - m * m
+    big = mean > 200.0                   # clamp at zero inactive
+    assert big.sum() >= 10
+    var = mean * (1 - mean / qa)
+    z = (m[big] - mean[big]) / np.sqrt(var[big] / n)
+    assert np.abs(z).max() < 4.5
+    assert np.abs(v[big] / var[big] - 1).max() < 4.5 * math.sqrt(2 / n)
+    # the total is not conserved bin by bin, but keeps its mean
+    tot = acc.sum() / n
+    assert tot == pytest.approx(mean.sum(), rel=5 * math.sqrt(mean.sum()) / mean.sum() / math.sqrt(n) + 1e-9)
+
+
+def test_fluctuation_keyed_by_depo_id_and_plane():
+    g = S.Geometry(n_wires=4, n_imp=10, n_ticks=48, pitch_mm=3.0)
+    a = O.rasterize(g, S.DriftParams(fluctuate=1, seed=9), one(6.05, -50.0, 60.0, 1e4, idx=1))
+    b = O.rasterize(g, S.DriftParams(fluctuate=1, seed=9), one(6.05, -50.0, 60.0, 1e4, idx=2))
+    c = O.rasterize(g, S.DriftParams(fluctuate=1, seed=9, plane_id=1),
+                    one(6.05, -50.0, 60.0, 1e4, idx=1))
+    a2 = O.rasterize(g, S.DriftParams(fluctuate=1, seed=9), one(6.05, -50.0, 60.0, 1e4, idx=1))
+    assert np.array_equal(a, a2)
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+# ------------------------------------------------------------------ a7: adjoint
+def test_convolve_adjoint_dot_product_identity():
+    """<G, conv(S)> = <dS, S> for the adjoint dS (any real S, G)."""
+    rng = np.random.default_rng(21)
+    g = S.Geometry(n_wires=9, n_imp=3, n_ticks=40, pitch_mm=3.0)
+    n_fw, n_ft = 12, 45
+    R = rng.normal(size=(3, n_fw, n_ft)) + 1j * rng.normal(size=(3, n_fw, n_ft))
+    grid = rng.normal(size=(g.n_rows, g.n_ticks))
+    G = rng.normal(size=(g.n_wires, g.n_ticks))
+    dS, dR = O.convolve_adjoint(g, R, grid, G)
+    assert np.vdot(G, O.convolve(g, R, grid)).real == pytest.approx(np.vdot(dS, grid).real, rel=1e-11)
+
+
+def test_convolve_adjoint_response_grad_matches_torch_autograd():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(22)
+    g = S.Geometry(n_wires=7, n_imp=2, n_ticks=20, pitch_mm=3.0)
+    n_fw, n_ft = 8, 24
+    R = rng.normal(size=(2, n_fw, n_ft)) + 1j * rng.normal(size=(2, n_fw, n_ft))
+    grid = rng.normal(size=(g.n_rows, g.n_ticks))
+    G = rng.normal(size=(g.n_wires, g.n_ticks))
+    _, dR = O.convolve_adjoint(g, R, grid, G)
+    Rt = torch.tensor(R, dtype=torch.complex128, requires_grad=True)
+    Mh = 0
+    for j in range(2):
+        s = torch.zeros(n_fw, n_ft, dtype=torch.float64)
+        s[:7, :20] = torch.tensor(grid[j::2])
+        Mh = Mh + Rt[j] * torch.fft.fft2(s)
+    M = torch.fft.ifft2(Mh).real[:7, :20]
+    (M * torch.tensor(G)).sum().backward()
+    assert np.allclose(Rt.grad.numpy(), dR, rtol=1e-10, atol=1e-12)
+
+
+def _loss(g, prm, R, d, G):
+    return float((O.run(g, prm, R, d) * G).sum())
+
+
+def test_depo_grads_match_central_finite_differences():
+    """Single depos: FD in Q, p, t, D_L, D_T, tau against the oracle's chain rule."""
+    import dataclasses
+    g = S.Geometry(n_wires=12, n_imp=10, n_ticks=128, pitch_mm=3.0)
+    rng = np.random.default_rng(23)
+    R = S.make_response(g, "induction").astype(np.complex128)
+    G = rng.normal(size=(g.n_wires, g.n_ticks))
+    prm = S.DriftParams(DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0)
+    checked = 0
+    for trial in range(6):
+        p = rng.uniform(8, 28); t = rng.uniform(5, 20); td = rng.uniform(20, 40); q = 5000.0
+        d = one(p, t, td, q)
+        w0 = O.windows(g, prm, d)[0]
+        dS, _ = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G)
+        gr = O.depo_grads(g, prm, d, dS)
+        def fd(make, x, rel=1e-4):
+            h = rel * abs(x)
+            dp_, dm_ = make(x + h), make(x - h)
+            for (dd, pp) in (dp_, dm_):
+                if not np.array_equal(O.windows(g, pp, dd)[0], w0):
+                    return None
+            return (_loss(g, dp_[1], R, dp_[0], G) - _loss(g, dm_[1], R, dm_[0], G)) / (2 * h)
+        cases = [
+            ("q", lambda x: (one(p, t, td, x), prm), q, gr["q"][0]),
+            ("p", lambda x: (one(x, t, td, q), prm), p, gr["p"][0]),
+            ("t", lambda x: (one(p, x, td, q), prm), t, gr["t"][0]),
+            ("DL", lambda x: (d, dataclasses.replace(prm, DL_cm2_s=x)), prm.DL_cm2_s, gr["DL"]),
+            ("DT", lambda x: (d, dataclasses.replace(prm, DT_cm2_s=x)), prm.DT_cm2_s, gr["DT"]),
+            ("tau", lambda x: (d, dataclasses.replace(prm, lifetime_us=x)), prm.lifetime_us, gr["lifetime"]),
+        ]
+        for name, make, x, ana in cases:
+            num = fd(make, x, 1e-6 if name in ("p", "t") else 1e-4)
+            if num is None:
+                continue
+            scale = max(abs(num), abs(ana), 1e-30)
+            assert abs(num - ana) <= 2e-5 * scale + 1e-9, (name, num, ana)
+            checked += 1
+    assert checked >= 30
+
+
+def test_depo_sigma_grads_individually():
+    """Per-depo sigma grads via the D derivative of a single depo: dL/dD = dsigma sigma/(2D)."""
+    g = S.Geometry(n_wires=12, n_imp=10, n_ticks=128, pitch_mm=3.0)
+    rng = np.random.default_rng(24)
+    R = S.make_response(g, "collection").astype(np.complex128)
+    G = rng.normal(size=(g.n_wires, g.n_ticks))
+    prm = S.DriftParams(DL_cm2_s=6.0, DT_cm2_s=10.0)
+    d = one(17.3, 9.0, 33.0, 4000.0)
+    dS, _ = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G)
+    gr = O.depo_grads(g, prm, d, dS)
+    sT = math.sqrt(2 * 10.0e-4 * 33.0)
+    sL = math.sqrt(2 * 6.0e-4 * 33.0)
+    assert gr["DT"] == pytest.approx(gr["sigma_T"][0] * sT / (2 * 10.0), rel=1e-12)
+    assert gr["DL"] == pytest.approx(gr["sigma_L"][0] * sL / (2 * 6.0), rel=1e-12)
