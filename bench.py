@@ -1,0 +1,345 @@
+"""Throughput of the LArTPC signal-simulation hot path on GB300.
+
+One step = one whole forward pass (zero grid, drift + rasterize + fluctuate + scatter-add,
+time-axis FFT, wire-axis FFT x response x sum over impacts x inverse, time-axis inverse
+FFT) over the 960-wire x 6000-tick plane with 100,000 depos (fluctuation on).
+
+Prints one JSON line.  `value` is depos/s of the device-resident step; `e2e` is the same
+through the public API with the depos copied from pinned host memory and the waveforms
+copied back inside the timed region.  `--impl reference` times the FP64 CPU oracle (the
+only place besides the cpu_baseline leg where this script runs it).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2104_08265_gb300 import synth  # noqa: E402
+
+METRIC = "depos/s (full forward: drift, rasterize, fluctuate, scatter-add, 2D FFT convolution)"
+L2_FLUSH_BYTES = 256 << 20          # > 126 MB of L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="wcsim", choices=["wcsim", "reference"])
+    ap.add_argument("--workload", default="plane960-100k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name):
+    wl = synth.make_workload(name)
+    g, prm, kind, d = wl.planes[0]
+    return wl, g, prm, kind, d
+
+
+def config(name, g, d, prm, extra=None):
+    c = {"workload": name, "n_wires": g.n_wires, "n_imp": g.n_imp, "n_ticks": g.n_ticks,
+         "pitch_mm": g.pitch_mm, "tick_us": g.tick_us, "n_depos": len(d),
+         "fluctuate": prm.fluctuate, "l2": "flushed between timed steps (256 MB write); "
+         "response + grid working set 690 MB > L2"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------- byte / flop models
+def stage_bytes(g, n_depos, mean_bins):
+    """Algorithmic (compulsory) bytes per launch of each stage."""
+    rows = g.n_rows
+    nh = g.n_ticks // 2 + 1
+    return {
+        "zero": rows * g.n_ticks * 4,
+        "rasterize": n_depos * (32 + 4 * mean_bins),
+        "rows_r2c": rows * g.n_ticks * 4 + rows * nh * 8,
+        "wire_pass": rows * nh * 8 + g.n_imp * g.n_wires * nh * 8 + g.n_wires * nh * 8,
+        "rows_c2r": g.n_wires * nh * 8 + g.n_wires * g.n_ticks * 4,
+    }
+
+
+def bmin_bytes(g, n_depos):
+    """Compulsory bytes of the whole step: depos in, response half-spectrum, waveforms out."""
+    nh = g.n_ticks // 2 + 1
+    return n_depos * 32 + g.n_imp * g.n_wires * nh * 8 + g.n_wires * g.n_ticks * 4
+
+
+def fft_flops(g):
+    import math
+    nh = g.n_ticks // 2 + 1
+    lt = math.log2(g.n_ticks)
+    lw = math.log2(g.n_wires)
+    fwd_rows = g.n_rows * 2.5 * g.n_ticks * lt
+    wire = (g.n_imp + 1) * nh * 5 * g.n_wires * lw
+    mult = g.n_imp * g.n_wires * nh * 8
+    inv_rows = g.n_wires * 2.5 * g.n_ticks * lt
+    return fwd_rows + wire + mult + inv_rows
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_step(g, prm, R, d):
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.run(g, prm, R, d)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(g, prm, R, d):
+    """The FP64 oracle as it stands, single-threaded, on one full plane-frame."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    dt = oracle_step(g, prm, R, d)
+    return {"value": len(d) / dt, "unit": "depos/s", "cores": 1, "kind": "oracle",
+            "sample": "1 full forward of the same workload (%d depos, %dx%d plane), "
+                      "%.1f s wall" % (len(d), g.n_wires, g.n_ticks, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl, g, prm, kind, d = workload(args.workload)
+    R = synth.make_response(g, kind)
+    steps = max(1, min(args.steps, 3))
+    warm = min(args.warmup, 0)
+    times = [oracle_step(g, prm, R, d) for _ in range(steps)]
+    tot = sum(times)
+    v = steps * len(d) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "depos/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm, "ms_per_step": 1e3 * tot / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args.workload, g, d, prm),
+            "cpu_baseline": {"value": v, "unit": "depos/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d full forward(s) of the workload" % steps},
+            "e2e": {"value": v, "unit": "depos/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2104_08265_gb300 import _build, wcsim
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    _build.build()
+
+    wl, g, prm, kind, d = workload(args.workload)
+    # every rank simulates its own event: per-rank seed offset, same shapes
+    prm = synth.DriftParams(**{**prm.__dict__, "seed": prm.seed + rank})
+    R = synth.make_response(g, kind)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, prm, R, d)
+
+    plane = wcsim.Plane(g, prm, torch.from_numpy(R).cuda())
+    dd = wcsim.DeviceDepos.from_host(d)
+    wave = torch.empty((g.n_wires, g.n_ticks), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    mean_bins = float(np.mean([(w[1] - w[0] + 1) * (w[3] - w[2] + 1)
+                               for w in plane.windows(dd).cpu().numpy() if w[0] >= 0]))
+
+    for _ in range(args.warmup):
+        plane.run(dd, out=wave)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    plane.set_timing(True)
+    clocks = Clocks(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = {k: [] for k in wcsim.STAGES}
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        plane.run(dd, out=wave)
+        ends[i].record(stream)
+        torch.cuda.synchronize()
+        for k, v in plane.stage_times().items():
+            stage_ms[k].append(v)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    plane.set_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    assert plane.check_flags() == 0
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hp = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in
+              (("p", d.p), ("t", d.t), ("td", d.td), ("q", d.q),
+               ("id", d.id.view(np.int32)))}
+        dev = {k: torch.empty_like(v, device="cuda") for k, v in hp.items()}
+        out_h = torch.empty((g.n_wires, g.n_ticks), dtype=torch.float32).pin_memory()
+        dd2 = wcsim.DeviceDepos(dev["p"], dev["t"], dev["td"], dev["q"], dev["id"])
+        h2d = sum(v.numel() * v.element_size() for v in hp.values())
+        d2h = out_h.numel() * out_h.element_size()
+
+        def e2e_step():
+            for k in hp:
+                dev[k].copy_(hp[k], non_blocking=True)
+            plane.run(dd2, out=wave)
+            out_h.copy_(wave, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            es[i].record(stream)
+            e2e_step()
+            ee[i].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = sum(s.elapsed_time(e) for s, e in zip(es, ee))
+        if ws > 1:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": ws * args.steps * len(d) / (e2e_ms / 1e3), "unit": "depos/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e2e_ms / args.steps}
+
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    sb = stage_bytes(g, len(d), mean_bins)
+    avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
+    stages = {k: {"ms": avg[k], "GB/s": sb[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None,
+                  "alg_bytes": sb[k]} for k in avg}
+    dom = max(avg, key=avg.get)
+    ach = sb[dom] / (avg[dom] * 1e-3) / 1e9
+    per_step = tot_ms / args.steps
+    line = {
+        "metric": METRIC, "value": ws * args.steps * len(d) / (tot_ms / 1e3), "unit": "depos/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config(args.workload, g, d, prm,
+                                              {"parallelism": "replicas" if ws > 1 else "1 gpu"}),
+        "plane_frames_per_s": {"fwd": ws * 1e3 / per_step},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm,
+                     "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                     "peak_kind": peak_kind + " (burst copy)"},
+        "step_roofline": {"bmin_bytes": bmin_bytes(g, len(d)),
+                          "bmin_GBps": bmin_bytes(g, len(d)) / (per_step * 1e-3) / 1e9,
+                          "frac_of_hbm": bmin_bytes(g, len(d)) / (per_step * 1e-3) / 1e9 / hbm,
+                          "fft_gflop": fft_flops(g) / 1e9,
+                          "fft_tflops": fft_flops(g) / (per_step * 1e-3) / 1e12},
+        "stages": stages,
+        "mean_bins_per_depo": mean_bins,
+        "gpu_launches": 4 * args.steps,
+        "wall_s_timed_loop": wall,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

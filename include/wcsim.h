@@ -1,0 +1,153 @@
+/*
+ * wcsim.h -- C-ABI of the GB300 LArTPC signal-simulation library (libwcsim.so).
+ *
+ * The library computes the signal term of Eq. 1 (Sec. 2): electron clouds drift to a wire
+ * plane (Fig. 2), each is rasterized into a small Gaussian patch over impact position x
+ * time tick, the patches are scatter-added into the plane's grid S(t, x) (Sec. 2.1.1,
+ * "rasterization" and "scatter adding"), and the grid is convolved with the detector
+ * response in the frequency domain (Eq. 2) to give per-wire waveforms M(t, x).
+ *
+ * Conventions shared by every call
+ *  - Units: mm, microseconds, electrons; diffusion constants in cm^2/s.
+ *  - Arrays passed to compute calls are DEVICE pointers owned by the caller, except where a
+ *    call says otherwise.  The plane object owns its response copy and all scratch.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls only enqueue
+ *    work on it and never synchronize the host, so they return before the work is done.
+ *  - Every call returns a wcsim_status and never aborts; wcsim_last_error() gives a
+ *    thread-local message for the last failing call of the calling thread.
+ *  - Depo values are checked on the device: a depo with a NaN/Inf field, negative drift time
+ *    or negative charge contributes nothing and raises a flag that wcsim_plane_check()
+ *    reports.  A depo that lies (partly or wholly) outside the grid contributes only its
+ *    in-grid bins; that is not an error.
+ *  - Layouts: grid S is float32 [n_wires * n_imp][n_ticks], row r = w * n_imp + j covering
+ *    pitch coordinate [p0 + r d, p0 + (r+1) d), d = pitch / n_imp; tick k covers
+ *    [t0 + k tick, t0 + (k+1) tick).  Waveforms are float32 [n_wires][n_ticks].  Response
+ *    spectra are complex64 (interleaved re, im float32) [n_imp][n_fw][n_ft].
+ */
+#ifndef WCSIM_H
+#define WCSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WCSIM_OK = 0,
+    WCSIM_EINVAL = 1,        /* null pointer, NaN / out-of-range scalar parameter */
+    WCSIM_ESHAPE = 2,        /* unsupported or inconsistent sizes */
+    WCSIM_ENOMEM = 3,        /* a device allocation failed */
+    WCSIM_ECUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+    WCSIM_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    WCSIM_EDEVICE_CHECK = 6  /* the device flagged invalid depo values (see plane_check) */
+} wcsim_status;
+
+/* Opaque plane object: geometry, parameters, response (Hermitian half, pre-scaled) and
+ * scratch.  Library-owned; create/destroy only. */
+typedef struct wcsim_plane wcsim_plane;
+
+/* Plane geometry (Sec. 2.1.1: patches on an impact-position x tick grid). */
+typedef struct {
+    int32_t n_wires;   /* wires in the plane, >= 1 */
+    int32_t n_imp;     /* impact positions per wire pitch, >= 1 */
+    int32_t n_ticks;   /* time ticks in the frame, >= 1 */
+    int32_t reserved;  /* must be 0 */
+    double pitch_mm;   /* wire pitch, > 0 */
+    double p0_mm;      /* pitch coordinate of the lower edge of row 0 */
+    double tick_us;    /* tick length, > 0 */
+    double t0_us;      /* time of the lower edge of tick 0 */
+} wcsim_geometry;
+
+/* Drift, diffusion, lifetime, truncation and fluctuation parameters.  The paper gives no
+ * formulas (Fig. 2 only); the library uses t_a = t + t_d, Q' = Q exp(-t_d / lifetime),
+ * sigma_T = sqrt(2 D_T t_d) [mm], sigma_t = sqrt(2 D_L t_d) / v [us]. */
+typedef struct {
+    double v_mm_per_us;  /* drift speed, > 0 */
+    double DL_cm2_s;     /* longitudinal diffusion constant, >= 0 */
+    double DT_cm2_s;     /* transverse diffusion constant, >= 0 */
+    double lifetime_us;  /* electron lifetime, > 0 (may be +inf) */
+    double nsigma;       /* patch half-width in sigmas, > 0 */
+    int32_t fluctuate;   /* 1: per-bin charge fluctuation (Sec. 3.3.1, Table 1), 0: mean */
+    uint32_t plane_id;   /* 4th Philox counter word */
+    uint64_t seed;       /* Philox key (lo, hi words) */
+} wcsim_drift_params;
+
+/* Depos, structure of arrays, DEVICE pointers (8-byte aligned), n entries each. */
+typedef struct {
+    const double* p_mm;       /* pitch-direction position */
+    const double* t_us;       /* deposition time */
+    const double* tdrift_us;  /* drift time to this plane, >= 0 */
+    const float* q;           /* charge (electrons), >= 0 */
+    const uint32_t* id;       /* depo id; keys the fluctuation random stream */
+    int64_t n;                /* number of depos, >= 0 */
+} wcsim_depos;
+
+/* Create a plane.  Defined by Eq. 2: `resp_c64` is the pre-calculated response
+ * R(omega_t, omega_x) per impact position, DEVICE complex64 [n_imp][n_fw][n_ft]; it is
+ * read during this call (stream-ordered) and not retained.  n_fw >= n_wires and
+ * n_ft >= n_ticks set the FFT size (the frame is zero-padded; equal sizes give circular
+ * convolution); 0 means "same as the frame".  Each of n_fw, n_ft must factor into 2, 3,
+ * 5 and 7, n_ft must be even, n_ft <= 14000 and n_fw <= 8192.  Allocates device memory
+ * (response half-spectrum, grid and spectrum scratch): WCSIM_ENOMEM if that fails.
+ * On success *out receives the plane; on failure *out is set to NULL. */
+wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64,
+                                int32_t n_fw, int32_t n_ft, const wcsim_drift_params* params,
+                                void* stream, wcsim_plane** out);
+
+/* Replace the drift parameters (e.g. while fitting D_L, D_T, lifetime).  Host-only. */
+wcsim_status wcsim_plane_set_params(wcsim_plane* plane, const wcsim_drift_params* params);
+
+/* Replace the response spectra (same shape as at create), stream-ordered. */
+wcsim_status wcsim_plane_set_response(wcsim_plane* plane, const void* resp_c64, void* stream);
+
+/* Rasterization + scatter adding (Sec. 2.1.1): drift every depo, rasterize it into its
+ * truncated Gaussian patch (bins meeting [mu - n sigma, mu + n sigma], weights from erf
+ * bin-edge integrals, optional fluctuation) and ADD the patch into `grid` (DEVICE float32
+ * [n_wires * n_imp][n_ticks]; the caller zeroes it).  Additions are atomic, so the
+ * summation order, and the last bits of overlapping bins, vary from run to run. */
+wcsim_status wcsim_rasterize(wcsim_plane* plane, const wcsim_depos* depos, float* grid,
+                             void* stream);
+
+/* Eq. 2: M = IFFT2( sum_j R_j . FFT2(S_j) ), S_j = rows j, j + n_imp, ... of `grid`
+ * (DEVICE float32 [n_wires * n_imp][n_ticks], read only), real part, cropped to the frame,
+ * written to `wave` (DEVICE float32 [n_wires][n_ticks]).  Uses the plane's scratch, so two
+ * calls on one plane must not run concurrently. */
+wcsim_status wcsim_convolve(wcsim_plane* plane, const float* grid, float* wave, void* stream);
+
+/* Whole signal simulation: zero the plane's grid, rasterize `depos` into it, convolve into
+ * `wave` (DEVICE float32 [n_wires][n_ticks]).  Same concurrency rule as wcsim_convolve. */
+wcsim_status wcsim_run(wcsim_plane* plane, const wcsim_depos* depos, float* wave,
+                       void* stream);
+
+/* Bins each depo covers, as decided by wcsim_rasterize: `out` DEVICE int32 [n][4] =
+ * (r_lo, r_hi, k_lo, k_hi) inclusive, or (-1, -1, -1, -1) when the depo covers nothing. */
+wcsim_status wcsim_windows(wcsim_plane* plane, const wcsim_depos* depos, int32_t* out,
+                           void* stream);
+
+/* Wait for the plane's work on `stream`, then read and clear its device flags.
+ * *flags (may be NULL) receives the bit set (bit 0: invalid depo values seen).
+ * Returns WCSIM_EDEVICE_CHECK if any flag was set, WCSIM_OK otherwise. */
+wcsim_status wcsim_plane_check(wcsim_plane* plane, void* stream, int32_t* flags);
+
+/* Per-stage device time of the last compute call on this plane (CUDA events), when
+ * enabled with wcsim_plane_set_timing(plane, 1).  ms[0..n) receives, in order: zero grid,
+ * rasterize+scatter, time-axis forward FFT, wire-axis FFT x response x sum x inverse,
+ * time-axis inverse FFT.  Synchronizes on the recorded events. */
+wcsim_status wcsim_plane_set_timing(wcsim_plane* plane, int32_t enable);
+wcsim_status wcsim_plane_stage_times(wcsim_plane* plane, float* ms, int32_t n);
+
+/* Release the plane and everything it owns.  NULL is accepted. */
+wcsim_status wcsim_plane_destroy(wcsim_plane* plane);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* wcsim_last_error(void);
+
+/* Library version string. */
+const char* wcsim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WCSIM_H */

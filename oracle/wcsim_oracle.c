@@ -146,7 +146,7 @@ static og_depo drift_and_window(const og_geom* g, const og_params* pr, const og_
     d.mu_t = t + td;
     d.att = exp(-td / pr->lifetime_us);
     d.qatt = (double)q * d.att;
-    if (!(d.qatt > 0.0)) return d;
+    if (!(q > 0.0f)) return d;                    /* no charge: covers nothing */
     d.sig_p = sqrt(2.0 * (pr->DT_cm2_s * 1e-4) * td);
     d.sig_t = sqrt(2.0 * (pr->DL_cm2_s * 1e-4) * td) / pr->v_mm_per_us;
     /* the bin decision, in the kernel's precision */
@@ -258,7 +258,7 @@ int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double*
     const uint32_t key[2] = {(uint32_t)pr->seed, (uint32_t)(pr->seed >> 32)};
     for (int64_t i = 0; i < n; ++i) {
         og_depo d = drift_and_window(g, pr, &c, p[i], t[i], td[i], q[i]);
-        if (!d.ok) continue;
+        if (!d.ok || !(d.qatt > 0.0)) continue;   /* Q' underflowed: adds nothing */
         if (d.r_hi - d.r_lo + 1 > OG_MAXB || d.k_hi - d.k_lo + 1 > OG_MAXB) return -1;
         axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
         axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);

@@ -2,15 +2,6 @@
 
 The compute path lives in the CUDA library ``libwcsim.so`` built from ``csrc/``; the Python
 binding in :mod:`paper_2104_08265_gb300.wcsim` only marshals arguments to its C-ABI.
-Import of the binding is lazy so that the input generators in :mod:`.synth` can be used
-without a GPU.
+Submodules are imported explicitly (``from paper_2104_08265_gb300 import wcsim``) so that
+the input generators in :mod:`.synth` can be used without the CUDA library.
 """
-
-__all__ = ["synth", "wcsim"]
-
-
-def __getattr__(name):
-    if name == "wcsim":
-        from . import wcsim as _w
-        return _w
-    raise AttributeError(name)

@@ -1,0 +1,400 @@
+// C-ABI of libwcsim: argument checks, the plane object and stream-ordered launches.
+// Every entry point returns a wcsim_status; nothing here aborts or synchronizes the host
+// except the calls whose contract says so (create, plane_check, stage_times).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "wcsim_internal.cuh"
+
+using namespace wcsim;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+wcsim_status fail(wcsim_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+wcsim_status cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(WCSIM_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(WCSIM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Make the plane's device current for the duration of a call and restore the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+constexpr int kStages = 5;
+
+struct wcsim_plane {
+    wcsim_geometry g;
+    wcsim_drift_params prm;
+    ConvDims dims;
+    FftPlan pt, pw;
+    float2* tw_t = nullptr;
+    float2* tw_w = nullptr;
+    float2* H = nullptr;        // [n_imp][n_fw][nh], Hermitian part of R / (n_fw n_ft)
+    float* grid = nullptr;      // [n_rows][n_ticks]
+    float2* shat = nullptr;     // [n_imp][n_wires][nh]
+    float2* mt = nullptr;       // [n_wires][nh]
+    int* flags = nullptr;       // device flag word
+    int device = 0;
+    bool timing = false;
+    cudaEvent_t ev[kStages + 1] = {};
+    bool ev_valid = false;
+};
+
+namespace {
+
+wcsim_status check_geometry(const wcsim_geometry* g)
+{
+    if (!g) return fail(WCSIM_EINVAL, "geometry is NULL");
+    if (g->n_wires < 1 || g->n_imp < 1 || g->n_ticks < 1)
+        return fail(WCSIM_ESHAPE, "n_wires, n_imp, n_ticks must be >= 1 (got %d, %d, %d)",
+                    g->n_wires, g->n_imp, g->n_ticks);
+    if (g->reserved != 0) return fail(WCSIM_EINVAL, "geometry.reserved must be 0");
+    if (!finite_pos(g->pitch_mm) || !finite_pos(g->tick_us))
+        return fail(WCSIM_EINVAL, "pitch_mm and tick_us must be finite and > 0");
+    if (!isfinite(g->p0_mm) || !isfinite(g->t0_us))
+        return fail(WCSIM_EINVAL, "p0_mm and t0_us must be finite");
+    if ((int64_t)g->n_wires * g->n_imp > (int64_t)1 << 30)
+        return fail(WCSIM_ESHAPE, "n_wires * n_imp too large");
+    return WCSIM_OK;
+}
+
+wcsim_status check_params(const wcsim_drift_params* p)
+{
+    if (!p) return fail(WCSIM_EINVAL, "params is NULL");
+    if (!finite_pos(p->v_mm_per_us)) return fail(WCSIM_EINVAL, "v_mm_per_us must be finite and > 0");
+    if (!(isfinite(p->DL_cm2_s) && p->DL_cm2_s >= 0.0) ||
+        !(isfinite(p->DT_cm2_s) && p->DT_cm2_s >= 0.0))
+        return fail(WCSIM_EINVAL, "DL_cm2_s and DT_cm2_s must be finite and >= 0");
+    if (!(p->lifetime_us > 0.0)) return fail(WCSIM_EINVAL, "lifetime_us must be > 0");
+    if (!finite_pos(p->nsigma)) return fail(WCSIM_EINVAL, "nsigma must be finite and > 0");
+    if (p->fluctuate != 0 && p->fluctuate != 1) return fail(WCSIM_EINVAL, "fluctuate must be 0 or 1");
+    return WCSIM_OK;
+}
+
+wcsim_status check_depos(const wcsim_depos* d)
+{
+    if (!d) return fail(WCSIM_EINVAL, "depos is NULL");
+    if (d->n < 0) return fail(WCSIM_ESHAPE, "depos.n must be >= 0");
+    if (d->n > ((int64_t)1 << 32)) return fail(WCSIM_ESHAPE, "depos.n too large (max 2^32)");
+    if (d->n > 0 && (!d->p_mm || !d->t_us || !d->tdrift_us || !d->q || !d->id))
+        return fail(WCSIM_EINVAL, "depo array pointer is NULL");
+    return WCSIM_OK;
+}
+
+// The per-call constants of the bin decision, in the same operation order the oracle
+// documents: d = pitch / n_imp, 1/d, 1/tick in FP64; 2 D [mm^2/us] = 2 (D 1e-4) rounded to
+// FP32; 1/v, n_sigma, 1/bin rounded to FP32.
+RasterConsts make_consts(const wcsim_plane* pl)
+{
+    RasterConsts c;
+    const wcsim_geometry& g = pl->g;
+    const wcsim_drift_params& p = pl->prm;
+    const double dp = g.pitch_mm / (double)g.n_imp;
+    c.p0 = g.p0_mm;
+    c.t0 = g.t0_us;
+    c.inv_dp = 1.0 / dp;
+    c.inv_dt = 1.0 / g.tick_us;
+    c.two_dt = (float)(2.0 * (p.DT_cm2_s * 1e-4));
+    c.two_dl = (float)(2.0 * (p.DL_cm2_s * 1e-4));
+    c.inv_v = (float)(1.0 / p.v_mm_per_us);
+    c.nsig = (float)p.nsigma;
+    c.inv_dp_f = (float)c.inv_dp;
+    c.inv_dt_f = (float)c.inv_dt;
+    c.dp_f = (float)dp;
+    c.dt_f = (float)g.tick_us;
+    c.inv_tau = (float)(1.0 / p.lifetime_us);
+    c.n_rows = (int64_t)g.n_wires * g.n_imp;
+    c.n_ticks = g.n_ticks;
+    c.fluctuate = p.fluctuate;
+    c.key0 = (uint32_t)p.seed;
+    c.key1 = (uint32_t)(p.seed >> 32);
+    c.plane_id = p.plane_id;
+    return c;
+}
+
+DepoArrays depo_arrays(const wcsim_depos* d)
+{
+    DepoArrays a;
+    a.p = d->p_mm;
+    a.t = d->t_us;
+    a.td = d->tdrift_us;
+    a.q = d->q;
+    a.id = d->id;
+    a.n = d->n;
+    return a;
+}
+
+void plane_free(wcsim_plane* pl)
+{
+    if (!pl) return;
+    cudaFree(pl->tw_t);
+    cudaFree(pl->tw_w);
+    cudaFree(pl->H);
+    cudaFree(pl->grid);
+    cudaFree(pl->shat);
+    cudaFree(pl->mt);
+    cudaFree(pl->flags);
+    if (pl->ev_valid)
+        for (auto& e : pl->ev) cudaEventDestroy(e);
+    delete pl;
+}
+
+inline void mark(wcsim_plane* pl, int i, cudaStream_t s)
+{
+    if (pl->timing) cudaEventRecord(pl->ev[i], s);
+}
+
+wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaStream_t s,
+                         int first_mark)
+{
+    cudaError_t e;
+    if ((e = launch_rows_r2c(pl->dims, pl->pt, grid, pl->shat, s))) return cuda_fail(e, "rows_r2c launch");
+    mark(pl, first_mark, s);
+    if ((e = launch_wire_pass(pl->dims, pl->pw, pl->shat, pl->H, pl->mt, s)))
+        return cuda_fail(e, "wire_pass launch");
+    mark(pl, first_mark + 1, s);
+    if ((e = launch_rows_c2r(pl->dims, pl->pt, pl->mt, wave, s))) return cuda_fail(e, "rows_c2r launch");
+    mark(pl, first_mark + 2, s);
+    return WCSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* wcsim_last_error(void) { return g_err; }
+
+const char* wcsim_version(void) { return "wcsim 0.1 (sm_103a)"; }
+
+wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64, int32_t n_fw,
+                                int32_t n_ft, const wcsim_drift_params* params, void* stream,
+                                wcsim_plane** out)
+{
+    if (!out) return fail(WCSIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    wcsim_status st;
+    if ((st = check_geometry(geom))) return st;
+    if ((st = check_params(params))) return st;
+    if (!resp_c64) return fail(WCSIM_EINVAL, "response pointer is NULL");
+    if (n_fw == 0) n_fw = geom->n_wires;
+    if (n_ft == 0) n_ft = geom->n_ticks;
+    if (n_fw < geom->n_wires || n_ft < geom->n_ticks)
+        return fail(WCSIM_ESHAPE, "spectrum (%d x %d) smaller than the frame (%d x %d)", n_fw,
+                    n_ft, geom->n_wires, geom->n_ticks);
+    if (n_ft > kMaxFftN || n_fw > kMaxWireN)
+        return fail(WCSIM_ESHAPE, "FFT size %d x %d above the supported %d x %d", n_fw, n_ft,
+                    kMaxWireN, kMaxFftN);
+    int32_t rad[kMaxPasses], np;
+    if (!fft_factor(n_fw, rad, &np) || !fft_factor(n_ft, rad, &np))
+        return fail(WCSIM_ESHAPE, "FFT sizes must factor into 2, 3, 5, 7 (got %d x %d)", n_fw, n_ft);
+
+    wcsim_plane* pl = new (std::nothrow) wcsim_plane();
+    if (!pl) return fail(WCSIM_ENOMEM, "host allocation failed");
+    pl->g = *geom;
+    pl->prm = *params;
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e) { plane_free(pl); return cuda_fail(e, "cudaGetDevice"); }
+    ConvDims& d = pl->dims;
+    d.n_w = geom->n_wires;
+    d.n_imp = geom->n_imp;
+    d.n_t = geom->n_ticks;
+    d.n_fw = n_fw;
+    d.n_ft = n_ft;
+    d.nh = n_ft / 2 + 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n_rows = (size_t)d.n_w * d.n_imp;
+#define WC_TRY(call, what)                                  \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) {                            \
+            plane_free(pl);                                 \
+            return cuda_fail(_e, what);                     \
+        }                                                   \
+    } while (0)
+    WC_TRY(fft_plan_create(n_ft, &pl->pt, &pl->tw_t), "time-axis FFT plan");
+    WC_TRY(fft_plan_create(n_fw, &pl->pw, &pl->tw_w), "wire-axis FFT plan");
+    WC_TRY(cudaMalloc(&pl->H, (size_t)d.n_imp * d.n_fw * d.nh * sizeof(float2)), "response allocation");
+    WC_TRY(cudaMalloc(&pl->grid, n_rows * d.n_t * sizeof(float)), "grid allocation");
+    WC_TRY(cudaMalloc(&pl->shat, n_rows * d.nh * sizeof(float2)), "spectrum allocation");
+    WC_TRY(cudaMalloc(&pl->mt, (size_t)d.n_w * d.nh * sizeof(float2)), "spectrum allocation");
+    WC_TRY(cudaMalloc(&pl->flags, sizeof(int)), "flag allocation");
+    WC_TRY(cudaMemsetAsync(pl->flags, 0, sizeof(int), s), "flag reset");
+    WC_TRY(launch_make_hermitian(d, (const float2*)resp_c64, pl->H,
+                                 (float)(1.0 / ((double)n_fw * (double)n_ft)), s),
+           "response preparation");
+    WC_TRY(cudaStreamSynchronize(s), "response preparation");
+    for (auto& ev : pl->ev) WC_TRY(cudaEventCreate(&ev), "event creation");
+    pl->ev_valid = true;
+#undef WC_TRY
+    *out = pl;
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_set_params(wcsim_plane* pl, const wcsim_drift_params* params)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    wcsim_status st = check_params(params);
+    if (st) return st;
+    pl->prm = *params;
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_set_response(wcsim_plane* pl, const void* resp_c64, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (!resp_c64) return fail(WCSIM_EINVAL, "response pointer is NULL");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    const ConvDims& d = pl->dims;
+    cudaError_t e = launch_make_hermitian(d, (const float2*)resp_c64, pl->H,
+                                          (float)(1.0 / ((double)d.n_fw * (double)d.n_ft)),
+                                          (cudaStream_t)stream);
+    return e ? cuda_fail(e, "response preparation") : WCSIM_OK;
+}
+
+wcsim_status wcsim_rasterize(wcsim_plane* pl, const wcsim_depos* depos, float* grid, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    wcsim_status st = check_depos(depos);
+    if (st) return st;
+    if (!grid) return fail(WCSIM_EINVAL, "grid is NULL");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    mark(pl, 0, s);
+    mark(pl, 1, s);
+    cudaError_t e = launch_rasterize(make_consts(pl), depo_arrays(depos), grid, pl->flags, s);
+    if (e) return cuda_fail(e, "rasterize launch");
+    for (int i = 2; i <= kStages; ++i) mark(pl, i, s);
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_convolve(wcsim_plane* pl, const float* grid, float* wave, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (!grid || !wave) return fail(WCSIM_EINVAL, "grid or wave is NULL");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    mark(pl, 0, s);
+    mark(pl, 1, s);
+    mark(pl, 2, s);
+    return do_convolve(pl, grid, wave, s, 3);
+}
+
+wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    wcsim_status st = check_depos(depos);
+    if (st) return st;
+    if (!wave) return fail(WCSIM_EINVAL, "wave is NULL");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ConvDims& d = pl->dims;
+    mark(pl, 0, s);
+    cudaError_t e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
+    if (e) return cuda_fail(e, "grid reset");
+    mark(pl, 1, s);
+    e = launch_rasterize(make_consts(pl), depo_arrays(depos), pl->grid, pl->flags, s);
+    if (e) return cuda_fail(e, "rasterize launch");
+    mark(pl, 2, s);
+    return do_convolve(pl, pl->grid, wave, s, 3);
+}
+
+wcsim_status wcsim_windows(wcsim_plane* pl, const wcsim_depos* depos, int32_t* out, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    wcsim_status st = check_depos(depos);
+    if (st) return st;
+    if (!out && depos->n > 0) return fail(WCSIM_EINVAL, "out is NULL");
+    if (((uintptr_t)out & 15) != 0) return fail(WCSIM_EINVAL, "out must be 16-byte aligned");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaError_t e = launch_windows(make_consts(pl), depo_arrays(depos), out, pl->flags,
+                                   (cudaStream_t)stream);
+    return e ? cuda_fail(e, "windows launch") : WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_check(wcsim_plane* pl, void* stream, int32_t* flags)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, pl->flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemsetAsync(pl->flags, 0, sizeof(int), s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "flag read");
+    if (flags) *flags = h;
+    if (h) return fail(WCSIM_EDEVICE_CHECK, "device flagged invalid depo values (flags 0x%x)", h);
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_set_timing(wcsim_plane* pl, int32_t enable)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    pl->timing = enable != 0;
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_stage_times(wcsim_plane* pl, float* ms, int32_t n)
+{
+    if (!pl || (!ms && n > 0)) return fail(WCSIM_EINVAL, "plane or ms is NULL");
+    if (!pl->timing) return fail(WCSIM_EINVAL, "timing is not enabled on this plane");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaError_t e = cudaEventSynchronize(pl->ev[kStages]);
+    if (e) return cuda_fail(e, "event synchronize");
+    for (int i = 0; i < n && i < kStages; ++i) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, pl->ev[i], pl->ev[i + 1]);
+        if (e) return cuda_fail(e, "event elapsed time");
+        ms[i] = t;
+    }
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_destroy(wcsim_plane* pl)
+{
+    if (!pl) return WCSIM_OK;
+    DeviceGuard dg(pl->device);
+    plane_free(pl);
+    return WCSIM_OK;
+}
+
+}  // extern "C"

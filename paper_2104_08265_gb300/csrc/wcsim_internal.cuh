@@ -1,0 +1,85 @@
+// Internal declarations shared by the CUDA translation units of libwcsim.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wcsim.h"
+
+namespace wcsim {
+
+// ------------------------------------------------------------------ depo rasterization
+// Per-call constants of the drift + bin decision.  The FP64 fields place a depo on the
+// grid (positions reach metres, bins are a fraction of a mm); the FP32 fields give the
+// half-width n*sigma/bin.  Both are formed on the host once per call.
+struct RasterConsts {
+    double p0, t0, inv_dp, inv_dt;          // FP64: origins, 1/bin
+    float two_dt, two_dl, inv_v, nsig;      // FP32: 2 D_T, 2 D_L [mm^2/us], 1/v, n_sigma
+    float inv_dp_f, inv_dt_f;               // FP32 copies of 1/bin
+    float dp_f, dt_f;                       // FP32 bin sizes [mm], [us]
+    float inv_tau;                          // FP32 1/lifetime
+    int64_t n_rows;                         // n_wires * n_imp
+    int32_t n_ticks;
+    int32_t fluctuate;
+    uint32_t key0, key1, plane_id;
+};
+
+struct DepoArrays {
+    const double* p;
+    const double* t;
+    const double* td;
+    const float* q;
+    const uint32_t* id;
+    int64_t n;
+};
+
+cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* grid,
+                             int* flags, cudaStream_t s);
+cudaError_t launch_windows(const RasterConsts& c, const DepoArrays& d, int32_t* out,
+                           int* flags, cudaStream_t s);
+
+// ------------------------------------------------------------------ FFT
+constexpr int kMaxPasses = 16;
+constexpr int kMaxFftN = 14000;       // time axis: 2 x N x 8 B of shared memory per CTA
+constexpr int kMaxWireN = 8192;
+
+// Mixed-radix Stockham plan for one length N = prod(radix[p]).  Pass p combines groups
+// of Ns[p] already-transformed points; tw_off[p] indexes (radix-1) * Ns twiddles in the
+// plan's table; ns_magic[p] = ceil(2^32 / Ns[p]) turns j / Ns into a multiply-high.
+struct FftPlan {
+    int32_t n;
+    int32_t npass;
+    int32_t radix[kMaxPasses];
+    int32_t ns[kMaxPasses];
+    int32_t tw_off[kMaxPasses];
+    uint32_t ns_magic[kMaxPasses];
+    uint32_t nb_magic[kMaxPasses];    // ceil(2^32 / (n / radix))
+    const float2* tw;                 // device table, forward sign (exp(-i ...))
+};
+
+// Factor n into supported radices (16, 8, 4, 2, 5, 3, 7); false if impossible.
+bool fft_factor(int n, int32_t* radix, int32_t* npass);
+// Build the plan and upload its twiddle table (FP64 host values rounded to FP32).
+cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw);
+
+struct ConvDims {
+    int32_t n_w, n_imp, n_t;   // frame
+    int32_t n_fw, n_ft;        // FFT sizes
+    int32_t nh;                // n_ft / 2 + 1
+};
+
+// H_j[kw][kt] = s * (R_j[kw][kt] + conj(R_j[-kw][-kt])) / 2 for kt in [0, nh).
+cudaError_t launch_make_hermitian(const ConvDims& d, const float2* resp, float2* H, float scale,
+                                  cudaStream_t s);
+// Time-axis real-to-complex FFT of every grid row; writes Shat[j][w][kt] (kt < nh).
+cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* grid,
+                            float2* shat, cudaStream_t s);
+// Per time-frequency column: wire FFT of each S_j, times H_j, summed over j, inverse
+// wire FFT; writes Mt[w][kt].
+cudaError_t launch_wire_pass(const ConvDims& d, const FftPlan& pw, const float2* shat,
+                             const float2* H, float2* mt, cudaStream_t s);
+// Time-axis complex-to-real inverse FFT of the Hermitian half rows of Mt -> wave.
+cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* mt,
+                            float* wave, cudaStream_t s);
+
+}  // namespace wcsim

@@ -1,0 +1,237 @@
+"""ctypes binding of libwcsim (include/wcsim.h).
+
+Argument marshalling only: torch tensors supply device memory and the current CUDA stream;
+every stage of the simulation runs in the library's CUDA kernels.  There is no CPU or
+eager fallback: if libwcsim.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .synth import Depos, DriftParams, Geometry
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libwcsim.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "wcsim.h")
+
+OK, EINVAL, ESHAPE, ENOMEM, ECUDA, ETIMEOUT, EDEVICE_CHECK = range(7)
+STATUS_NAMES = {0: "WCSIM_OK", 1: "WCSIM_EINVAL", 2: "WCSIM_ESHAPE", 3: "WCSIM_ENOMEM",
+                4: "WCSIM_ECUDA", 5: "WCSIM_ETIMEOUT", 6: "WCSIM_EDEVICE_CHECK"}
+STAGES = ("zero", "rasterize", "rows_r2c", "wire_pass", "rows_c2r")
+
+
+class WcsimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class CGeometry(ctypes.Structure):
+    _fields_ = [("n_wires", ctypes.c_int32), ("n_imp", ctypes.c_int32),
+                ("n_ticks", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pitch_mm", ctypes.c_double), ("p0_mm", ctypes.c_double),
+                ("tick_us", ctypes.c_double), ("t0_us", ctypes.c_double)]
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("v_mm_per_us", ctypes.c_double), ("DL_cm2_s", ctypes.c_double),
+                ("DT_cm2_s", ctypes.c_double), ("lifetime_us", ctypes.c_double),
+                ("nsigma", ctypes.c_double), ("fluctuate", ctypes.c_int32),
+                ("plane_id", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class CDepos(ctypes.Structure):
+    _fields_ = [("p_mm", ctypes.c_void_p), ("t_us", ctypes.c_void_p),
+                ("tdrift_us", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("id", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError("libwcsim.so is not built (%s); run __graft_entry__.build()" % _LIB_PATH)
+    L = ctypes.CDLL(_LIB_PATH)
+    P, vp, i32, st = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int
+    sig = {
+        "wcsim_plane_create": [P(CGeometry), vp, i32, i32, P(CParams), vp, P(vp)],
+        "wcsim_plane_set_params": [vp, P(CParams)],
+        "wcsim_plane_set_response": [vp, vp, vp],
+        "wcsim_rasterize": [vp, P(CDepos), vp, vp],
+        "wcsim_convolve": [vp, vp, vp, vp],
+        "wcsim_run": [vp, P(CDepos), vp, vp],
+        "wcsim_windows": [vp, P(CDepos), vp, vp],
+        "wcsim_plane_check": [vp, vp, P(i32)],
+        "wcsim_plane_set_timing": [vp, i32],
+        "wcsim_plane_stage_times": [vp, P(ctypes.c_float), i32],
+        "wcsim_plane_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L.wcsim_last_error.restype = ctypes.c_char_p
+    L.wcsim_last_error.argtypes = []
+    L.wcsim_version.restype = ctypes.c_char_p
+    L.wcsim_version.argtypes = []
+    _lib = L
+    return L
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/wcsim.h declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(wcsim_[a-z_0-9]+)\s*\(", txt)))
+
+
+def check(status: int):
+    if status != OK:
+        raise WcsimError(status, lib().wcsim_last_error().decode())
+
+
+def c_geometry(g: Geometry) -> CGeometry:
+    return CGeometry(int(g.n_wires), int(g.n_imp), int(g.n_ticks), 0, float(g.pitch_mm),
+                     float(g.p0_mm), float(g.tick_us), float(g.t0_us))
+
+
+def c_params(p: DriftParams) -> CParams:
+    return CParams(float(p.v_mm_per_us), float(p.DL_cm2_s), float(p.DT_cm2_s),
+                   float(p.lifetime_us), float(p.nsigma), int(p.fluctuate),
+                   int(p.plane_id) & 0xFFFFFFFF, int(p.seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+class DeviceDepos:
+    """Depos resident on the GPU (torch tensors); keeps the tensors alive for the C struct."""
+
+    def __init__(self, p, t, td, q, ids):
+        self.p, self.t, self.td, self.q, self.id = p, t, td, q, ids
+        n = int(p.shape[0])
+        for a in (p, t, td, q, ids):
+            assert int(a.shape[0]) == n and a.is_cuda and a.is_contiguous()
+        self.c = CDepos(p.data_ptr(), t.data_ptr(), td.data_ptr(), q.data_ptr(),
+                        ids.data_ptr(), n)
+
+    def __len__(self):
+        return int(self.c.n)
+
+    @classmethod
+    def from_host(cls, d: Depos, device="cuda", non_blocking=False):
+        import torch
+        ids = torch.from_numpy(np.ascontiguousarray(d.id, np.uint32).view(np.int32))
+        return cls(torch.from_numpy(np.ascontiguousarray(d.p, np.float64)).to(device, non_blocking=non_blocking),
+                   torch.from_numpy(np.ascontiguousarray(d.t, np.float64)).to(device, non_blocking=non_blocking),
+                   torch.from_numpy(np.ascontiguousarray(d.td, np.float64)).to(device, non_blocking=non_blocking),
+                   torch.from_numpy(np.ascontiguousarray(d.q, np.float32)).to(device, non_blocking=non_blocking),
+                   ids.to(device, non_blocking=non_blocking))
+
+
+class Plane:
+    """A wire plane: geometry, drift parameters and the detector response (Eq. 2)."""
+
+    def __init__(self, geom: Geometry, params: DriftParams, response, n_fw: int = 0,
+                 n_ft: int = 0, stream=None):
+        import torch
+        L = lib()
+        self.geom, self.params = geom, params
+        if not isinstance(response, torch.Tensor):
+            response = torch.from_numpy(np.ascontiguousarray(response, np.complex64))
+        if not response.is_cuda:
+            response = response.cuda()
+        response = response.contiguous()
+        assert response.dtype == torch.complex64 and response.dim() == 3
+        self.n_fw = n_fw or int(response.shape[1])
+        self.n_ft = n_ft or int(response.shape[2])
+        h = ctypes.c_void_p()
+        check(L.wcsim_plane_create(ctypes.byref(c_geometry(geom)), response.data_ptr(),
+                                   self.n_fw, self.n_ft, ctypes.byref(c_params(params)),
+                                   _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wcsim_plane_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: DriftParams):
+        check(lib().wcsim_plane_set_params(self._h, ctypes.byref(c_params(params))))
+        self.params = params
+
+    def set_response(self, response, stream=None):
+        check(lib().wcsim_plane_set_response(self._h, response.contiguous().data_ptr(),
+                                             _stream_handle(stream)))
+
+    def _wave(self, out):
+        import torch
+        if out is None:
+            out = torch.empty((self.geom.n_wires, self.geom.n_ticks), dtype=torch.float32,
+                              device="cuda")
+        assert out.dtype == torch.float32 and out.is_contiguous()
+        return out
+
+    def rasterize(self, depos: DeviceDepos, grid, stream=None):
+        """Add every depo's patch into ``grid`` (float32 [n_wires*n_imp][n_ticks])."""
+        assert grid.is_contiguous() and grid.numel() == self.geom.n_rows * self.geom.n_ticks
+        check(lib().wcsim_rasterize(self._h, ctypes.byref(depos.c), grid.data_ptr(),
+                                    _stream_handle(stream)))
+        return grid
+
+    def convolve(self, grid, out=None, stream=None):
+        out = self._wave(out)
+        check(lib().wcsim_convolve(self._h, grid.data_ptr(), out.data_ptr(),
+                                   _stream_handle(stream)))
+        return out
+
+    def run(self, depos: DeviceDepos, out=None, stream=None):
+        out = self._wave(out)
+        check(lib().wcsim_run(self._h, ctypes.byref(depos.c), out.data_ptr(),
+                              _stream_handle(stream)))
+        return out
+
+    def windows(self, depos: DeviceDepos, stream=None):
+        import torch
+        out = torch.empty((len(depos), 4), dtype=torch.int32, device="cuda")
+        check(lib().wcsim_windows(self._h, ctypes.byref(depos.c), out.data_ptr(),
+                                  _stream_handle(stream)))
+        return out
+
+    def check_flags(self, stream=None) -> int:
+        f = ctypes.c_int32(0)
+        st = lib().wcsim_plane_check(self._h, _stream_handle(stream), ctypes.byref(f))
+        if st not in (OK, EDEVICE_CHECK):
+            check(st)
+        return int(f.value)
+
+    def set_timing(self, enable: bool = True):
+        check(lib().wcsim_plane_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self) -> dict:
+        arr = (ctypes.c_float * len(STAGES))()
+        check(lib().wcsim_plane_stage_times(self._h, arr, len(STAGES)))
+        return dict(zip(STAGES, [float(x) for x in arr]))
