@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--workload", default="plane960-100k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--soak-s", type=float, default=0.5,
+                    help="untimed load before the timed loop, so the clock sampler sees the GPU busy")
     return ap.parse_args()
 
 
@@ -118,7 +121,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -191,6 +194,34 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- cuFFT comparison
+def cufft_comparison(g, reps=10):
+    """The same three transforms through torch.fft (cuFFT), for context only: never on
+    the simulation path.  ms per transform set, averaged over `reps` after 2 warm-ups."""
+    import torch
+    nh = g.n_ticks // 2 + 1
+    grid = torch.randn(g.n_rows, g.n_ticks, device="cuda")
+    spec = torch.randn(g.n_imp, g.n_wires, nh, dtype=torch.complex64, device="cuda")
+    mt = torch.randn(g.n_wires, nh, dtype=torch.complex64, device="cuda")
+    ops = {"rows_r2c": lambda: torch.fft.rfft(grid, dim=1),
+           "wire_fft_fwd_all_j": lambda: torch.fft.fft(spec, dim=1),
+           "wire_fft_inv": lambda: torch.fft.ifft(mt, dim=0),
+           "rows_c2r": lambda: torch.fft.irfft(mt, n=g.n_ticks, dim=1)}
+    out = {}
+    for k, f in ops.items():
+        for _ in range(2):
+            f()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        out[k + "_ms"] = a.elapsed_time(b) / reps
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -226,8 +257,13 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
 
-    plane.set_timing(True)
     clocks = Clocks(local)
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < args.soak_s:
+        for _ in range(20):
+            plane.run(dd, out=wave)
+        torch.cuda.synchronize()
+    plane.set_timing(True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage_ms = {k: [] for k in wcsim.STAGES}
@@ -295,6 +331,9 @@ def run_gpu(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_ms / args.steps}
 
+    cufft = None
+    if rank == 0 and not args.no_cufft:
+        cufft = cufft_comparison(g)
     if rank != 0:
         return
     hbm, peak_kind = peaks()
@@ -326,6 +365,7 @@ def run_gpu(args):
         "wall_s_timed_loop": wall,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "cufft_comparison": cufft,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -88,7 +88,7 @@ typedef struct {
  * read during this call (stream-ordered) and not retained.  n_fw >= n_wires and
  * n_ft >= n_ticks set the FFT size (the frame is zero-padded; equal sizes give circular
  * convolution); 0 means "same as the frame".  Each of n_fw, n_ft must factor into 2, 3,
- * 5 and 7, n_ft must be even, n_ft <= 14000 and n_fw <= 8192.  Allocates device memory
+ * 5 and 7, n_ft <= 13500 and n_fw <= 8192.  Allocates device memory
  * (response half-spectrum, grid and spectrum scratch): WCSIM_ENOMEM if that fails.
  * On success *out receives the plane; on failure *out is set to NULL. */
 wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64,

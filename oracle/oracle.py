@@ -74,8 +74,10 @@ def _load():
             P = ctypes.POINTER
             d, f, u32, i64 = ctypes.c_double, ctypes.c_float, ctypes.c_uint32, ctypes.c_int64
             lib.og_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
-            lib.og_normal.argtypes = [u32, u32]
+            lib.og_normal.argtypes = [u32, u32, ctypes.c_int]
             lib.og_normal.restype = d
+            lib.og_bin_normal.argtypes = [i64, i64, u32, u32, P(u32)]
+            lib.og_bin_normal.restype = d
             lib.og_windows.argtypes = [P(_Geom), P(_Params), i64, P(d), P(d), P(d), P(f),
                                        P(i64)]
             lib.og_depo_weights.argtypes = [P(_Geom), P(_Params), d, d, d, f, P(d), P(d),
@@ -126,9 +128,16 @@ def philox4x32_10(ctr, key):
     return [int(o[i]) for i in range(4)]
 
 
-def normal_from_words(x0: int, x1: int) -> float:
-    """Box-Muller standard normal from two Philox words (FP64)."""
-    return float(_load().og_normal(int(x0) & 0xFFFFFFFF, int(x1) & 0xFFFFFFFF))
+def normal_from_words(x0: int, x1: int, which: int = 0) -> float:
+    """Box-Muller standard normal from two Philox words (FP64); which: 0 cos, 1 sin."""
+    return float(_load().og_normal(int(x0) & 0xFFFFFFFF, int(x1) & 0xFFFFFFFF, int(which)))
+
+
+def bin_normal(r: int, k: int, depo_id: int, plane_id: int, seed: int) -> float:
+    """The standard normal that fluctuates bin (row r, tick k) of a depo."""
+    key = (ctypes.c_uint32 * 2)(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    return float(_load().og_bin_normal(int(r), int(k), int(depo_id) & 0xFFFFFFFF,
+                                       int(plane_id) & 0xFFFFFFFF, key))
 
 
 # --------------------------------------------------------------------------- a1-a3

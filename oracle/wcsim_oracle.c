@@ -25,8 +25,12 @@
  *     both sides pick the same bins; everything else here is FP64;
  *   - sigma == 0 (in that FP32 decision) puts all of an axis' weight into the single bin;
  *   - no renormalisation after truncation;
- *   - Philox counter = (tick k, row r, depo id, plane id), key = (seed lo, seed hi);
- *     u = (x + 0.5) 2^-32;  z = sqrt(-2 ln u1) cos(2 pi u2).
+ *   - one Philox block per aligned group of four ticks of a row: counter = (k div 4, row r,
+ *     depo id, plane id), key = (seed lo, seed hi).  Its four words form two Box-Muller
+ *     pairs, u = (x + 0.5) 2^-32, giving four normals
+ *       z0 = sqrt(-2 ln u0) cos(2 pi u1),  z1 = sqrt(-2 ln u0) sin(2 pi u1),
+ *       z2 = sqrt(-2 ln u2) cos(2 pi u3),  z3 = sqrt(-2 ln u2) sin(2 pi u3);
+ *     bin (r, k) takes z_(k mod 4).
  *
  * Build: cc -O2 -ffp-contract=off -fPIC -shared wcsim_oracle.c -lm
  * (no FMA contraction: the bin decision must be evaluated operation by operation).
@@ -73,13 +77,25 @@ void og_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Box-Muller (Box & Muller 1958) on the first two Philox words, in FP64. */
-double og_normal(uint32_t x0, uint32_t x1)
+/* Box-Muller (Box & Muller 1958): two independent standard normals from two words,
+ * u = (x + 0.5) 2^-32, in FP64.  which = 0 gives the cosine member, 1 the sine member. */
+double og_normal(uint32_t x0, uint32_t x1, int which)
 {
     const double two_m32 = 1.0 / 4294967296.0;
     double u1 = ((double)x0 + 0.5) * two_m32;
     double u2 = ((double)x1 + 0.5) * two_m32;
-    return sqrt(-2.0 * log(u1)) * cos(2.0 * OG_PI * u2);
+    double rad = sqrt(-2.0 * log(u1));
+    return which ? rad * sin(2.0 * OG_PI * u2) : rad * cos(2.0 * OG_PI * u2);
+}
+
+/* The normal of bin (row r, tick k): member k mod 4 of the block keyed by k div 4. */
+double og_bin_normal(int64_t r, int64_t k, uint32_t id, uint32_t plane_id, const uint32_t key[2])
+{
+    uint32_t ctr[4] = {(uint32_t)(k >> 2), (uint32_t)r, id, plane_id};
+    uint32_t x[4];
+    og_philox4x32_10(ctr, key, x);
+    int m = (int)(k & 3);
+    return (m < 2) ? og_normal(x[0], x[1], m) : og_normal(x[2], x[3], m - 2);
 }
 
 /* Per-call constants of the bin decision, formed the same way for every depo. */
@@ -269,10 +285,7 @@ int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double*
                 double val = mean;
                 if (pr->fluctuate) {
                     /* normal approximation to Binomial(Q', mean/Q') */
-                    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)r, id[i], pr->plane_id};
-                    uint32_t x[4];
-                    og_philox4x32_10(ctr, key, x);
-                    double z = og_normal(x[0], x[1]);
+                    double z = og_bin_normal(r, k, id[i], pr->plane_id, key);
                     double var = mean * (1.0 - mean / d.qatt);
                     if (var < 0.0) var = 0.0;
                     val = mean + sqrt(var) * z;

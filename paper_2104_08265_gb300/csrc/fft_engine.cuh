@@ -1,0 +1,320 @@
+// Device FFT engine: register DFTs and mixed-radix Stockham passes over shared memory.
+//
+// A plan factors N into a few radices R <= 25 (composite radices such as 20 or 24 are
+// transformed entirely in registers), so that a 6000-point transform takes three
+// shared-memory passes.  Pass p (Ns = product of the earlier radices) reads
+// x[j + r N/R], r < R, multiplies by exp(-+2 pi i r (j mod Ns) / (Ns R)), applies the
+// R-point DFT and writes y[(j / Ns) Ns R + (j mod Ns) + r Ns]; the result is in natural
+// order.  B = 2^LOGB independent sequences are transformed together; element (c, i) of the
+// batch lives at buf[pad(i) * B + c], where pad() inserts one slot every 16 elements so
+// that the stride-R writes of early passes do not pile onto one shared-memory bank.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dft_roots.cuh"
+#include "wcsim_internal.cuh"
+
+namespace wcsim {
+
+__host__ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4) + 1; }
+
+// ------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * w (forward) or a * conj(w) (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 twiddle(float2 a, float2 w)
+{
+    return INV ? make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y) : cmul(a, w);
+}
+// -i a (forward) or +i a (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ------------------------------------------------------------------ small DFTs
+template <bool INV>
+__device__ __forceinline__ void dft4v(float2& v0, float2& v1, float2& v2, float2& v3)
+{
+    const float2 s02 = cadd(v0, v2), d02 = csub(v0, v2);
+    const float2 s13 = cadd(v1, v3), d13 = rot<INV>(csub(v1, v3));
+    v0 = cadd(s02, s13);
+    v2 = csub(s02, s13);
+    v1 = cadd(d02, d13);
+    v3 = csub(d02, d13);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3v(float2* v)
+{
+    const float s3 = 0.866025403784438647f;
+    const float2 t = cadd(v[1], v[2]);
+    const float2 d = rot<INV>(cscale(csub(v[1], v[2]), s3));
+    const float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, d);
+    v[2] = csub(m, d);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft5v(float2* v)
+{
+    const float c1 = 0.309016994374947424f, c2 = -0.809016994374947424f;
+    const float s1 = 0.951056516295153572f, s2 = 0.587785252292473129f;
+    const float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+    const float2 d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
+    const float2 v0 = v[0];
+    const float2 a1 = make_float2(v0.x + c1 * t1.x + c2 * t2.x, v0.y + c1 * t1.y + c2 * t2.y);
+    const float2 a2 = make_float2(v0.x + c2 * t1.x + c1 * t2.x, v0.y + c2 * t1.y + c1 * t2.y);
+    const float2 b1 = rot<INV>(make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
+    const float2 b2 = rot<INV>(make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+    v[0] = cadd(v0, cadd(t1, t2));
+    v[1] = cadd(a1, b1);
+    v[4] = csub(a1, b1);
+    v[2] = cadd(a2, b2);
+    v[3] = csub(a2, b2);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft7v(float2* v)
+{
+    // cos / sin (2 pi m / 7), m = 1, 2, 3
+    const float c[3] = {0.623489801858733530f, -0.222520933956314404f, -0.900968867902419126f};
+    const float s[3] = {0.781831482468029809f, 0.974927912181823607f, 0.433883739117558120f};
+    float2 t[3], d[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        t[p] = cadd(v[p + 1], v[6 - p]);
+        d[p] = csub(v[p + 1], v[6 - p]);
+    }
+    const float2 v0 = v[0];
+    v[0] = cadd(v0, cadd(t[0], cadd(t[1], t[2])));
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) {
+        float2 a = v0, b = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int p = 1; p <= 3; ++p) {
+            const int m = (p * k) % 7;
+            const float cm = (m <= 3) ? c[m - 1] : c[7 - m - 1];
+            const float sm = (m <= 3) ? s[m - 1] : -s[7 - m - 1];
+            a.x += cm * t[p - 1].x; a.y += cm * t[p - 1].y;
+            b.x += sm * d[p - 1].x; b.y += sm * d[p - 1].y;
+        }
+        const float2 rb = rot<INV>(b);
+        v[k] = cadd(a, rb);
+        v[7 - k] = csub(a, rb);
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8v(float2* v)
+{
+    const float h = 0.707106781186547524f;
+    dft4v<INV>(v[0], v[2], v[4], v[6]);
+    dft4v<INV>(v[1], v[3], v[5], v[7]);
+    float2 o1 = v[3], o2 = v[5], o3 = v[7];
+    o1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y))
+             : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    o2 = rot<INV>(o2);
+    o3 = INV ? make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y))
+             : make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    const float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16v(float2* v)
+{
+    // X[k1 + 4 k2] = sum_b w16^(b k1) w4^(b k2) Y_b[k1],  Y_b = DFT4 of v[b + 4 a] over a
+#pragma unroll
+    for (int b = 0; b < 4; ++b) dft4v<INV>(v[b], v[b + 4], v[b + 8], v[b + 12]);
+    const float cs[4] = {1.0f, 0.923879532511286756f, 0.707106781186547524f, 0.382683432365089772f};
+#pragma unroll
+    for (int b = 1; b < 4; ++b)
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) {
+            const int m = b * k1;
+            const int q = m / 4, rr = m % 4;
+            const float cr = cs[rr], sr = (rr == 0) ? 0.0f : cs[4 - rr];
+            float cm, sm;
+            if (q == 0) { cm = cr; sm = sr; }
+            else if (q == 1) { cm = -sr; sm = cr; }
+            else { cm = -cr; sm = -sr; }
+            v[b + 4 * k1] = cmul(v[b + 4 * k1], make_float2(cm, INV ? sm : -sm));
+        }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4v<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    float2 o[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = o[i];
+}
+
+// First factor of a composite radix for the Cooley-Tukey split R = A * B.
+template <int R>
+struct Split {
+    static constexpr int A = (R % 16 == 0 && R != 16) ? 16
+                           : (R % 8 == 0 && R != 8) ? 8
+                           : (R % 4 == 0 && R != 4) ? 4
+                           : (R % 2 == 0) ? 2
+                           : (R % 3 == 0) ? 3
+                           : (R % 5 == 0) ? 5 : 7;
+    static constexpr int B = R / A;
+};
+
+// In-register R-point DFT, natural order in and out.  Composite R: n = B n1 + n2,
+// k = k1 + A k2;  A-point DFTs over n1, twiddle exp(-+2 pi i n2 k1 / R), B-point DFTs over n2.
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v)
+{
+    if constexpr (R == 1) {
+    } else if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 3) {
+        dft3v<INV>(v);
+    } else if constexpr (R == 4) {
+        dft4v<INV>(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 5) {
+        dft5v<INV>(v);
+    } else if constexpr (R == 7) {
+        dft7v<INV>(v);
+    } else if constexpr (R == 8) {
+        dft8v<INV>(v);
+    } else if constexpr (R == 16) {
+        dft16v<INV>(v);
+    } else {
+        constexpr int A = Split<R>::A, B = Split<R>::B;
+        float2 y[R];
+#pragma unroll
+        for (int n2 = 0; n2 < B; ++n2) {
+            float2 t[A];
+#pragma unroll
+            for (int n1 = 0; n1 < A; ++n1) t[n1] = v[B * n1 + n2];
+            dft<A, INV>(t);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) {
+                float2 x = t[k1];
+                if (n2 * k1 != 0) {
+                    const float c = Roots<R>::c((n2 * k1) % R), s = Roots<R>::s((n2 * k1) % R);
+                    x = INV ? make_float2(x.x * c - x.y * s, x.x * s + x.y * c)
+                            : make_float2(x.x * c + x.y * s, x.y * c - x.x * s);
+                }
+                y[n2 * A + k1] = x;
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+            float2 t[B];
+#pragma unroll
+            for (int n2 = 0; n2 < B; ++n2) t[n2] = y[n2 * A + k1];
+            dft<B, INV>(t);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = t[k2];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ shared-memory access
+template <int LOGB>
+struct SmemLd {
+    const float2* p;
+    __device__ __forceinline__ float2 operator()(int c, int i) const { return p[(pad16(i) << LOGB) + c]; }
+};
+template <int LOGB>
+struct SmemSt {
+    float2* p;
+    __device__ __forceinline__ void operator()(int c, int i, float2 v) const { p[(pad16(i) << LOGB) + c] = v; }
+};
+
+struct PassArgs {
+    int n, ns;
+    uint32_t ns_magic;
+    const float2* tw;
+};
+
+// One Stockham pass of radix R over a batch of 2^LOGB sequences.
+template <int R, bool INV, int LOGB, class Ld, class St>
+__device__ __forceinline__ void pass_r(const Ld& ld, const St& st, const PassArgs& a)
+{
+    const int nb = a.n / R;
+    const int total = nb << LOGB;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int c = idx & ((1 << LOGB) - 1);
+        const int j = idx >> LOGB;
+        const int q = (a.ns == 1) ? j : (int)__umulhi((uint32_t)j, a.ns_magic);
+        const int k = j - q * a.ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = ld(c, j + r * nb);
+        if (k > 0) {
+            const float2* t = a.tw + k * (R - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], __ldg(t + r - 1));
+        }
+        dft<R, INV>(v);
+        const int o = q * a.ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) st(c, o + r * a.ns, v[r]);
+    }
+}
+
+// Radices a plan may use (every one has a pass_r instantiation below).
+#define WCSIM_FOR_EACH_RADIX(X) \
+    X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(10) X(12) X(14) X(15) X(16) X(20) X(24) X(25)
+
+template <bool INV, int LOGB, class Ld, class St>
+__device__ __forceinline__ void pass_any(int R, const Ld& ld, const St& st, const PassArgs& a)
+{
+    switch (R) {
+#define WCSIM_CASE(RR) case RR: pass_r<RR, INV, LOGB>(ld, st, a); break;
+        WCSIM_FOR_EACH_RADIX(WCSIM_CASE)
+#undef WCSIM_CASE
+        default: {   // R == 1: a copy
+            for (int idx = threadIdx.x; idx < (a.n << LOGB); idx += blockDim.x) {
+                const int c = idx & ((1 << LOGB) - 1), i = idx >> LOGB;
+                st(c, i, ld(c, i));
+            }
+        }
+    }
+}
+
+// All passes of plan p.  The first pass reads through `first` (global memory or a shared
+// buffer outside X/Y), later passes ping-pong between X and Y.  Returns the buffer holding
+// the transform; ends with a block barrier.
+template <bool INV, int LOGB, class FirstLd>
+__device__ __forceinline__ float2* run_plan(const FftPlan& p, const FirstLd& first, float2* X, float2* Y)
+{
+    float2* dst = X;
+    for (int i = 0; i < p.npass; ++i) {
+        const PassArgs a = {p.n, p.ns[i], p.ns_magic[i], p.tw + p.tw_off[i]};
+        dst = (i & 1) ? Y : X;
+        if (i == 0) {
+            pass_any<INV, LOGB>(p.radix[0], first, SmemSt<LOGB>{dst}, a);
+        } else {
+            const float2* src = (i & 1) ? X : Y;
+            pass_any<INV, LOGB>(p.radix[i], SmemLd<LOGB>{src}, SmemSt<LOGB>{dst}, a);
+        }
+        __syncthreads();
+    }
+    return dst;
+}
+
+}  // namespace wcsim

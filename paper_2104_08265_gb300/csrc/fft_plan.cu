@@ -1,0 +1,105 @@
+// Host side of the FFT engine: choosing the radices of a plan and its twiddle table.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "wcsim_internal.cuh"
+
+namespace wcsim {
+
+namespace {
+
+// Radices with a register DFT (the WCSIM_FOR_EACH_RADIX list in fft_engine.cuh), with a rough per-element
+// arithmetic cost used to rank plans of the same pass count.
+struct RadixCost {
+    int r;
+    double cost;
+};
+const RadixCost kRadices[] = {{2, 2.0},  {3, 4.0},  {4, 4.0},  {5, 6.8},  {6, 6.0},
+                              {7, 10.0}, {8, 5.5},  {10, 7.2}, {12, 7.3}, {14, 11.0},
+                              {15, 9.0}, {16, 6.5}, {20, 8.5}, {24, 8.7}, {25, 10.8}};
+
+// Fewest passes first (each pass is a round trip through shared memory), then the
+// smallest arithmetic; depth-first over divisors.
+void search(int n, int depth, int* cur, double cost, int* best, int* best_len, double* best_cost)
+{
+    if (n == 1) {
+        const double total = cost + 100.0 * depth;
+        if (*best_len < 0 || total < *best_cost) {
+            *best_cost = total;
+            *best_len = depth;
+            for (int i = 0; i < depth; ++i) best[i] = cur[i];
+        }
+        return;
+    }
+    if (depth >= kMaxPasses) return;
+    if (*best_len >= 0 && cost + 100.0 * (depth + 1) >= *best_cost) return;
+    const int nr = (int)(sizeof(kRadices) / sizeof(kRadices[0]));
+    for (int i = nr - 1; i >= 0; --i) {       // large radices first: good plans early
+        const RadixCost& rc = kRadices[i];
+        if (n % rc.r) continue;
+        cur[depth] = rc.r;
+        search(n / rc.r, depth + 1, cur, cost + rc.cost, best, best_len, best_cost);
+    }
+}
+
+uint32_t magic_for(int d) { return d <= 1 ? 0u : (uint32_t)((0x100000000ull + d - 1) / (uint64_t)d); }
+
+}  // namespace
+
+bool fft_factor(int n, int32_t* radix, int32_t* npass)
+{
+    if (n < 1) return false;
+    if (n == 1) {
+        radix[0] = 1;
+        *npass = 1;
+        return true;
+    }
+    int cur[kMaxPasses], best[kMaxPasses], best_len = -1;
+    double best_cost = 0.0;
+    search(n, 0, cur, 0.0, best, &best_len, &best_cost);
+    if (best_len < 0) return false;
+    // larger radices first: the first pass carries no twiddles
+    for (int i = 0; i < best_len; ++i)
+        for (int k = i + 1; k < best_len; ++k)
+            if (best[k] > best[i]) { int t = best[i]; best[i] = best[k]; best[k] = t; }
+    for (int i = 0; i < best_len; ++i) radix[i] = best[i];
+    *npass = best_len;
+    return true;
+}
+
+cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw)
+{
+    FftPlan p{};
+    p.n = n;
+    if (!fft_factor(n, p.radix, &p.npass)) return cudaErrorInvalidValue;
+    std::vector<float2> tw;
+    int ns = 1;
+    for (int i = 0; i < p.npass; ++i) {
+        const int R = p.radix[i];
+        p.ns[i] = ns;
+        p.tw_off[i] = (int32_t)tw.size();
+        p.ns_magic[i] = magic_for(ns);
+        // twiddle (k, r) = exp(-2 pi i r k / (ns R)), stored at k (R - 1) + r - 1
+        for (int k = 0; k < ns; ++k)
+            for (int r = 1; r < R; ++r) {
+                const double a = -2.0 * M_PI * (double)r * (double)k / ((double)ns * R);
+                tw.push_back(make_float2((float)cos(a), (float)sin(a)));
+            }
+        ns *= R;
+    }
+    if (tw.empty()) tw.push_back(make_float2(1.f, 0.f));
+    float2* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, tw.size() * sizeof(float2));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return e; }
+    p.tw = d;
+    *plan = p;
+    *dev_tw = d;
+    return cudaSuccess;
+}
+
+}  // namespace wcsim

@@ -2,14 +2,14 @@
 // (Sec. 2.1.1 "rasterization" and "scatter adding"; drift and diffusion as in Fig. 2;
 // fluctuation with a Box-Muller normal as in Sec. 3.3.1).
 //
-// Work split.  A warp owns 32 consecutive depos.  First every lane takes the FP64 bin
-// decision of its own depo (one thread per depo: FP64 is scarce on this part, so it is
-// never evaluated redundantly by a whole warp).  Then the warp walks its 32 depos one by
-// one: lanes compute the per-bin 1D weights of the depo's patch into shared memory (FP32
-// erf/erfc of bin-edge offsets), then stride over the patch bins, form the value
-// Q' * w_p * w_t (optionally fluctuated) and add it into the grid with a fire-and-forget
-// global reduction.  Adjacent lanes take adjacent ticks of a row, so the reductions of a
-// warp land in a few contiguous sectors.
+// Work split.  A block owns 64 consecutive depos.  Threads 0..63 take the FP64 bin decision
+// of one depo each (one thread per depo: FP64 is scarce on this part, so it is never
+// evaluated redundantly by a whole warp) and park it in shared memory.  Each warp then walks
+// 8 of the block's depos: lanes compute the per-bin 1D weights of the patch into shared
+// memory (FP32 erf/erfc of bin-edge offsets) and stride over (row, 4-tick group) items.
+// An item draws one Philox block for its four ticks when fluctuating (four Box-Muller
+// normals), forms Q' w_p w_t per bin and adds the four values into the grid with one
+// vector reduction.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -20,6 +20,7 @@ namespace wcsim {
 namespace {
 
 constexpr int kWarps = 8;       // warps per block
+constexpr int kDepos = 64;      // depos per block
 constexpr int kWmax = 64;       // weights per axis held per patch tile
 
 struct Decision {
@@ -29,6 +30,7 @@ struct Decision {
     float frac_p, frac_t;       // position - floor, FP32
     float sp, st;               // sigma_T [mm], sigma_t [us] (FP32)
     float qatt;                 // Q' = Q exp(-t_d / lifetime)
+    uint32_t id;                // depo id (fluctuation key)
 };
 
 // One axis of the bin decision.  Every operation is an explicitly rounded IEEE operation
@@ -108,81 +110,102 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
-// Standard normal from two 32-bit words (Box & Muller 1958), u = (x + 1/2) 2^-32.
-__device__ __forceinline__ float box_muller(uint32_t x0, uint32_t x1)
+// Four standard normals from one Philox block: two Box-Muller pairs (Box & Muller 1958),
+// u = (x + 1/2) 2^-32; z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1), z2, z3 likewise.
+__device__ __forceinline__ void box_muller4(uint4 x, float z[4])
 {
-    const float u1 = fmaf((float)x0, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float u2 = fmaf((float)x1, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    const float sc = 2.3283064365386963e-10f, off = 1.1641532182693481e-10f;
+    const float u0 = fmaf((float)x.x, sc, off), u1 = fmaf((float)x.y, sc, off);
+    const float u2 = fmaf((float)x.z, sc, off), u3 = fmaf((float)x.w, sc, off);
+    const float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
+    float sa, ca, sb, cb;
+    sincospif(2.0f * u1, &sa, &ca);
+    sincospif(2.0f * u3, &sb, &cb);
+    z[0] = ra * ca;
+    z[1] = ra * sa;
+    z[2] = rb * cb;
+    z[3] = rb * sb;
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
 k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
 {
+    __shared__ Decision s_dec[kDepos];
     __shared__ float s_wp[kWarps][kWmax];
     __shared__ float s_wt[kWarps][kWmax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32;
-    if (base >= d.n) return;
-
-    Decision me;
-    me.ok = 0;
-    uint32_t my_id = 0;
-    if (base + lane < d.n) {
-        me = decide(c, d, base + lane, flags);
-        my_id = d.id[base + lane];
+    const int64_t base = (int64_t)blockIdx.x * kDepos;
+    if (threadIdx.x < kDepos) {
+        Decision r;
+        r.ok = 0;
+        const int64_t i = base + threadIdx.x;
+        if (i < d.n) {
+            r = decide(c, d, i, flags);
+            r.id = d.id[i];
+        }
+        s_dec[threadIdx.x] = r;
     }
-    unsigned todo = __ballot_sync(0xffffffffu, me.ok != 0);
+    __syncthreads();
+    // 16-byte reductions need 4-tick groups to start on 16-byte boundaries
+    const bool vec4 = ((c.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
     float* wp = s_wp[warp];
     float* wt = s_wt[warp];
 
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int32_t r_lo = __shfl_sync(0xffffffffu, me.r_lo, src);
-        const int32_t r_hi = __shfl_sync(0xffffffffu, me.r_hi, src);
-        const int32_t k_lo = __shfl_sync(0xffffffffu, me.k_lo, src);
-        const int32_t k_hi = __shfl_sync(0xffffffffu, me.k_hi, src);
-        const int64_t i0p = __shfl_sync(0xffffffffu, me.i0p, src);
-        const int64_t i0t = __shfl_sync(0xffffffffu, me.i0t, src);
-        const float frac_p = __shfl_sync(0xffffffffu, me.frac_p, src);
-        const float frac_t = __shfl_sync(0xffffffffu, me.frac_t, src);
-        const float sp = __shfl_sync(0xffffffffu, me.sp, src);
-        const float st = __shfl_sync(0xffffffffu, me.st, src);
-        const float qatt = __shfl_sync(0xffffffffu, me.qatt, src);
-        const uint32_t id = __shfl_sync(0xffffffffu, my_id, src);
-        if (!(qatt > 0.0f)) continue;      // Q' underflowed: nothing to add
+    for (int i = warp; i < kDepos; i += kWarps) {
+        const Decision dd = s_dec[i];
+        if (!dd.ok || !(dd.qatt > 0.0f)) continue;    // nothing, or Q' underflowed
         // u = offset_in_bins * bin / (sqrt(2) sigma); sigma == 0 puts all weight in the
         // single bin of the window.
-        const float s_p = (sp > 0.0f) ? c.dp_f / (1.41421356237309505f * sp) : 0.0f;
-        const float s_t = (st > 0.0f) ? c.dt_f / (1.41421356237309505f * st) : 0.0f;
+        const float s_p = (dd.sp > 0.0f) ? c.dp_f / (1.41421356237309505f * dd.sp) : 0.0f;
+        const float s_t = (dd.st > 0.0f) ? c.dt_f / (1.41421356237309505f * dd.st) : 0.0f;
+        const float inv_q = 1.0f / dd.qatt;
 
-        for (int32_t r0 = r_lo; r0 <= r_hi; r0 += kWmax) {
-            const int nr = min(kWmax, r_hi - r0 + 1);
-            for (int32_t k0 = k_lo; k0 <= k_hi; k0 += kWmax) {
-                const int nt = min(kWmax, k_hi - k0 + 1);
+        for (int32_t r0 = dd.r_lo; r0 <= dd.r_hi; r0 += kWmax) {
+            const int nr = min(kWmax, dd.r_hi - r0 + 1);
+            for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kWmax) {
+                const int nt = min(kWmax, dd.k_hi - k0 + 1);
                 for (int e = lane; e < nr; e += 32)
-                    wp[e] = qatt * ((sp > 0.0f) ? bin_weight((int64_t)(r0 + e) - i0p, frac_p, s_p)
-                                                : 1.0f);
+                    wp[e] = dd.qatt * ((dd.sp > 0.0f) ? bin_weight((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p) : 1.0f);
                 for (int e = lane; e < nt; e += 32)
-                    wt[e] = (st > 0.0f) ? bin_weight((int64_t)(k0 + e) - i0t, frac_t, s_t) : 1.0f;
+                    wt[e] = (dd.st > 0.0f) ? bin_weight((int64_t)(k0 + e) - dd.i0t, dd.frac_t, s_t) : 1.0f;
                 __syncwarp();
-                const float inv_nt = 1.0f / (float)nt;
-                for (int b = lane; b < nr * nt; b += 32) {
-                    const int ir = (int)(((float)b + 0.5f) * inv_nt);
-                    const int ik = b - ir * nt;
+                const int q_lo = k0 >> 2, q_hi = (k0 + nt - 1) >> 2;
+                const int nq = q_hi - q_lo + 1;
+                const float inv_nq = 1.0f / (float)nq;
+                for (int item = lane; item < nr * nq; item += 32) {
+                    const int ir = (int)(((float)item + 0.5f) * inv_nq);
+                    const int iq = item - ir * nq;
                     const int64_t r = r0 + ir;
-                    const int32_t k = k0 + ik;
-                    float val = wp[ir] * wt[ik];
-                    if (c.fluctuate) {
-                        // normal approximation to Binomial(Q', mean / Q')
-                        const uint4 x = philox(make_uint4((uint32_t)k, (uint32_t)r, id, c.plane_id),
-                                               c.key0, c.key1);
-                        const float z = box_muller(x.x, x.y);
-                        const float var = fmaxf(0.0f, val * (1.0f - val / qatt));
-                        val = fmaxf(0.0f, val + sqrtf(var) * z);
+                    const int kq = (q_lo + iq) * 4;
+                    const float w = wp[ir];
+                    float v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int ik = kq + e - k0;
+                        v[e] = (ik >= 0 && ik < nt) ? w * wt[ik] : 0.0f;
                     }
-                    atomicAdd(grid + r * c.n_ticks + k, val);
+                    if (c.fluctuate) {
+                        // normal approximation to Binomial(Q', mean / Q'); zero-mean bins
+                        // (outside the window) stay zero
+                        float z[4];
+                        box_muller4(philox(make_uint4((uint32_t)(q_lo + iq), (uint32_t)r, dd.id,
+                                                      c.plane_id), c.key0, c.key1), z);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float var = fmaxf(0.0f, v[e] * (1.0f - v[e] * inv_q));
+                            v[e] = fmaxf(0.0f, v[e] + sqrtf(var) * z[e]);
+                        }
+                    }
+                    float* dst = grid + r * c.n_ticks + kq;
+                    if (vec4) {
+                        atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int ik = kq + e - k0;
+                            if (ik >= 0 && ik < nt) atomicAdd(dst + e, v[e]);
+                        }
+                    }
                 }
                 __syncwarp();
             }
@@ -205,8 +228,7 @@ cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* 
                              int* flags, cudaStream_t s)
 {
     if (d.n <= 0) return cudaSuccess;
-    const int64_t per_block = kWarps * 32;
-    const int64_t blocks = (d.n + per_block - 1) / per_block;
+    const int64_t blocks = (d.n + kDepos - 1) / kDepos;
     k_rasterize<<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, grid, flags);
     return cudaGetLastError();
 }

@@ -40,12 +40,12 @@ cudaError_t launch_windows(const RasterConsts& c, const DepoArrays& d, int32_t* 
 
 // ------------------------------------------------------------------ FFT
 constexpr int kMaxPasses = 16;
-constexpr int kMaxFftN = 14000;       // time axis: 2 x N x 8 B of shared memory per CTA
+constexpr int kMaxFftN = 13500;       // time axis: two padded N-point buffers per CTA
 constexpr int kMaxWireN = 8192;
 
 // Mixed-radix Stockham plan for one length N = prod(radix[p]).  Pass p combines groups
-// of Ns[p] already-transformed points; tw_off[p] indexes (radix-1) * Ns twiddles in the
-// plan's table; ns_magic[p] = ceil(2^32 / Ns[p]) turns j / Ns into a multiply-high.
+// of ns[p] already-transformed points; tw_off[p] indexes (radix-1) * ns twiddles in the
+// plan's table; ns_magic[p] = ceil(2^32 / ns[p]) turns j / ns into a multiply-high.
 struct FftPlan {
     int32_t n;
     int32_t npass;
@@ -53,11 +53,11 @@ struct FftPlan {
     int32_t ns[kMaxPasses];
     int32_t tw_off[kMaxPasses];
     uint32_t ns_magic[kMaxPasses];
-    uint32_t nb_magic[kMaxPasses];    // ceil(2^32 / (n / radix))
     const float2* tw;                 // device table, forward sign (exp(-i ...))
 };
 
-// Factor n into supported radices (16, 8, 4, 2, 5, 3, 7); false if impossible.
+// Factor n into register-DFT radices (<= 25, primes 2, 3, 5, 7) with the fewest passes;
+// false if impossible.
 bool fft_factor(int n, int32_t* radix, int32_t* npass);
 // Build the plan and upload its twiddle table (FP64 host values rounded to FP32).
 cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw);

@@ -155,7 +155,7 @@ CONV_CASES = [
     (5, 1, 49, 5, 49, True),          # odd length 7^2
     (33, 4, 96, 35, 98, False),
     (1, 1, 64, 1, 64, True),          # single wire, single impact
-    (3, 2, 14000, 3, 14000, True),    # longest supported time axis
+    (3, 2, 13500, 3, 13500, True),    # longest supported time axis
     (960, 10, 16, 960, 16, True),     # many wires, short time axis
 ]
 

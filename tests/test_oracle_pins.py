@@ -284,13 +284,22 @@ np.save(sys.argv[2], np.stack([ctr.reshape(-1), out.numpy().view(np.uint32)]))
 
 
 def test_box_muller_normal_distribution():
-    """z from Philox words is standard normal (KS test) and uses both words."""
+    """Every member of the four normals per Philox block is standard normal (KS test),
+    and members are uncorrelated."""
     from scipy import stats
-    zs = np.array([O.normal_from_words(*O.philox4x32_10((i, 7, 9, 1), (1, 2))[:2])
-                   for i in range(20000)])
-    assert stats.kstest(zs, "norm").pvalue > 1e-3
-    assert abs(zs.mean()) < 4 / math.sqrt(len(zs))
-    assert abs(zs.var() - 1) < 4 * math.sqrt(2 / len(zs))
+    zs = np.array([[O.bin_normal(3, 4 * i + m, 11, 2, 0x5EED0001) for m in range(4)]
+                   for i in range(6000)])
+    for m in range(4):
+        z = zs[:, m]
+        assert stats.kstest(z, "norm").pvalue > 1e-3, m
+        assert abs(z.mean()) < 4 / math.sqrt(len(z))
+        assert abs(z.var() - 1) < 4 * math.sqrt(2 / len(z))
+    c = np.corrcoef(zs.T)
+    assert np.abs(c - np.eye(4)).max() < 4 / math.sqrt(len(zs))
+    # the block's words feed the members: (x0, x1) -> z0, z1 and (x2, x3) -> z2, z3
+    x = O.philox4x32_10((5, 3, 11, 2), (0x5EED0001, 0))
+    assert O.bin_normal(3, 21, 11, 2, 0x5EED0001) == O.normal_from_words(x[0], x[1], 1)
+    assert O.bin_normal(3, 22, 11, 2, 0x5EED0001) == O.normal_from_words(x[2], x[3], 0)
     # u2 -> cos(2 pi u2): quarter-turn values
     assert O.normal_from_words(2**31, 0) == pytest.approx(math.sqrt(-2 * math.log((2**31 + .5) / 2**32)), rel=1e-12)
     assert O.normal_from_words(2**31, 2**31) == pytest.approx(-math.sqrt(-2 * math.log((2**31 + .5) / 2**32)), rel=1e-9)
