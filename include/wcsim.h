@@ -126,8 +126,10 @@ wcsim_status wcsim_windows(wcsim_plane* plane, const wcsim_depos* depos, int32_t
                            void* stream);
 
 /* Wait for the plane's work on `stream`, then read and clear its device flags.
- * *flags (may be NULL) receives the bit set (bit 0: invalid depo values seen).
- * Returns WCSIM_EDEVICE_CHECK if any flag was set, WCSIM_OK otherwise. */
+ * *flags (may be NULL) receives the bit set (bit 0: invalid depo values seen; bit 1: a
+ * kernel's bounded wait for an asynchronous copy gave up, so its output is incomplete).
+ * Returns WCSIM_ETIMEOUT if bit 1 is set, else WCSIM_EDEVICE_CHECK if bit 0 is set, else
+ * WCSIM_OK. */
 wcsim_status wcsim_plane_check(wcsim_plane* plane, void* stream, int32_t* flags);
 
 /* Per-stage device time of the last compute call on this plane (CUDA events), when

@@ -5,10 +5,12 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
 
+#include "async_copy.cuh"
 #include "wcsim_internal.cuh"
 
 using namespace wcsim;
@@ -62,10 +64,11 @@ struct wcsim_plane {
     FftPlan pt, pw;
     float2* tw_t = nullptr;
     float2* tw_w = nullptr;
-    float2* H = nullptr;        // [n_imp][n_fw][nh], Hermitian part of R / (n_fw n_ft)
+    float2* tw_warp = nullptr;  // twiddles of the one-warp-per-column wire pass (or NULL)
+    float2* H = nullptr;        // Hermitian part of R / (n_fw n_ft), blocked [n_imp][nkb][n_fw][4]
     float* grid = nullptr;      // [n_rows][n_ticks]
-    float2* shat = nullptr;     // [n_imp][n_wires][nh]
-    float2* mt = nullptr;       // [n_wires][nh]
+    float2* shat = nullptr;     // time-axis spectra, blocked [n_imp][nkb][n_wires][4]
+    float2* mt = nullptr;       // wire-summed spectra, blocked [nkb][n_wires][4]
     int* flags = nullptr;       // device flag word
     int device = 0;
     bool timing = false;
@@ -162,6 +165,7 @@ void plane_free(wcsim_plane* pl)
     if (!pl) return;
     cudaFree(pl->tw_t);
     cudaFree(pl->tw_w);
+    cudaFree(pl->tw_warp);
     cudaFree(pl->H);
     cudaFree(pl->grid);
     cudaFree(pl->shat);
@@ -181,10 +185,14 @@ wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaSt
                          int first_mark)
 {
     cudaError_t e;
-    if ((e = launch_rows_r2c(pl->dims, pl->pt, grid, pl->shat, s))) return cuda_fail(e, "rows_r2c launch");
+    if ((e = launch_rows_r2c(pl->dims, pl->pt, grid, pl->shat, pl->flags, s)))
+        return cuda_fail(e, "rows_r2c launch");
     mark(pl, first_mark, s);
-    if ((e = launch_wire_pass(pl->dims, pl->pw, pl->shat, pl->H, pl->mt, s)))
-        return cuda_fail(e, "wire_pass launch");
+    if (pl->tw_warp)
+        e = launch_wire_warp(pl->dims, pl->tw_warp, pl->shat, pl->H, pl->mt, s);
+    else
+        e = launch_wire_pass(pl->dims, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s);
+    if (e) return cuda_fail(e, "wire_pass launch");
     mark(pl, first_mark + 1, s);
     if ((e = launch_rows_c2r(pl->dims, pl->pt, pl->mt, wave, s))) return cuda_fail(e, "rows_c2r launch");
     mark(pl, first_mark + 2, s);
@@ -234,6 +242,10 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     d.n_fw = n_fw;
     d.n_ft = n_ft;
     d.nh = n_ft / 2 + 1;
+    d.nkb = (d.nh + kBlockCols - 1) / kBlockCols;
+    // Kernel variant of the time-axis forward FFT; WCSIM_ROWS_KERNEL=staged|direct overrides.
+    d.rows_variant = 0;
+    if (const char* v = getenv("WCSIM_ROWS_KERNEL")) d.rows_variant = (strcmp(v, "staged") == 0) ? 1 : 0;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n_rows = (size_t)d.n_w * d.n_imp;
 #define WC_TRY(call, what)                                  \
@@ -246,10 +258,18 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     } while (0)
     WC_TRY(fft_plan_create(n_ft, &pl->pt, &pl->tw_t), "time-axis FFT plan");
     WC_TRY(fft_plan_create(n_fw, &pl->pw, &pl->tw_w), "wire-axis FFT plan");
-    WC_TRY(cudaMalloc(&pl->H, (size_t)d.n_imp * d.n_fw * d.nh * sizeof(float2)), "response allocation");
+    // Wire-axis kernel; WCSIM_WIRE_KERNEL=block forces the block-level engine.
+    {
+        const char* v = getenv("WCSIM_WIRE_KERNEL");
+        const bool block = v && strcmp(v, "block") == 0;
+        if (!block && wire_warp_supported(n_fw) && geom->n_wires <= n_fw)
+            WC_TRY(wire_warp_twiddles(n_fw, &pl->tw_warp), "wire-axis twiddles");
+    }
+    const size_t cols = (size_t)d.nkb * kBlockCols;
+    WC_TRY(cudaMalloc(&pl->H, (size_t)d.n_imp * d.n_fw * cols * sizeof(float2)), "response allocation");
     WC_TRY(cudaMalloc(&pl->grid, n_rows * d.n_t * sizeof(float)), "grid allocation");
-    WC_TRY(cudaMalloc(&pl->shat, n_rows * d.nh * sizeof(float2)), "spectrum allocation");
-    WC_TRY(cudaMalloc(&pl->mt, (size_t)d.n_w * d.nh * sizeof(float2)), "spectrum allocation");
+    WC_TRY(cudaMalloc(&pl->shat, n_rows * cols * sizeof(float2)), "spectrum allocation");
+    WC_TRY(cudaMalloc(&pl->mt, (size_t)d.n_w * cols * sizeof(float2)), "spectrum allocation");
     WC_TRY(cudaMalloc(&pl->flags, sizeof(int)), "flag allocation");
     WC_TRY(cudaMemsetAsync(pl->flags, 0, sizeof(int), s), "flag reset");
     WC_TRY(launch_make_hermitian(d, (const float2*)resp_c64, pl->H,
@@ -361,6 +381,8 @@ wcsim_status wcsim_plane_check(wcsim_plane* pl, void* stream, int32_t* flags)
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "flag read");
     if (flags) *flags = h;
+    if (h & kErrTimeout)
+        return fail(WCSIM_ETIMEOUT, "a device-side wait for an asynchronous copy gave up (flags 0x%x)", h);
     if (h) return fail(WCSIM_EDEVICE_CHECK, "device flagged invalid depo values (flags 0x%x)", h);
     return WCSIM_OK;
 }

@@ -265,9 +265,9 @@ __device__ __forceinline__ void pass_r(const Ld& ld, const St& st, const PassArg
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = ld(c, j + r * nb);
         if (k > 0) {
-            const float2* t = a.tw + k * (R - 1);
+            const float2* t = a.tw + k;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], __ldg(t + r - 1));
+            for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], __ldg(t + (r - 1) * a.ns));
         }
         dft<R, INV>(v);
         const int o = q * a.ns * R + k;

@@ -65,6 +65,22 @@ bool fft_factor(int n, int32_t* radix, int32_t* npass)
     for (int i = 0; i < best_len; ++i)
         for (int k = i + 1; k < best_len; ++k)
             if (best[k] > best[i]) { int t = best[i]; best[i] = best[k]; best[k] = t; }
+    // A radix-16 first pass writes with stride 16, which the one-slot-per-16 padding of
+    // the shared buffers spreads over all banks; other even first radices (12, 20, 24)
+    // collide 2-8 ways.  Take 16 first whenever that costs no extra pass.
+    if (n % 16 == 0 && n > 16) {
+        int rest[kMaxPasses], rest_len = -1;
+        double rest_cost = 0.0;
+        search(n / 16, 0, cur, 0.0, rest, &rest_len, &rest_cost);
+        if (rest_len >= 0 && rest_len + 1 <= best_len) {
+            for (int i = 0; i < rest_len; ++i)
+                for (int k = i + 1; k < rest_len; ++k)
+                    if (rest[k] > rest[i]) { int t = rest[i]; rest[i] = rest[k]; rest[k] = t; }
+            best[0] = 16;
+            for (int i = 0; i < rest_len; ++i) best[i + 1] = rest[i];
+            best_len = rest_len + 1;
+        }
+    }
     for (int i = 0; i < best_len; ++i) radix[i] = best[i];
     *npass = best_len;
     return true;
@@ -82,9 +98,10 @@ cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw)
         p.ns[i] = ns;
         p.tw_off[i] = (int32_t)tw.size();
         p.ns_magic[i] = magic_for(ns);
-        // twiddle (k, r) = exp(-2 pi i r k / (ns R)), stored at k (R - 1) + r - 1
-        for (int k = 0; k < ns; ++k)
-            for (int r = 1; r < R; ++r) {
+        // twiddle (k, r) = exp(-2 pi i r k / (ns R)), stored at (r - 1) ns + k so that the
+        // lanes of a warp (consecutive k) read consecutive entries
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < ns; ++k) {
                 const double a = -2.0 * M_PI * (double)r * (double)k / ((double)ns * R);
                 tw.push_back(make_float2((float)cos(a), (float)sin(a)));
             }

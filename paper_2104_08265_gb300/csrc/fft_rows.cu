@@ -1,18 +1,26 @@
 // Time-axis transforms of Eq. 2: forward real-to-complex FFT of every grid row and inverse
 // complex-to-real FFT of every wire's spectrum.  Two real rows ride in one complex FFT
 // (z = x0 + i x1); their spectra are separated with X0 = (Z[k] + conj Z[-k]) / 2,
-// X1 = (Z[k] - conj Z[-k]) / 2i.  One CTA per pair of rows, two padded N-point buffers in
-// shared memory, the first pass reads global memory directly.
+// X1 = (Z[k] - conj Z[-k]) / 2i.
+//
+// rows_r2c (staged) is persistent: one CTA per SM walks pairs of rows; the two rows of a
+// pair are adjacent in the grid, so one bulk copy brings both into a two-stage shared
+// buffer while the previous pair is transformed.  Planes whose rows are not a multiple of
+// 16 bytes, or too long for the staging buffers, use the direct kernel, whose first pass
+// reads global memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "async_copy.cuh"
 #include "fft_engine.cuh"
 #include "wcsim_internal.cuh"
 
 namespace wcsim {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kStagedThreads = 512;
+constexpr int kDirectThreads = 256;
+constexpr size_t kMaxSmem = 227 * 1024;
 
 // First-pass source: element i of z = x0 + i x1 (zero beyond the frame).
 struct RealPairLd {
@@ -26,65 +34,146 @@ struct RealPairLd {
     }
 };
 
-// First-pass source of the inverse: z[i] = X0[i] + i X1[i], both Hermitian, from the
-// stored half spectra m0, m1 (k < nh), conj(m[N - k]) above.
+// Same, from a staged pair (row 0 then row 1) in shared memory.
+struct StagedPairLd {
+    const float* t;
+    int n_t;
+    bool has1;
+    __device__ __forceinline__ float2 operator()(int, int i) const
+    {
+        if (i >= n_t) return make_float2(0.f, 0.f);
+        return make_float2(t[i], has1 ? t[n_t + i] : 0.f);
+    }
+};
+
+// First-pass source of the inverse: z[k] = X0[k] + i X1[k], both Hermitian, from the
+// blocked half spectra of wires w0, w1 (k < nh), conj(X[N - k]) above.
 struct HermPairLd {
-    const float2* m0;
-    const float2* m1;     // nullptr: second wire absent
-    int nh, n;
+    const float2* mt;     // blocked [nkb][n_w][4]
+    int w0, w1, n_w, nh, n;
+    bool has1;
     __device__ __forceinline__ float2 operator()(int, int k) const
     {
-        float2 a, b = make_float2(0.f, 0.f);
-        if (k < nh) {
-            a = __ldg(m0 + k);
-            if (m1) b = __ldg(m1 + k);
-        } else {
-            const float2 ac = __ldg(m0 + (n - k));
-            a = make_float2(ac.x, -ac.y);
-            if (m1) {
-                const float2 bc = __ldg(m1 + (n - k));
-                b = make_float2(bc.x, -bc.y);
-            }
+        const bool lo = k < nh;
+        const int kk = lo ? k : n - k;
+        float2 a = __ldg(mt + blk_index(kk, w0, n_w));
+        float2 b = has1 ? __ldg(mt + blk_index(kk, w1, n_w)) : make_float2(0.f, 0.f);
+        if (!lo) {
+            a.y = -a.y;
+            b.y = -b.y;
         }
         return make_float2(a.x - b.y, a.y + b.x);
     }
 };
 
-__global__ void __launch_bounds__(kThreads, 2)
-k_rows_r2c(ConvDims d, FftPlan p, const float* __restrict__ grid, float2* __restrict__ shat)
+// Separate the two real rows' half spectra and store them in the blocked layout (zeros in
+// the padding columns nh .. 4 nkb - 1).
+__device__ __forceinline__ void store_pair_spectra(const ConvDims& d, const float2* z, int N,
+                                                   int64_t r0, bool has1, float2* shat)
 {
-    extern __shared__ float2 sm[];
-    const int N = p.n;
-    float2* X = sm;
-    float2* Y = sm + padded_len(N);
-    const int64_t n_rows = (int64_t)d.n_w * d.n_imp;
-    const int64_t r0 = 2 * (int64_t)blockIdx.x, r1 = r0 + 1;
-    const bool has1 = r1 < n_rows;
-    const RealPairLd src{grid + r0 * d.n_t, has1 ? grid + r1 * d.n_t : nullptr, d.n_t};
-    const float2* z = run_plan<false, 0>(p, src, X, Y);
     const int w0 = (int)(r0 / d.n_imp), j0 = (int)(r0 % d.n_imp);
+    const int64_t r1 = r0 + 1;
     const int w1 = (int)(r1 / d.n_imp), j1 = (int)(r1 % d.n_imp);
-    float2* o0 = shat + ((int64_t)j0 * d.n_w + w0) * d.nh;
-    float2* o1 = shat + ((int64_t)j1 * d.n_w + w1) * d.nh;
-    for (int k = threadIdx.x; k < d.nh; k += blockDim.x) {
-        const float2 a = z[pad16(k)];
-        const float2 b = z[pad16(k == 0 ? 0 : N - k)];
-        o0[k] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-        if (has1) o1[k] = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+    float2* o0 = shat + (int64_t)j0 * d.nkb * d.n_w * kBlockCols;
+    float2* o1 = shat + (int64_t)j1 * d.nkb * d.n_w * kBlockCols;
+    for (int k = threadIdx.x; k < d.nkb * kBlockCols; k += blockDim.x) {
+        float2 x0 = make_float2(0.f, 0.f), x1 = x0;
+        if (k < d.nh) {
+            const float2 a = z[pad16(k)];
+            const float2 b = z[pad16(k == 0 ? 0 : N - k)];
+            x0 = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+            x1 = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+        }
+        o0[blk_index(k, w0, d.n_w)] = x0;
+        if (has1) o1[blk_index(k, w1, d.n_w)] = x1;
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__host__ __device__ inline size_t staged_smem(int n_t, int n)
+{
+    return 2 * 2 * (size_t)n_t * sizeof(float) + 2 * (size_t)padded_len(n) * sizeof(float2) +
+           2 * sizeof(uint64_t);
+}
+
+__global__ void __launch_bounds__(kStagedThreads, 1)
+k_rows_r2c_staged(ConvDims d, FftPlan p, const float* __restrict__ grid, float2* __restrict__ shat,
+                  int* flags)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int N = p.n;
+    float* st = reinterpret_cast<float*>(smraw);           // stage s at st + s * 2 n_t
+    float2* X = reinterpret_cast<float2*>(st + 4 * d.n_t);
+    float2* Y = X + padded_len(N);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Y + padded_len(N));
+    const int64_t n_rows = (int64_t)d.n_w * d.n_imp;
+    const int64_t n_pairs = (n_rows + 1) / 2;
+    const int n_items = (n_pairs > (int64_t)blockIdx.x)
+                            ? (int)((n_pairs - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    const int tid = threadIdx.x;
+
+    auto issue = [&](int i) {
+        const int64_t r0 = 2 * ((int64_t)blockIdx.x + (int64_t)i * gridDim.x);
+        const uint32_t bytes = (uint32_t)((r0 + 1 < n_rows ? 2 : 1) * d.n_t * sizeof(float));
+        mbar_arrive_expect_tx(&bar[i & 1], bytes);
+        bulk_g2s(st + (i & 1) * 2 * d.n_t, grid + r0 * d.n_t, bytes, &bar[i & 1]);
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (n_items > 0) issue(0);
+        if (n_items > 1) issue(1);
+    }
+    int i = 0;
+    for (; i < n_items; ++i) {
+        const int s = i & 1;
+        const int64_t r0 = 2 * ((int64_t)blockIdx.x + (int64_t)i * gridDim.x);
+        const bool has1 = r0 + 1 < n_rows;
+        const bool landed = mbar_wait(&bar[s], (i >> 1) & 1);
+        if (!__syncthreads_and(landed)) break;
+        const float2* z = run_plan<false, 0>(p, StagedPairLd{st + s * 2 * d.n_t, d.n_t, has1}, X, Y);
+        if (tid == 0 && i + 2 < n_items) {     // stage s was read by the first pass only
+            fence_proxy_async_smem();
+            issue(i + 2);
+        }
+        store_pair_spectra(d, z, N, r0, has1, shat);
+        __syncthreads();
+    }
+    if (i < n_items && tid == 0) {
+        atomicOr(flags, kErrTimeout);
+        for (int k = i; k < n_items && k < i + 2; ++k) mbar_wait(&bar[k & 1], (k >> 1) & 1);
+    }
+}
+
+__global__ void __launch_bounds__(kDirectThreads, 2)
+k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2* __restrict__ shat)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int N = p.n;
+    float2* X = reinterpret_cast<float2*>(smraw);
+    float2* Y = X + padded_len(N);
+    const int64_t n_rows = (int64_t)d.n_w * d.n_imp;
+    const int64_t r0 = 2 * (int64_t)blockIdx.x;
+    const bool has1 = r0 + 1 < n_rows;
+    const RealPairLd src{grid + r0 * d.n_t, has1 ? grid + (r0 + 1) * d.n_t : nullptr, d.n_t};
+    const float2* z = run_plan<false, 0>(p, src, X, Y);
+    store_pair_spectra(d, z, N, r0, has1, shat);
+}
+
+__global__ void __launch_bounds__(kDirectThreads, 2)
 k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, float* __restrict__ wave)
 {
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     const int N = p.n;
-    float2* X = sm;
-    float2* Y = sm + padded_len(N);
+    float2* X = reinterpret_cast<float2*>(smraw);
+    float2* Y = X + padded_len(N);
     const int w0 = 2 * blockIdx.x, w1 = w0 + 1;
     const bool has1 = w1 < d.n_w;
-    const HermPairLd src{mt + (int64_t)w0 * d.nh, has1 ? mt + (int64_t)w1 * d.nh : nullptr,
-                         d.nh, N};
+    const HermPairLd src{mt, w0, has1 ? w1 : w0, d.n_w, d.nh, N, has1};
     const float2* z = run_plan<true, 0>(p, src, X, Y);
     float* o0 = wave + (int64_t)w0 * d.n_t;
     float* o1 = wave + (int64_t)w1 * d.n_t;
@@ -95,14 +184,15 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, float* __restri
     }
 }
 
-size_t rows_smem(int n) { return 2 * (size_t)padded_len(n) * sizeof(float2); }
+size_t direct_smem(int n) { return 2 * (size_t)padded_len(n) * sizeof(float2); }
 
 bool g_attr = false;
 cudaError_t attrs()
 {
     if (g_attr) return cudaSuccess;
-    const int mx = 227 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_rows_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    const int mx = (int)kMaxSmem;
+    cudaError_t e = cudaFuncSetAttribute(k_rows_r2c_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rows_r2c_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (!e) e = cudaFuncSetAttribute(k_rows_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (!e) g_attr = true;
     return e;
@@ -111,12 +201,20 @@ cudaError_t attrs()
 }  // namespace
 
 cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* grid,
-                            float2* shat, cudaStream_t s)
+                            float2* shat, int* flags, cudaStream_t s)
 {
     cudaError_t e = attrs();
     if (e) return e;
     const int64_t n_rows = (int64_t)d.n_w * d.n_imp;
-    k_rows_r2c<<<(unsigned)((n_rows + 1) / 2), kThreads, rows_smem(pt.n), s>>>(d, pt, grid, shat);
+    const int64_t n_pairs = (n_rows + 1) / 2;
+    const size_t smem = staged_smem(d.n_t, pt.n);
+    const bool aligned = (d.n_t % 4 == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
+    if (d.rows_variant == 1 && aligned && smem <= kMaxSmem) {
+        const int grid_n = n_pairs < sm_count() ? (int)n_pairs : sm_count();
+        k_rows_r2c_staged<<<grid_n, kStagedThreads, smem, s>>>(d, pt, grid, shat, flags);
+    } else {
+        k_rows_r2c_direct<<<(unsigned)n_pairs, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, grid, shat);
+    }
     return cudaGetLastError();
 }
 
@@ -125,7 +223,7 @@ cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* 
 {
     cudaError_t e = attrs();
     if (e) return e;
-    k_rows_c2r<<<(unsigned)((d.n_w + 1) / 2), kThreads, rows_smem(pt.n), s>>>(d, pt, mt, wave);
+    k_rows_c2r<<<(unsigned)((d.n_w + 1) / 2), kDirectThreads, direct_smem(pt.n), s>>>(d, pt, mt, wave);
     return cudaGetLastError();
 }
 

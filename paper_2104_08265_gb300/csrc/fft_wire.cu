@@ -1,129 +1,260 @@
 // Wire-axis part of Eq. 2 and the response preparation.
 //
-// wire_pass: a CTA owns B = 2^LOGB adjacent time frequencies.  For each impact position j
-// it transforms the B columns Shat_j[.][kt] along the wire axis (first pass straight from
-// global memory), multiplies them by H_j and accumulates over j in shared memory; the sum is
-// transformed back along the wire axis and written as Mt[w][kt].
+// wire_pass is persistent: one CTA per SM walks work items (block kb of 4 time
+// frequencies, impact position j).  For each item it bulk-copies the contiguous tiles
+// Shat_j(kb) and H_j(kb) into a two-stage shared buffer (the copy of item i + 1 runs while
+// item i is transformed), transforms the 4 columns along the wire axis, multiplies by H_j
+// and accumulates over j in shared memory; after the last j of a block it transforms the
+// sum back along the wire axis and writes the block of Mt.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "async_copy.cuh"
 #include "fft_engine.cuh"
 #include "wcsim_internal.cuh"
 
 namespace wcsim {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+constexpr int LOGB = 2;                 // 4 columns per block (kBlockCols)
 
-// First-pass source: column kt0 + c of Shat_j, zero beyond the frame's wires or the
-// half spectrum.
-struct TileLd {
-    const float2* src;    // Shat_j, [n_w][nh]
-    int nh, kt0, n_w;
+// First-pass source: dense staged tile [w][4], zero for padded wires w >= n_w.
+struct StagedTileLd {
+    const float2* t;
+    int n_w;
     __device__ __forceinline__ float2 operator()(int c, int w) const
     {
-        const int kt = kt0 + c;
-        return (w < n_w && kt < nh) ? __ldg(src + (int64_t)w * nh + kt) : make_float2(0.f, 0.f);
+        return (w < n_w) ? t[(w << LOGB) + c] : make_float2(0.f, 0.f);
     }
 };
 
-template <int LOGB>
-__global__ void __launch_bounds__(kThreads, 2)
-k_wire_pass(ConvDims d, FftPlan p, const float2* __restrict__ shat, const float2* __restrict__ H,
-            float2* __restrict__ mt)
+// Stage s holds the Shat tile at st + s * stage and the H tile right after it.
+struct WireSmem {
+    float2* st;
+    int stage;
+    float2 *X, *Y, *acc;
+    uint64_t* bar;
+    __device__ __forceinline__ float2* st_s(int s) const { return st + s * stage; }
+    __device__ __forceinline__ float2* st_h(int s, int n_w) const { return st + s * stage + n_w * kBlockCols; }
+};
+
+__host__ __device__ inline size_t wire_smem_bytes(int n_w, int n_fw)
 {
-    constexpr int B = 1 << LOGB;
-    extern __shared__ float2 sm[];
-    const int N = p.n;          // n_fw
-    const int plen = padded_len(N) << LOGB;
-    float2* X = sm;
-    float2* Y = sm + plen;
-    float2* acc = sm + 2 * plen;
-    const int kt0 = blockIdx.x * B;
+    const size_t tile = (size_t)(n_w + n_fw) * kBlockCols * sizeof(float2);
+    const size_t buf = (size_t)padded_len(n_fw) * kBlockCols * sizeof(float2);
+    return 2 * tile + 3 * buf + 2 * sizeof(uint64_t);
+}
+
+__device__ inline WireSmem carve(unsigned char* base, int n_w, int n_fw)
+{
+    WireSmem m;
+    float2* p = reinterpret_cast<float2*>(base);
+    const int pl = padded_len(n_fw) * kBlockCols;
+    m.st = p;
+    m.stage = (n_w + n_fw) * kBlockCols;
+    p += 2 * m.stage;
+    m.X = p; p += pl;
+    m.Y = p; p += pl;
+    m.acc = p; p += pl;
+    m.bar = reinterpret_cast<uint64_t*>(p);
+    return m;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_wire_pass(ConvDims d, FftPlan p, const float2* __restrict__ shat, const float2* __restrict__ H,
+            float2* __restrict__ mt, int* flags)
+{
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int N = p.n;
+    WireSmem sm = carve(smraw, d.n_w, N);
+    const int tid = threadIdx.x;
+    const int my_blocks = (d.nkb > (int)blockIdx.x) ? (d.nkb - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int n_items = my_blocks * d.n_imp;
+    const uint32_t bytes_s = (uint32_t)(d.n_w * kBlockCols * sizeof(float2));
+    const uint32_t bytes_h = (uint32_t)(N * kBlockCols * sizeof(float2));
+
+    auto issue = [&](int i) {           // thread 0: start the copies of item i
+        const int kb = blockIdx.x + (i / d.n_imp) * gridDim.x, j = i % d.n_imp, s = i & 1;
+        const int64_t blk = (int64_t)j * d.nkb + kb;
+        mbar_arrive_expect_tx(&sm.bar[s], bytes_s + bytes_h);
+        bulk_g2s(sm.st_s(s), shat + blk * d.n_w * kBlockCols, bytes_s, &sm.bar[s]);
+        bulk_g2s(sm.st_h(s, d.n_w), H + blk * N * kBlockCols, bytes_h, &sm.bar[s]);
+    };
+
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    const int plen = padded_len(N) * kBlockCols;
+    for (int e = tid; e < plen; e += blockDim.x) sm.acc[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (tid == 0) {
+        if (n_items > 0) issue(0);
+        if (n_items > 1) issue(1);
+    }
+
+    int i = 0;
+    for (; i < n_items; ++i) {
+        const int s = i & 1, j = i % d.n_imp;
+        const int kb = blockIdx.x + (i / d.n_imp) * gridDim.x;
+        const bool landed = mbar_wait(&sm.bar[s], (i >> 1) & 1);
+        if (!__syncthreads_and(landed)) break;
+        const float2* z = run_plan<false, LOGB>(p, StagedTileLd{sm.st_s(s), d.n_w}, sm.X, sm.Y);
+        const float2* h = sm.st_h(s, d.n_w);
+        for (int e = tid; e < N * kBlockCols; e += blockDim.x) {
+            const int idx = (pad16(e >> LOGB) << LOGB) + (e & (kBlockCols - 1));
+            const float2 hv = h[e], v = z[idx];
+            float2 a = sm.acc[idx];
+            a.x += hv.x * v.x - hv.y * v.y;
+            a.y += hv.x * v.y + hv.y * v.x;
+            sm.acc[idx] = a;
+        }
+        __syncthreads();                         // stage s is free again
+        if (tid == 0 && i + 2 < n_items) {
+            fence_proxy_async_smem();
+            issue(i + 2);
+        }
+        if (j == d.n_imp - 1) {
+            const float2* m = run_plan<true, LOGB>(p, SmemLd<LOGB>{sm.acc}, sm.X, sm.Y);
+            float2* out = mt + (int64_t)kb * d.n_w * kBlockCols;
+            for (int e = tid; e < d.n_w * kBlockCols; e += blockDim.x)
+                out[e] = m[(pad16(e >> LOGB) << LOGB) + (e & (kBlockCols - 1))];
+            for (int e = tid; e < plen; e += blockDim.x) sm.acc[e] = make_float2(0.f, 0.f);
+            __syncthreads();
+        }
+    }
+    if (i < n_items && tid == 0) {
+        // a copy never landed: flag it, let what is still in flight finish, and leave
+        atomicOr(flags, kErrTimeout);
+        for (int k = i; k < n_items && k < i + 2; ++k) mbar_wait(&sm.bar[k & 1], (k >> 1) & 1);
+    }
+}
+
+// Direct variant for planes too wide for the staged kernel's shared memory: one CTA per
+// group of 2^LG time frequencies, the first wire pass reads global memory directly.
+template <int LG>
+struct BlockedColLd {
+    const float2* src;   // Shat_j, blocked [nkb][n_w][4]
+    int n_w, kt0;
+    __device__ __forceinline__ float2 operator()(int c, int w) const
+    {
+        return (w < n_w) ? __ldg(src + blk_index(kt0 + c, w, n_w)) : make_float2(0.f, 0.f);
+    }
+};
+
+template <int LG>
+__global__ void __launch_bounds__(256, 1)
+k_wire_direct(ConvDims d, FftPlan p, const float2* __restrict__ shat, const float2* __restrict__ H,
+              float2* __restrict__ mt)
+{
+    constexpr int B = 1 << LG;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int N = p.n;
+    const int plen = padded_len(N) << LG;
+    float2* X = reinterpret_cast<float2*>(smraw);
+    float2* Y = X + plen;
+    float2* acc = Y + plen;
+    const int kt0 = blockIdx.x * B;        // B divides 4: a group never straddles blocks
     for (int e = threadIdx.x; e < plen; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
     for (int j = 0; j < d.n_imp; ++j) {
-        const TileLd src{shat + (int64_t)j * d.n_w * d.nh, d.nh, kt0, d.n_w};
-        const float2* z = run_plan<false, LOGB>(p, src, X, Y);
-        const float2* hj = H + (int64_t)j * d.n_fw * d.nh;
-        for (int e = threadIdx.x; e < (N << LOGB); e += blockDim.x) {
-            const int c = e & (B - 1), kw = e >> LOGB, kt = kt0 + c;
-            if (kt < d.nh) {
-                const int s = (pad16(kw) << LOGB) + c;
-                const float2 h = __ldg(hj + (int64_t)kw * d.nh + kt);
-                const float2 v = z[s];
-                float2 a = acc[s];
-                a.x += h.x * v.x - h.y * v.y;
-                a.y += h.x * v.y + h.y * v.x;
-                acc[s] = a;
-            }
+        const float2* sj = shat + (int64_t)j * d.nkb * d.n_w * kBlockCols;
+        const float2* z = run_plan<false, LG>(p, BlockedColLd<LG>{sj, d.n_w, kt0}, X, Y);
+        const float2* hj = H + (int64_t)j * d.nkb * N * kBlockCols;
+        for (int e = threadIdx.x; e < (N << LG); e += blockDim.x) {
+            const int c = e & (B - 1), kw = e >> LG;
+            const int idx = (pad16(kw) << LG) + c;
+            const float2 hv = __ldg(hj + blk_index(kt0 + c, kw, N)), v = z[idx];
+            float2 a = acc[idx];
+            a.x += hv.x * v.x - hv.y * v.y;
+            a.y += hv.x * v.y + hv.y * v.x;
+            acc[idx] = a;
         }
         __syncthreads();
     }
-    const float2* m = run_plan<true, LOGB>(p, SmemLd<LOGB>{acc}, X, Y);
-    for (int e = threadIdx.x; e < (d.n_w << LOGB); e += blockDim.x) {
-        const int c = e & (B - 1), w = e >> LOGB, kt = kt0 + c;
-        if (kt < d.nh) mt[(int64_t)w * d.nh + kt] = m[(pad16(w) << LOGB) + c];
+    const float2* m = run_plan<true, LG>(p, SmemLd<LG>{acc}, X, Y);
+    for (int e = threadIdx.x; e < (d.n_w << LG); e += blockDim.x) {
+        const int c = e & (B - 1), w = e >> LG;
+        mt[blk_index(kt0 + c, w, d.n_w)] = m[(pad16(w) << LG) + c];
     }
 }
 
 __global__ void k_make_hermitian(ConvDims d, const float2* __restrict__ R, float2* __restrict__ H,
                                  float scale)
 {
-    const int64_t total = (int64_t)d.n_imp * d.n_fw * d.nh;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int kt = (int)(i % d.nh);
-        const int64_t rest = i / d.nh;
+    // blocked output element e = ((j * nkb + kb) * n_fw + kw) * 4 + c, kt = 4 kb + c
+    const int64_t total = (int64_t)d.n_imp * d.nkb * d.n_fw * kBlockCols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e & (kBlockCols - 1));
+        int64_t rest = e >> 2;
         const int kw = (int)(rest % d.n_fw);
-        const int j = (int)(rest / d.n_fw);
-        const float2 a = R[((int64_t)j * d.n_fw + kw) * d.n_ft + kt];
-        const int kwm = (d.n_fw - kw) % d.n_fw, ktm = (d.n_ft - kt) % d.n_ft;
-        const float2 b = R[((int64_t)j * d.n_fw + kwm) * d.n_ft + ktm];
-        const float h = 0.5f * scale;
-        H[i] = make_float2(h * (a.x + b.x), h * (a.y - b.y));
+        rest /= d.n_fw;
+        const int kb = (int)(rest % d.nkb);
+        const int j = (int)(rest / d.nkb);
+        const int kt = kb * kBlockCols + c;
+        float2 h = make_float2(0.f, 0.f);
+        if (kt < d.nh) {
+            const float2 a = R[((int64_t)j * d.n_fw + kw) * d.n_ft + kt];
+            const int kwm = (d.n_fw - kw) % d.n_fw, ktm = (d.n_ft - kt) % d.n_ft;
+            const float2 b = R[((int64_t)j * d.n_fw + kwm) * d.n_ft + ktm];
+            const float f = 0.5f * scale;
+            h = make_float2(f * (a.x + b.x), f * (a.y - b.y));
+        }
+        H[e] = h;
     }
 }
 
-// Columns per CTA: 4 (full 32-byte sectors per wire row) when three padded 4-column
-// buffers fit two CTAs per SM, else 1.
-int wire_logb(int n_fw) { return (3 * (size_t)(padded_len(n_fw) << 2) * sizeof(float2) <= 110 * 1024) ? 2 : 0; }
-
 bool g_attr = false;
-cudaError_t attrs()
-{
-    if (g_attr) return cudaSuccess;
-    const int mx = 227 * 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_wire_pass<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) e = cudaFuncSetAttribute(k_wire_pass<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) g_attr = true;
-    return e;
-}
 
 }  // namespace
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 1;
+    }
+    return n;
+}
 
 cudaError_t launch_make_hermitian(const ConvDims& d, const float2* resp, float2* H, float scale,
                                   cudaStream_t s)
 {
-    const int64_t total = (int64_t)d.n_imp * d.n_fw * d.nh;
+    const int64_t total = (int64_t)d.n_imp * d.nkb * d.n_fw * kBlockCols;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 65535 * 16) blocks = 65535 * 16;
     k_make_hermitian<<<(unsigned)blocks, 256, 0, s>>>(d, resp, H, scale);
     return cudaGetLastError();
 }
 
+constexpr size_t kMaxSmem = 227 * 1024;
+
 cudaError_t launch_wire_pass(const ConvDims& d, const FftPlan& pw, const float2* shat,
-                             const float2* H, float2* mt, cudaStream_t s)
+                             const float2* H, float2* mt, int* flags, cudaStream_t s)
 {
-    cudaError_t e = attrs();
-    if (e) return e;
-    const int logb = wire_logb(pw.n);
-    const int B = 1 << logb;
-    const unsigned blocks = (unsigned)((d.nh + B - 1) / B);
-    const size_t smem = 3 * (size_t)(padded_len(pw.n) << logb) * sizeof(float2);
-    if (logb == 2)
-        k_wire_pass<2><<<blocks, kThreads, smem, s>>>(d, pw, shat, H, mt);
-    else
-        k_wire_pass<0><<<blocks, kThreads, smem, s>>>(d, pw, shat, H, mt);
+    if (!g_attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_wire_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (!e) e = cudaFuncSetAttribute(k_wire_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (!e) e = cudaFuncSetAttribute(k_wire_direct<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (e) return e;
+        g_attr = true;
+    }
+    const size_t staged = wire_smem_bytes(d.n_w, pw.n);
+    if (staged <= kMaxSmem) {
+        const int grid = d.nkb < sm_count() ? d.nkb : sm_count();
+        k_wire_pass<<<grid, kThreads, staged, s>>>(d, pw, shat, H, mt, flags);
+    } else if (3 * (size_t)(padded_len(pw.n) << 2) * sizeof(float2) <= kMaxSmem) {
+        k_wire_direct<2><<<d.nkb, 256, 3 * (size_t)(padded_len(pw.n) << 2) * sizeof(float2), s>>>(
+            d, pw, shat, H, mt);
+    } else {
+        k_wire_direct<0><<<d.nkb * kBlockCols, 256, 3 * (size_t)padded_len(pw.n) * sizeof(float2), s>>>(
+            d, pw, shat, H, mt);
+    }
     return cudaGetLastError();
 }
 

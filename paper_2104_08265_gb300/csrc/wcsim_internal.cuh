@@ -44,8 +44,9 @@ constexpr int kMaxFftN = 13500;       // time axis: two padded N-point buffers p
 constexpr int kMaxWireN = 8192;
 
 // Mixed-radix Stockham plan for one length N = prod(radix[p]).  Pass p combines groups
-// of ns[p] already-transformed points; tw_off[p] indexes (radix-1) * ns twiddles in the
-// plan's table; ns_magic[p] = ceil(2^32 / ns[p]) turns j / ns into a multiply-high.
+// of ns[p] already-transformed points; tw_off[p] indexes its (radix-1) * ns twiddles in
+// the plan's table (entry (r - 1) ns + k = exp(-2 pi i r k / (ns radix)));
+// ns_magic[p] = ceil(2^32 / ns[p]) turns j / ns into a multiply-high.
 struct FftPlan {
     int32_t n;
     int32_t npass;
@@ -62,24 +63,49 @@ bool fft_factor(int n, int32_t* radix, int32_t* npass);
 // Build the plan and upload its twiddle table (FP64 host values rounded to FP32).
 cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw);
 
+// Spectra over (time frequency kt < nh, wire or wire frequency) are stored in blocks of
+// kBlockCols adjacent time frequencies: element (kt, w) of an [n][nh] spectrum lives at
+// ((kt / 4) * n + w) * 4 + kt % 4.  One block is a contiguous 32 n-byte tile: the wire
+// pass fetches it with a single bulk copy.  Columns nh .. 4 nkb - 1 are zero.
+constexpr int kBlockCols = 4;
+
 struct ConvDims {
     int32_t n_w, n_imp, n_t;   // frame
     int32_t n_fw, n_ft;        // FFT sizes
     int32_t nh;                // n_ft / 2 + 1
+    int32_t nkb;               // ceil(nh / kBlockCols)
+    int32_t rows_variant;      // time-axis forward kernel: 0 direct loads, 1 bulk-staged
 };
 
-// H_j[kw][kt] = s * (R_j[kw][kt] + conj(R_j[-kw][-kt])) / 2 for kt in [0, nh).
+__host__ __device__ inline int64_t blk_index(int kt, int w, int n)
+{
+    return ((int64_t)(kt >> 2) * n + w) * kBlockCols + (kt & 3);
+}
+
+// H_j(kt, kw) = s * (R_j[kw][kt] + conj(R_j[-kw][-kt])) / 2, blocked [n_imp][nkb][n_fw][4].
 cudaError_t launch_make_hermitian(const ConvDims& d, const float2* resp, float2* H, float scale,
                                   cudaStream_t s);
-// Time-axis real-to-complex FFT of every grid row; writes Shat[j][w][kt] (kt < nh).
+// Time-axis real-to-complex FFT of every grid row; writes Shat_j blocked
+// [n_imp][nkb][n_w][4].
 cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* grid,
-                            float2* shat, cudaStream_t s);
-// Per time-frequency column: wire FFT of each S_j, times H_j, summed over j, inverse
-// wire FFT; writes Mt[w][kt].
+                            float2* shat, int* flags, cudaStream_t s);
+// Per block of time frequencies: wire FFT of each S_j, times H_j, summed over j, inverse
+// wire FFT; writes Mt blocked [nkb][n_w][4].
 cudaError_t launch_wire_pass(const ConvDims& d, const FftPlan& pw, const float2* shat,
+                             const float2* H, float2* mt, int* flags, cudaStream_t s);
+// Wire axes of 32 M points, M in this set, run as one warp per time frequency
+// (lanes x registers, no block barriers); others use the block-level engine.
+bool wire_warp_supported(int n_fw);
+// Twiddles of the warp kernel: [2][n_fw], exp(-2 pi i a b / n_fw) at a * 32 + b (a < M,
+// b < 32) and at b * M + a, FP64 rounded to FP32.  Device allocation owned by the caller.
+cudaError_t wire_warp_twiddles(int n_fw, float2** dev);
+cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
                              const float2* H, float2* mt, cudaStream_t s);
 // Time-axis complex-to-real inverse FFT of the Hermitian half rows of Mt -> wave.
 cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* mt,
                             float* wave, cudaStream_t s);
+
+// Streaming multiprocessors of the current device (cached).
+int sm_count();
 
 }  // namespace wcsim

@@ -156,7 +156,10 @@ CONV_CASES = [
     (33, 4, 96, 35, 98, False),
     (1, 1, 64, 1, 64, True),          # single wire, single impact
     (3, 2, 13500, 3, 13500, True),    # longest supported time axis
-    (960, 10, 16, 960, 16, True),     # many wires, short time axis
+    (960, 10, 16, 960, 16, True),     # many wires, short time axis (staged wire pass)
+    (1200, 1, 32, 1200, 32, True),    # wire pass without staging, 4 columns per CTA
+    (2400, 2, 16, 2400, 16, False),   # wire pass without staging, 1 column per CTA
+    (8192, 1, 8, 8192, 8, True),      # widest supported wire axis
 ]
 
 
@@ -178,6 +181,26 @@ def test_convolve_matches_oracle(W, case):
     wave = pl.convolve(torch.from_numpy(grid).cuda())
     ref = O.convolve(g, R, grid.astype(np.float64))
     assert_close(wave.cpu().numpy(), ref, what=str(case))
+
+
+@pytest.mark.parametrize("variant", [("", ""), ("staged", ""), ("", "block"), ("staged", "block")])
+def test_kernel_variants_match_oracle(W, variant, monkeypatch):
+    """Every time-axis / wire-axis kernel variant on the 960 x 6000 plane."""
+    import torch
+    rows, wire = variant
+    if rows:
+        monkeypatch.setenv("WCSIM_ROWS_KERNEL", rows)
+    if wire:
+        monkeypatch.setenv("WCSIM_WIRE_KERNEL", wire)
+    rng = np.random.default_rng(41)
+    g = S.Geometry(n_wires=960, n_imp=10, n_ticks=6000, pitch_mm=4.7)
+    grid = np.zeros((g.n_rows, g.n_ticks), np.float32)
+    idx = rng.integers(0, grid.size, 200000)
+    grid.reshape(-1)[idx] = rng.normal(size=idx.size).astype(np.float32)
+    R = S.make_response(g, "induction")
+    pl = plane_for(W, g, S.DriftParams(), R)
+    wave = pl.convolve(torch.from_numpy(grid).cuda()).cpu().numpy()
+    assert_close(wave, O.convolve(g, R, grid.astype(np.float64)), what=str(variant))
 
 
 def test_point_depo_gives_shifted_response(W):
