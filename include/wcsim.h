@@ -139,6 +139,28 @@ wcsim_status wcsim_plane_check(wcsim_plane* plane, void* stream, int32_t* flags)
 wcsim_status wcsim_plane_set_timing(wcsim_plane* plane, int32_t enable);
 wcsim_status wcsim_plane_stage_times(wcsim_plane* plane, float* ms, int32_t n);
 
+/* Bytes of the static device scratch used by wcsim_convolve_noalloc (16 MiB). */
+#define WCSIM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* The convolution of wcsim_convolve without any device allocation, for callers that may
+ * not allocate: code running under an allocator it does not own (a framework's caching
+ * allocator, a pool with a fixed budget) or a process that forbids allocation after
+ * start-up.  The paper has no counterpart; it is a deployment variant of wcsim_convolve.
+ * Inputs as in wcsim_plane_create + wcsim_convolve: geometry, DEVICE response complex64
+ * [n_imp][n_fw][n_ft] (n_fw, n_ft = 0: the frame size), DEVICE grid float32
+ * [n_wires * n_imp][n_ticks]; output DEVICE wave float32 [n_wires][n_ticks].  All
+ * intermediate arrays (Hermitian response, spectra, twiddle tables) live in one static
+ * device array of WCSIM_NOALLOC_SCRATCH_BYTES per device; frames whose scratch does not fit
+ * (e.g. 128 wires x 10 impacts x 1024 ticks needs about 11 MiB) are rejected with
+ * WCSIM_ESHAPE.  No cudaMalloc, cudaFree or allocating library call is made.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares the array and
+ * overwrites what the previous call left: calls whose GPU work overlaps race on it, so the
+ * caller must serialise them.  Stream-ordered; returns before the work is done. */
+wcsim_status wcsim_convolve_noalloc(const wcsim_geometry* geom, const void* resp_c64,
+                                    int32_t n_fw, int32_t n_ft, const float* grid, float* wave,
+                                    void* stream);
+
 /* Release the plane and everything it owns.  NULL is accepted. */
 wcsim_status wcsim_plane_destroy(wcsim_plane* plane);
 

@@ -201,6 +201,8 @@ wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaSt
 
 }  // namespace
 
+wcsim_status wcsim::report_error(wcsim_status s, const char* msg) { return fail(s, "%s", msg); }
+
 extern "C" {
 
 const char* wcsim_last_error(void) { return g_err; }

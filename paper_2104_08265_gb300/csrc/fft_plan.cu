@@ -120,3 +120,26 @@ cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw)
 }
 
 }  // namespace wcsim
+
+namespace wcsim {
+
+int fft_plan_describe(int n, FftPlan* plan)
+{
+    FftPlan p{};
+    p.n = n;
+    if (!fft_factor(n, p.radix, &p.npass)) return -1;
+    int ns = 1, len = 0;
+    for (int i = 0; i < p.npass; ++i) {
+        const int R = p.radix[i];
+        p.ns[i] = ns;
+        p.tw_off[i] = len;
+        p.ns_magic[i] = magic_for(ns);
+        len += (R - 1) * ns;
+        ns *= R;
+    }
+    p.tw = nullptr;
+    *plan = p;
+    return len < 1 ? 1 : len;
+}
+
+}  // namespace wcsim

@@ -62,6 +62,11 @@ struct FftPlan {
 bool fft_factor(int n, int32_t* radix, int32_t* npass);
 // Build the plan and upload its twiddle table (FP64 host values rounded to FP32).
 cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw);
+// The plan without its table (plan->tw left NULL); returns the table length in entries,
+// or -1 if n does not factor.  Allocates nothing.
+int fft_plan_describe(int n, FftPlan* plan);
+// Record a failure message for wcsim_last_error() and return s.
+wcsim_status report_error(wcsim_status s, const char* msg);
 
 // Spectra over (time frequency kt < nh, wire or wire frequency) are stored in blocks of
 // kBlockCols adjacent time frequencies: element (kt, w) of an [n][nh] spectrum lives at

@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_set_timing": [vp, i32],
         "wcsim_plane_stage_times": [vp, P(ctypes.c_float), i32],
         "wcsim_plane_destroy": [vp],
+        "wcsim_convolve_noalloc": [P(CGeometry), vp, i32, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -235,3 +236,20 @@ class Plane:
         arr = (ctypes.c_float * len(STAGES))()
         check(lib().wcsim_plane_stage_times(self._h, arr, len(STAGES)))
         return dict(zip(STAGES, [float(x) for x in arr]))
+
+
+def convolve_noalloc(geom: Geometry, response, grid, out=None, n_fw: int = 0, n_ft: int = 0,
+                     stream=None):
+    """Eq. 2 convolution through wcsim_convolve_noalloc: no device allocation inside the
+    library (its scratch is a fixed static device array, shared by all calls on a device;
+    calls must not overlap on the GPU).  `response`, `grid` and `out` are CUDA tensors."""
+    import torch
+    if out is None:
+        out = torch.empty((geom.n_wires, geom.n_ticks), dtype=torch.float32, device="cuda")
+    assert response.is_cuda and grid.is_cuda and out.is_cuda
+    assert response.dtype == torch.complex64 and grid.dtype == torch.float32
+    check(lib().wcsim_convolve_noalloc(ctypes.byref(c_geometry(geom)),
+                                       response.contiguous().data_ptr(), int(n_fw), int(n_ft),
+                                       grid.contiguous().data_ptr(), out.data_ptr(),
+                                       _stream_handle(stream)))
+    return out
