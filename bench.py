@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--soak-s", type=float, default=0.5,
                     help="untimed load before the timed loop, so the clock sampler sees the GPU busy")
     return ap.parse_args()
@@ -293,6 +294,35 @@ def run_gpu(args):
         tot_ms = float(t.item())
     assert plane.check_flags() == 0
 
+    # ---- forward + backward (loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10,
+    # lifetime 8 ms; the backward runs on the mean path and includes dL/dR)
+    fb_ms = None
+    if not args.no_backward:
+        import dataclasses
+        tgt = dataclasses.replace(prm, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0, fluctuate=0)
+        plane.set_params(tgt)
+        m_target = plane.run(dd).clone()
+        plane.set_params(prm)
+        G = torch.empty_like(wave)
+
+        def fb_step():
+            plane.run(dd, out=wave)
+            torch.sub(wave, m_target, out=G)
+            plane.backward(dd, G, want_resp=True)
+
+        for _ in range(args.warmup):
+            fb_step()
+        torch.cuda.synchronize()
+        fs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            fs[i].record(stream)
+            fb_step()
+            fe[i].record(stream)
+        torch.cuda.synchronize()
+        fb_ms = sum(s.elapsed_time(e) for s, e in zip(fs, fe)) / args.steps
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -350,7 +380,9 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config(args.workload, g, d, prm,
                                               {"parallelism": "replicas" if ws > 1 else "1 gpu"}),
-        "plane_frames_per_s": {"fwd": ws * 1e3 / per_step},
+        "plane_frames_per_s": {"fwd": ws * 1e3 / per_step,
+                               "fwd_bwd": (ws * 1e3 / fb_ms) if fb_ms else None},
+        "fwd_bwd_ms_per_step": fb_ms,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm,
                      "unit": "GB/s", "frac": ach / hbm, "traffic": None,
                      "peak_kind": peak_kind + " (burst copy)"},

@@ -125,6 +125,48 @@ wcsim_status wcsim_run(wcsim_plane* plane, const wcsim_depos* depos, float* wave
 wcsim_status wcsim_windows(wcsim_plane* plane, const wcsim_depos* depos, int32_t* out,
                            void* stream);
 
+/* Per-depo and global gradients of a scalar loss L (see wcsim_run_backward).  Every
+ * pointer is DEVICE memory and may be NULL (that output is then skipped).  Per-depo arrays
+ * have n entries, float32; dglobal has 3 doubles.  Units follow the inputs: dq per
+ * electron, dp per mm, dt per us, dsigma_L and dsigma_T per mm (sigma_L = sqrt(2 D_L t_d),
+ * the longitudinal spread in mm before division by v; sigma_T = sqrt(2 D_T t_d)), and
+ * dglobal = (dL/dD_L per cm^2/s, dL/dD_T per cm^2/s, dL/dlifetime per us). */
+typedef struct {
+    float* dq;
+    float* dp;
+    float* dt;
+    float* dsigma_L;
+    float* dsigma_T;
+    double* dglobal;
+} wcsim_depo_grads;
+
+/* Adjoint of wcsim_convolve (Eq. 2): given G = dL/dM (DEVICE float32 [n_wires][n_ticks])
+ * and the grid S the forward used (DEVICE float32 [n_wires * n_imp][n_ticks]), write
+ * dgrid = dL/dS = Re IFFT2(conj(R_j) . FFT2(G)) per impact row (DEVICE float32, same shape
+ * as S; may alias `grid`) and, if grad_resp is not NULL, dL/dR_j = conj(FFT2(S_j)) .
+ * FFT2(G) / (n_fw n_ft) (DEVICE complex64 [n_imp][n_fw][n_ft], the PyTorch convention for
+ * complex gradients: dL/dRe + i dL/dIm).  Requires n_fw = 32 M with M in {4, 8, 15, 16,
+ * 20, 24, 25, 30} (WCSIM_ESHAPE otherwise).  Uses the plane's scratch. */
+wcsim_status wcsim_convolve_adjoint(wcsim_plane* plane, const float* grad_wave, const float* grid,
+                                    float* dgrid, void* grad_resp_c64, void* stream);
+
+/* Adjoint of rasterization + drift on the mean path (no fluctuation), with each depo's bin
+ * window held fixed: given dgrid = dL/dS, write the gradients of L with respect to each
+ * depo's charge, pitch position, time, sigma_L, sigma_T, and the sums over depos for D_L,
+ * D_T and the lifetime (dglobal is overwritten).  sigma = 0 (t_d = 0) depos get zero sigma
+ * and position gradients; D_L or D_T = 0 give no gradient for that constant (the
+ * derivative of sqrt(2 D t) is unbounded there). */
+wcsim_status wcsim_rasterize_adjoint(wcsim_plane* plane, const wcsim_depos* depos,
+                                     const float* dgrid, wcsim_depo_grads* grads, void* stream);
+
+/* Backward pass of wcsim_run for L with dL/dwave = grad_wave: recompute the grid on the
+ * mean path (fluctuation off: the gradient is that of the expected waveform), run
+ * wcsim_convolve_adjoint and wcsim_rasterize_adjoint.  grad_resp_c64 as in
+ * wcsim_convolve_adjoint (NULL skips it).  Uses the plane's scratch and grid. */
+wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
+                                const float* grad_wave, wcsim_depo_grads* grads,
+                                void* grad_resp_c64, void* stream);
+
 /* Wait for the plane's work on `stream`, then read and clear its device flags.
  * *flags (may be NULL) receives the bit set (bit 0: invalid depo values seen; bit 1: a
  * kernel's bounded wait for an asynchronous copy gave up, so its output is incomplete).

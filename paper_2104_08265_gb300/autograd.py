@@ -1,0 +1,56 @@
+"""torch.autograd wrapper of the simulation: waveforms as a differentiable function of the
+depo charges, positions and times, the diffusion constants, the electron lifetime and the
+response spectrum.  Forward and backward both run in the CUDA library
+(wcsim_run / wcsim_run_backward); this module only moves tensors across the C ABI.
+
+The backward pass differentiates the mean (fluctuation-free) waveform with every depo's bin
+window held fixed, so a plane created with fluctuation on still gets the gradient of the
+expected frame.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import wcsim
+from .synth import DriftParams
+
+
+class WcsimFn(torch.autograd.Function):
+    """wave = WcsimFn.apply(plane, q, p, t, td, ids, DL, DT, lifetime, response).
+
+    q: float32 [n]; p, t, td: float64 [n]; ids: int32 [n] (CUDA).  DL, DT [cm^2/s] and
+    lifetime [us]: 0-d float64 tensors.  response: complex64 [n_imp][n_fw][n_ft] CUDA tensor
+    or None (keep the plane's).  Gradients flow to q, p, t, DL, DT, lifetime and response.
+    """
+
+    @staticmethod
+    def forward(ctx, plane, q, p, t, td, ids, DL, DT, lifetime, response):
+        prm = dataclasses.replace(plane.params, DL_cm2_s=float(DL), DT_cm2_s=float(DT),
+                                  lifetime_us=float(lifetime))
+        plane.set_params(prm)
+        if response is not None:
+            plane.set_response(response)
+        depos = wcsim.DeviceDepos(p.contiguous(), t.contiguous(), td.contiguous(),
+                                  q.contiguous(), ids.contiguous())
+        wave = plane.run(depos)
+        ctx.plane = plane
+        ctx.depos = depos
+        ctx.want_resp = response is not None and response.requires_grad
+        ctx.scalar_meta = [(x.dtype, x.device) for x in (DL, DT, lifetime)]
+        return wave
+
+    @staticmethod
+    def backward(ctx, grad_wave):
+        g = ctx.plane.backward(ctx.depos, grad_wave.contiguous().float(), want_resp=ctx.want_resp)
+        (dl_t, dl_d), (dt_t, dt_d), (tau_t, tau_d) = ctx.scalar_meta
+        return (None, g["q"], g["p"].double(), g["t"].double(), None, None,
+                g["DL"].to(dl_t).to(dl_d), g["DT"].to(dt_t).to(dt_d),
+                g["lifetime"].to(tau_t).to(tau_d), g["response"])
+
+
+def simulate(plane, depos: "wcsim.DeviceDepos", DL, DT, lifetime, response=None):
+    """Differentiable waveforms of `depos` on `plane` (see WcsimFn)."""
+    return WcsimFn.apply(plane, depos.q, depos.p, depos.t, depos.td, depos.id, DL, DT,
+                         lifetime, response)

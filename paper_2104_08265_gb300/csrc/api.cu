@@ -145,6 +145,10 @@ RasterConsts make_consts(const wcsim_plane* pl)
     c.key0 = (uint32_t)p.seed;
     c.key1 = (uint32_t)(p.seed >> 32);
     c.plane_id = p.plane_id;
+    c.DL = p.DL_cm2_s;
+    c.DT = p.DT_cm2_s;
+    c.v = p.v_mm_per_us;
+    c.tau = p.lifetime_us;
     return c;
 }
 
@@ -355,6 +359,73 @@ wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, v
     if (e) return cuda_fail(e, "rasterize launch");
     mark(pl, 2, s);
     return do_convolve(pl, pl->grid, wave, s, 3);
+}
+
+wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, const float* grid,
+                                    float* dgrid, void* grad_resp_c64, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (!grad_wave || !grid || !dgrid) return fail(WCSIM_EINVAL, "grad_wave, grid or dgrid is NULL");
+    if (!pl->tw_warp)
+        return fail(WCSIM_ESHAPE, "the adjoint needs a wire FFT size of 32 M, M in {4, 8, 15, 16, "
+                                  "20, 24, 25, 30} (got %d)", pl->dims.n_fw);
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ConvDims& d = pl->dims;
+    ConvDims dG = d;                    // G's rows: one "impact position" per wire
+    dG.n_imp = 1;
+    cudaError_t e;
+    if ((e = launch_rows_r2c(d, pl->pt, grid, pl->shat, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
+    if ((e = launch_rows_r2c(dG, pl->pt, grad_wave, pl->mt, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
+    if ((e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, (float2*)grad_resp_c64,
+                                      (float)(1.0 / ((double)d.n_fw * (double)d.n_ft)), s)))
+        return cuda_fail(e, "wire adjoint launch");
+    if ((e = launch_rows_c2r_grid(d, pl->pt, pl->shat, dgrid, s))) return cuda_fail(e, "rows_c2r_grid launch");
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_rasterize_adjoint(wcsim_plane* pl, const wcsim_depos* depos, const float* dgrid,
+                                     wcsim_depo_grads* grads, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    wcsim_status st = check_depos(depos);
+    if (st) return st;
+    if (!dgrid || !grads) return fail(WCSIM_EINVAL, "dgrid or grads is NULL");
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (grads->dglobal && (e = cudaMemsetAsync(grads->dglobal, 0, 3 * sizeof(double), s)))
+        return cuda_fail(e, "gradient reset");
+    DepoGrads g{grads->dq, grads->dp, grads->dt, grads->dsigma_L, grads->dsigma_T, grads->dglobal};
+    if ((e = launch_depo_adjoint(make_consts(pl), depo_arrays(depos), dgrid, g, pl->flags, s)))
+        return cuda_fail(e, "depo adjoint launch");
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_run_backward(wcsim_plane* pl, const wcsim_depos* depos, const float* grad_wave,
+                                wcsim_depo_grads* grads, void* grad_resp_c64, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    wcsim_status st = check_depos(depos);
+    if (st) return st;
+    if (!grad_wave || !grads) return fail(WCSIM_EINVAL, "grad_wave or grads is NULL");
+    if (!pl->tw_warp)
+        return fail(WCSIM_ESHAPE, "the adjoint needs a wire FFT size of 32 M, M in {4, 8, 15, 16, "
+                                  "20, 24, 25, 30} (got %d)", pl->dims.n_fw);
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ConvDims& d = pl->dims;
+    cudaError_t e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
+    if (e) return cuda_fail(e, "grid reset");
+    RasterConsts c = make_consts(pl);
+    c.fluctuate = 0;                    // the gradient is that of the mean waveform
+    if ((e = launch_rasterize(c, depo_arrays(depos), pl->grid, pl->flags, s)))
+        return cuda_fail(e, "rasterize launch");
+    if ((st = wcsim_convolve_adjoint(pl, grad_wave, pl->grid, pl->grid, grad_resp_c64, stream))) return st;
+    return wcsim_rasterize_adjoint(pl, depos, pl->grid, grads, stream);
 }
 
 wcsim_status wcsim_windows(wcsim_plane* pl, const wcsim_depos* depos, int32_t* out, void* stream)

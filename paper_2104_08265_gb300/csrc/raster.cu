@@ -213,6 +213,148 @@ k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
     }
 }
 
+// Derivatives of the bin weight w = Phi(b') - Phi(a') (a', b' = edge offsets / sigma) with
+// respect to mu and sigma, in units of 1/sigma:  -(phi(b') - phi(a')) and
+// -(b' phi(b') - a' phi(a')), with u = offset / (sqrt(2) sigma) = a' / sqrt(2).
+__device__ __forceinline__ void bin_weight_derivs(int64_t koff, float frac, float s, float& dmu,
+                                                  float& dsig)
+{
+    const float ua = ((float)koff - frac) * s;
+    const float ub = ((float)(koff + 1) - frac) * s;
+    const float inv_sqrt_2pi = 0.398942280401432678f;
+    const float pa = inv_sqrt_2pi * expf(-ua * ua), pb = inv_sqrt_2pi * expf(-ub * ub);
+    dmu = -(pb - pa);
+    dsig = -1.41421356237309505f * (ub * pb - ua * pa);
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per depo: recompute the patch weights and their mu / sigma derivatives, gather dL/dS over
+// the patch and apply the chain rule through Q' = Q exp(-t_d / tau), t_a = t + t_d and
+// sigma = sqrt(2 D t_d).  The global sums are reduced per block in FP64.
+__global__ void __launch_bounds__(kWarps * 32)
+k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, DepoGrads g,
+               int* flags)
+{
+    __shared__ Decision s_dec[kDepos];
+    __shared__ float s_w[kWarps][6][kWmax];      // wp, dwp/dmu, dwp/dsig, wt, dwt/dmu, dwt/dsig
+    __shared__ double s_glob[kWarps][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kDepos;
+    if (threadIdx.x < kDepos) {
+        Decision r;
+        r.ok = 0;
+        const int64_t i = base + threadIdx.x;
+        if (i < d.n) {
+            r = decide(c, d, i, flags);
+            r.id = d.id[i];
+        }
+        s_dec[threadIdx.x] = r;
+    }
+    __syncthreads();
+    double gl0 = 0.0, gl1 = 0.0, gl2 = 0.0;       // lane 0 of each warp
+    float* wp = s_w[warp][0];
+    float* wpm = s_w[warp][1];
+    float* wps = s_w[warp][2];
+    float* wt = s_w[warp][3];
+    float* wtm = s_w[warp][4];
+    float* wts = s_w[warp][5];
+
+    for (int i = warp; i < kDepos; i += kWarps) {
+        const int64_t gi = base + i;
+        if (gi >= d.n) break;
+        const Decision dd = s_dec[i];
+        float a_q = 0.f, a_pm = 0.f, a_ps = 0.f, a_tm = 0.f, a_ts = 0.f;
+        if (dd.ok && dd.qatt > 0.0f) {
+            const float s_p = (dd.sp > 0.0f) ? c.dp_f / (1.41421356237309505f * dd.sp) : 0.0f;
+            const float s_t = (dd.st > 0.0f) ? c.dt_f / (1.41421356237309505f * dd.st) : 0.0f;
+            const float isp = (dd.sp > 0.0f) ? 1.0f / dd.sp : 0.0f;
+            const float ist = (dd.st > 0.0f) ? 1.0f / dd.st : 0.0f;
+            for (int32_t r0 = dd.r_lo; r0 <= dd.r_hi; r0 += kWmax) {
+                const int nr = min(kWmax, dd.r_hi - r0 + 1);
+                for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kWmax) {
+                    const int nt = min(kWmax, dd.k_hi - k0 + 1);
+                    for (int e = lane; e < nr; e += 32) {
+                        const int64_t ko = (int64_t)(r0 + e) - dd.i0p;
+                        float m = 0.f, sg = 0.f;
+                        if (dd.sp > 0.0f) {
+                            wp[e] = bin_weight(ko, dd.frac_p, s_p);
+                            bin_weight_derivs(ko, dd.frac_p, s_p, m, sg);
+                        } else {
+                            wp[e] = 1.0f;
+                        }
+                        wpm[e] = m * isp;
+                        wps[e] = sg * isp;
+                    }
+                    for (int e = lane; e < nt; e += 32) {
+                        const int64_t ko = (int64_t)(k0 + e) - dd.i0t;
+                        float m = 0.f, sg = 0.f;
+                        if (dd.st > 0.0f) {
+                            wt[e] = bin_weight(ko, dd.frac_t, s_t);
+                            bin_weight_derivs(ko, dd.frac_t, s_t, m, sg);
+                        } else {
+                            wt[e] = 1.0f;
+                        }
+                        wtm[e] = m * ist;
+                        wts[e] = sg * ist;
+                    }
+                    __syncwarp();
+                    const float inv_nt = 1.0f / (float)nt;
+                    for (int b = lane; b < nr * nt; b += 32) {
+                        const int ir = (int)(((float)b + 0.5f) * inv_nt);
+                        const int ik = b - ir * nt;
+                        const float sv = __ldg(dgrid + (int64_t)(r0 + ir) * c.n_ticks + (k0 + ik));
+                        const float pw = wp[ir], tw = wt[ik];
+                        a_q += sv * pw * tw;
+                        a_pm += sv * wpm[ir] * tw;
+                        a_ps += sv * wps[ir] * tw;
+                        a_tm += sv * pw * wtm[ik];
+                        a_ts += sv * pw * wts[ik];
+                    }
+                    __syncwarp();
+                }
+            }
+            a_q = warp_sum(a_q);
+            a_pm = warp_sum(a_pm);
+            a_ps = warp_sum(a_ps);
+            a_tm = warp_sum(a_tm);
+            a_ts = warp_sum(a_ts);
+        }
+        if (lane == 0) {
+            const float qa = dd.ok ? dd.qatt : 0.0f;
+            const float att = (dd.ok && qa > 0.0f) ? qa / d.q[gi] : 0.0f;
+            const float dst = qa * a_ps, dsl = qa * a_ts * c.inv_v;
+            if (g.dq) g.dq[gi] = a_q * att;
+            if (g.dp) g.dp[gi] = qa * a_pm;
+            if (g.dt) g.dt[gi] = qa * a_tm;
+            if (g.dsl) g.dsl[gi] = dsl;
+            if (g.dst) g.dst[gi] = dst;
+            if (dd.ok && qa > 0.0f) {
+                // sigma = sqrt(2 D t_d): dsigma / dD = sigma / (2 D);  dQ'/dtau = Q' t_d / tau^2
+                if (c.DL > 0.0) gl0 += (double)dsl * ((double)dd.st * c.v) / (2.0 * c.DL);
+                if (c.DT > 0.0) gl1 += (double)dst * (double)dd.sp / (2.0 * c.DT);
+                gl2 += (double)a_q * (double)qa * d.td[gi] / (c.tau * c.tau);
+            }
+        }
+    }
+    if (lane == 0) {
+        s_glob[warp][0] = gl0;
+        s_glob[warp][1] = gl1;
+        s_glob[warp][2] = gl2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && g.dglobal) {
+        double acc = 0.0;
+        for (int w = 0; w < kWarps; ++w) acc += s_glob[w][threadIdx.x];
+        atomicAdd(g.dglobal + threadIdx.x, acc);
+    }
+}
+
 __global__ void k_windows(RasterConsts c, DepoArrays d, int32_t* __restrict__ out, int* flags)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,6 +372,15 @@ cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* 
     if (d.n <= 0) return cudaSuccess;
     const int64_t blocks = (d.n + kDepos - 1) / kDepos;
     k_rasterize<<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, grid, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_depo_adjoint(const RasterConsts& c, const DepoArrays& d, const float* dgrid,
+                                const DepoGrads& g, int* flags, cudaStream_t s)
+{
+    if (d.n <= 0) return cudaSuccess;
+    const int64_t blocks = (d.n + kDepos - 1) / kDepos;
+    k_depo_adjoint<<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, dgrid, g, flags);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,12 @@ struct RasterConsts {
     int32_t n_ticks;
     int32_t fluctuate;
     uint32_t key0, key1, plane_id;
+    double DL, DT, v, tau;                  // FP64 parameters for the global gradients
+};
+
+struct DepoGrads {
+    float *dq, *dp, *dt, *dsl, *dst;        // per depo, each may be null
+    double* dglobal;                        // [3]: dL/dD_L, dL/dD_T, dL/dtau (accumulated)
 };
 
 struct DepoArrays {
@@ -37,6 +43,10 @@ cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* 
                              int* flags, cudaStream_t s);
 cudaError_t launch_windows(const RasterConsts& c, const DepoArrays& d, int32_t* out,
                            int* flags, cudaStream_t s);
+// Adjoint of drift + rasterization (mean path, windows fixed): dgrid -> per-depo and global
+// gradients (dglobal must be zeroed by the caller).
+cudaError_t launch_depo_adjoint(const RasterConsts& c, const DepoArrays& d, const float* dgrid,
+                                const DepoGrads& g, int* flags, cudaStream_t s);
 
 // ------------------------------------------------------------------ FFT
 constexpr int kMaxPasses = 16;
@@ -106,6 +116,15 @@ bool wire_warp_supported(int n_fw);
 cudaError_t wire_warp_twiddles(int n_fw, float2** dev);
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
                              const float2* H, float2* mt, cudaStream_t s);
+// Adjoint of the wire pass (n_fw = 32 M): reads the time-axis spectra of the forward grid
+// (shat) and of G (gt, blocked [nkb][n_w][4]); overwrites shat with the time-axis spectra
+// of dL/dS and, if dR is not null, writes dL/dR_j (full [n_imp][n_fw][n_ft] layout).
+cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const float2* gt,
+                                     float2* shat, const float2* H, float2* dR, float inv_n,
+                                     cudaStream_t s);
+// Inverse time-axis FFT of every grid row from blocked spectra [n_imp][nkb][n_w][4].
+cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const float2* shat,
+                                 float* grid, cudaStream_t s);
 // Time-axis complex-to-real inverse FFT of the Hermitian half rows of Mt -> wave.
 cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* mt,
                             float* wave, cudaStream_t s);

@@ -51,6 +51,14 @@ class CDepos(ctypes.Structure):
                 ("id", ctypes.c_void_p), ("n", ctypes.c_int64)]
 
 
+class CDepoGrads(ctypes.Structure):
+    _fields_ = [("dq", ctypes.c_void_p), ("dp", ctypes.c_void_p), ("dt", ctypes.c_void_p),
+                ("dsigma_L", ctypes.c_void_p), ("dsigma_T", ctypes.c_void_p),
+                ("dglobal", ctypes.c_void_p)]
+
+
+GRAD_NAMES = ("q", "p", "t", "sigma_L", "sigma_T")
+
 _lib = None
 
 
@@ -76,6 +84,9 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_stage_times": [vp, P(ctypes.c_float), i32],
         "wcsim_plane_destroy": [vp],
         "wcsim_convolve_noalloc": [P(CGeometry), vp, i32, i32, vp, vp, vp],
+        "wcsim_convolve_adjoint": [vp, vp, vp, vp, vp, vp],
+        "wcsim_rasterize_adjoint": [vp, P(CDepos), vp, P(CDepoGrads), vp],
+        "wcsim_run_backward": [vp, P(CDepos), vp, P(CDepoGrads), vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -213,6 +224,60 @@ class Plane:
         out = self._wave(out)
         check(lib().wcsim_run(self._h, ctypes.byref(depos.c), out.data_ptr(),
                               _stream_handle(stream)))
+        return out
+
+    # ------------------------------------------------------------ adjoint
+    def _grads(self, n):
+        import torch
+        out = {k: torch.empty(n, dtype=torch.float32, device="cuda") for k in GRAD_NAMES}
+        out["global"] = torch.empty(3, dtype=torch.float64, device="cuda")
+        c = CDepoGrads(*[out[k].data_ptr() for k in GRAD_NAMES], out["global"].data_ptr())
+        return out, c
+
+    @staticmethod
+    def _split_global(out):
+        g = out.pop("global")
+        out["DL"], out["DT"], out["lifetime"] = g[0], g[1], g[2]
+        return out
+
+    def _resp_buffer(self, want):
+        import torch
+        if not want:
+            return None
+        return torch.empty((self.geom.n_imp, self.n_fw, self.n_ft), dtype=torch.complex64,
+                           device="cuda")
+
+    def convolve_adjoint(self, grad_wave, grid, dgrid=None, want_resp=False, stream=None):
+        """dL/dS (float32 grid shape) and, if asked, dL/dR (complex64) for dL/dM = grad_wave."""
+        import torch
+        if dgrid is None:
+            dgrid = torch.empty_like(grid)
+        dR = self._resp_buffer(want_resp)
+        check(lib().wcsim_convolve_adjoint(self._h, grad_wave.contiguous().data_ptr(),
+                                           grid.contiguous().data_ptr(), dgrid.data_ptr(),
+                                           dR.data_ptr() if dR is not None else None,
+                                           _stream_handle(stream)))
+        return dgrid, dR
+
+    def rasterize_adjoint(self, depos: DeviceDepos, dgrid, stream=None) -> dict:
+        """Per-depo and global gradients given dL/dS (mean path, windows fixed)."""
+        out, c = self._grads(len(depos))
+        check(lib().wcsim_rasterize_adjoint(self._h, ctypes.byref(depos.c),
+                                            dgrid.contiguous().data_ptr(), ctypes.byref(c),
+                                            _stream_handle(stream)))
+        return self._split_global(out)
+
+    def backward(self, depos: DeviceDepos, grad_wave, want_resp=False, stream=None) -> dict:
+        """Gradients of L with dL/dwave = grad_wave: per-depo q, p, t, sigma_L, sigma_T,
+        global DL, DT, lifetime and (if asked) the response spectrum."""
+        out, c = self._grads(len(depos))
+        dR = self._resp_buffer(want_resp)
+        check(lib().wcsim_run_backward(self._h, ctypes.byref(depos.c),
+                                       grad_wave.contiguous().data_ptr(), ctypes.byref(c),
+                                       dR.data_ptr() if dR is not None else None,
+                                       _stream_handle(stream)))
+        out = self._split_global(out)
+        out["response"] = dR
         return out
 
     def windows(self, depos: DeviceDepos, stream=None):

@@ -1,0 +1,151 @@
+"""Adjoint (backward) CUDA path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+The oracle's adjoint is pinned on CPU (finite differences, dot-product identity, torch
+autograd); here the GPU gradients must match it per output with relative L2 <= 1e-5 and
+max |err| <= 1e-4 x peak.  The three global sums (dL/dD_L, dL/dD_T, dL/dtau) add up
+terms of both signs over every depo, so they are compared with a relative error of 1e-4.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2104_08265_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+MAX_PEAK = 1e-4
+GLOBAL_REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2104_08265_gb300 import _build
+    _build.build()
+    from paper_2104_08265_gb300 import wcsim
+    return wcsim
+
+
+def assert_close(got, ref, rel=REL_L2, peak=MAX_PEAK, what=""):
+    got = np.asarray(got, np.complex128 if np.iscomplexobj(got) else np.float64)
+    ref = np.asarray(ref, got.dtype)
+    nref = np.linalg.norm(ref)
+    err = np.linalg.norm(got - ref)
+    mx = np.abs(got - ref).max()
+    pk = np.abs(ref).max()
+    assert np.isfinite(got).all(), what
+    assert err <= rel * nref, "%s rel L2 %.3e" % (what, err / nref)
+    assert mx <= peak * pk, "%s max/peak %.3e" % (what, mx / pk)
+    return err / nref, mx / pk
+
+
+def plane_for(W, g, prm, R):
+    import torch
+    return W.Plane(g, prm, torch.from_numpy(np.ascontiguousarray(R, np.complex64)).cuda())
+
+
+@pytest.mark.parametrize("shape", [(128, 10, 1024, 128, 1024), (250, 4, 1000, 256, 1024),
+                                   (960, 10, 6000, 960, 6000)])
+def test_convolve_adjoint_matches_oracle(W, shape):
+    import torch
+    n_w, n_imp, n_t, n_fw, n_ft = shape
+    rng = np.random.default_rng(n_w + n_t)
+    g = S.Geometry(n_wires=n_w, n_imp=n_imp, n_ticks=n_t, pitch_mm=3.0)
+    grid = np.zeros((g.n_rows, n_t), np.float32)
+    idx = rng.integers(0, grid.size, grid.size // 20)
+    grid.reshape(-1)[idx] = rng.normal(size=idx.size).astype(np.float32)
+    G = rng.normal(size=(n_w, n_t)).astype(np.float32)
+    R = S.make_response(g, "induction", n_fw=n_fw, n_ft=n_ft)
+    pl = plane_for(W, g, S.DriftParams(), R)
+    dS, dR = pl.convolve_adjoint(torch.from_numpy(G).cuda(), torch.from_numpy(grid).cuda(),
+                                 want_resp=True)
+    rdS, rdR = O.convolve_adjoint(g, R, grid.astype(np.float64), G.astype(np.float64))
+    assert_close(dS.cpu().numpy(), rdS, what="dS %s" % (shape,))
+    assert_close(dR.cpu().numpy(), rdR, what="dR %s" % (shape,))
+
+
+def _grads_close(got, ref, what):
+    for k in ("q", "p", "t", "sigma_L", "sigma_T"):
+        assert_close(got[k].cpu().numpy(), ref[k], what="%s %s" % (what, k))
+    for k in ("DL", "DT", "lifetime"):
+        a, b = float(got[k].cpu()), float(ref[k])
+        assert abs(a - b) <= GLOBAL_REL * abs(b), (what, k, a, b)
+
+
+def test_rasterize_adjoint_matches_oracle(W):
+    import torch
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0)
+    rng = np.random.default_rng(81)
+    dS = rng.normal(size=(g.n_rows, g.n_ticks)).astype(np.float32)
+    pl = plane_for(W, g, prm, S.make_response(g, kind))
+    got = pl.rasterize_adjoint(W.DeviceDepos.from_host(d), torch.from_numpy(dS).cuda())
+    ref = O.depo_grads(g, prm, d, dS.astype(np.float64))
+    _grads_close(got, ref, "rasterize_adjoint")
+
+
+def _oracle_backward(g, prm, R, d, G):
+    mean = dataclasses.replace(prm, fluctuate=0)
+    grid = O.rasterize(g, mean, d)
+    dS, dR = O.convolve_adjoint(g, R, grid, G)
+    return O.depo_grads(g, mean, d, dS), dR
+
+
+@pytest.mark.parametrize("name", ["plane128-2k", "fit960-100k"])
+def test_run_backward_matches_oracle(W, name):
+    """Loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10 cm^2/s, tau = 8 ms."""
+    import torch
+    wl = S.make_workload(name)
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=0)
+    R = S.make_response(g, kind)
+    target = dataclasses.replace(prm, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0)
+    pl = plane_for(W, g, target, R)
+    dd = W.DeviceDepos.from_host(d)
+    M_target = pl.run(dd).clone()
+    pl.set_params(prm)
+    M = pl.run(dd)
+    G = (M - M_target).contiguous()
+    got = pl.backward(dd, G, want_resp=True)
+    ref, rdR = _oracle_backward(g, prm, R, d, G.cpu().numpy().astype(np.float64))
+    _grads_close(got, ref, name)
+    assert_close(got["response"].cpu().numpy(), rdR, what=name + " dR")
+
+
+def test_autograd_function_gradients_and_a_fit_step(W):
+    """The autograd wrapper returns the library's gradients, and a gradient step on
+    (D_L, D_T, tau) toward a target frame lowers the loss."""
+    import torch
+    from paper_2104_08265_gb300.autograd import simulate
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    R = torch.from_numpy(S.make_response(g, kind)).cuda()
+    pl = W.Plane(g, prm, R)
+    dd = W.DeviceDepos.from_host(d)
+    t64 = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        target = simulate(pl, dd, t64(6.0), t64(10.0), t64(8000.0)).clone()
+    DL, DT, tau = (t64(4.0).requires_grad_(), t64(8.8).requires_grad_(),
+                   t64(10000.0).requires_grad_())
+    q = dd.q.clone().requires_grad_()
+    resp = R.clone().requires_grad_()
+    wave = simulate(pl, W.DeviceDepos(dd.p, dd.t, dd.td, q, dd.id), DL, DT, tau, resp)
+    loss = 0.5 * ((wave - target) ** 2).sum()
+    loss.backward()
+    ref = pl.backward(dd, (wave - target).detach().contiguous(), want_resp=True)
+    # two backward runs differ only by the summation order of the atomic scatter-add
+    for a, b in ((q.grad, ref["q"]), (resp.grad, ref["response"])):
+        assert float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) < 1e-6
+    for x, k in ((DL, "DL"), (DT, "DT"), (tau, "lifetime")):
+        assert float(x.grad) == pytest.approx(float(ref[k]), rel=1e-5)
+    # one small step along -grad lowers the loss
+    with torch.no_grad():
+        step = [DL, DT, tau]
+        gnorm = sum(float(x.grad) ** 2 for x in step) ** 0.5
+        scale = [4.0, 8.8, 10000.0]
+        new = [x - 0.02 * s * x.grad / gnorm for x, s in zip(step, scale)]
+        loss2 = 0.5 * ((simulate(pl, dd, *new) - target) ** 2).sum()
+    assert float(loss2) < float(loss)
