@@ -102,6 +102,28 @@ def fft_flops(g):
     return fwd_rows + wire + mult + inv_rows
 
 
+STAGE_KERNEL = {"rows_r2c": "k_rows_r2c_direct", "wire_pass": "k_wire_warp",
+                "rasterize": "k_rasterize", "rows_c2r": "k_rows_c2r"}
+
+
+def ncu_traffic(stage):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu record, or None
+    when the CUDA sources changed since the counters were taken."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path) or stage not in STAGE_KERNEL:
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2104_08265_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(src, "*.cu")) + glob.glob(os.path.join(src, "*.cuh"))):
+        h.update(open(f, "rb").read())
+    if h.hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec["bytes_per_launch"].get(STAGE_KERNEL[stage])
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -384,7 +406,8 @@ def run_gpu(args):
                                "fwd_bwd": (ws * 1e3 / fb_ms) if fb_ms else None},
         "fwd_bwd_ms_per_step": fb_ms,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm,
-                     "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                     "unit": "GB/s", "frac": ach / hbm, "traffic": ncu_traffic(dom),
+                     "alg_bytes": sb[dom],
                      "peak_kind": peak_kind + " (burst copy)"},
         "step_roofline": {"bmin_bytes": bmin_bytes(g, len(d)),
                           "bmin_GBps": bmin_bytes(g, len(d)) / (per_step * 1e-3) / 1e9,
