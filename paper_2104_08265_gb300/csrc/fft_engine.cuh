@@ -235,14 +235,23 @@ __device__ __forceinline__ void dft(float2* v)
 // ------------------------------------------------------------------ shared-memory access
 template <int LOGB>
 struct SmemLd {
+    static constexpr bool kShared = true;
     const float2* p;
     __device__ __forceinline__ float2 operator()(int c, int i) const { return p[(pad16(i) << LOGB) + c]; }
+    __device__ __forceinline__ float2 at(int c, int pi) const { return p[(pi << LOGB) + c]; }
 };
 template <int LOGB>
 struct SmemSt {
+    static constexpr bool kShared = true;
     float2* p;
     __device__ __forceinline__ void operator()(int c, int i, float2 v) const { p[(pad16(i) << LOGB) + c] = v; }
+    __device__ __forceinline__ void at(int c, int pi, float2 v) const { p[(pi << LOGB) + c] = v; }
 };
+
+template <class T, class = void>
+struct IsShared { static constexpr bool value = false; };
+template <class T>
+struct IsShared<T, decltype((void)T::kShared)> { static constexpr bool value = T::kShared; };
 
 struct PassArgs {
     int n, ns;
@@ -262,8 +271,20 @@ __device__ __forceinline__ void pass_r(const Ld& ld, const St& st, const PassArg
         const int q = (a.ns == 1) ? j : (int)__umulhi((uint32_t)j, a.ns_magic);
         const int k = j - q * a.ns;
         float2 v[R];
+        // Padded shared indices: pad16(j + r nb) = pad16(j) + r (nb + nb / 16) when 16 | nb.
+        if constexpr (IsShared<Ld>::value) {
+            if ((nb & 15) == 0) {
+                const int p0 = pad16(j), ps = nb + (nb >> 4);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = ld(c, j + r * nb);
+                for (int r = 0; r < R; ++r) v[r] = ld.at(c, p0 + r * ps);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[r] = ld(c, j + r * nb);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = ld(c, j + r * nb);
+        }
         if (k > 0) {
             const float2* t = a.tw + k;
 #pragma unroll
@@ -271,8 +292,21 @@ __device__ __forceinline__ void pass_r(const Ld& ld, const St& st, const PassArg
         }
         dft<R, INV>(v);
         const int o = q * a.ns * R + k;
+        // pad16(o + r ns) = pad16(o) + r (ns + ns / 16) when 16 | ns; a radix-16 first pass
+        // (ns = 1, o = 16 q) writes 16 consecutive padded slots.
+        if constexpr (IsShared<St>::value) {
+            if ((a.ns & 15) == 0 || (R == 16 && a.ns == 1)) {
+                const int p0 = pad16(o), ps = (a.ns == 1) ? 1 : a.ns + (a.ns >> 4);
 #pragma unroll
-        for (int r = 0; r < R; ++r) st(c, o + r * a.ns, v[r]);
+                for (int r = 0; r < R; ++r) st.at(c, p0 + r * ps, v[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) st(c, o + r * a.ns, v[r]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) st(c, o + r * a.ns, v[r]);
+        }
     }
 }
 

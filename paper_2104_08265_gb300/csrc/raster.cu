@@ -110,21 +110,28 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp, 0 at 0).
+__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 // Four standard normals from one Philox block: two Box-Muller pairs (Box & Muller 1958),
 // u = (x + 1/2) 2^-32; z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1), z2, z3 likewise.
+// Hardware log2 / sin / cos (absolute error ~1e-6 in z); the angle is taken as
+// 2 pi (u - 1/2) in [-pi, pi], where the hardware sine and cosine are accurate, and the
+// half turn is undone by negating both.
 __device__ __forceinline__ void box_muller4(uint4 x, float z[4])
 {
     const float sc = 2.3283064365386963e-10f, off = 1.1641532182693481e-10f;
+    const float two_pi = 6.28318530717958648f, ln2x2 = -1.38629436111989061f;   // -2 ln 2
     const float u0 = fmaf((float)x.x, sc, off), u1 = fmaf((float)x.y, sc, off);
     const float u2 = fmaf((float)x.z, sc, off), u3 = fmaf((float)x.w, sc, off);
-    const float ra = sqrtf(-2.0f * logf(u0)), rb = sqrtf(-2.0f * logf(u2));
+    const float ra = sqrt_fast(ln2x2 * __log2f(u0)), rb = sqrt_fast(ln2x2 * __log2f(u2));
     float sa, ca, sb, cb;
-    sincospif(2.0f * u1, &sa, &ca);
-    sincospif(2.0f * u3, &sb, &cb);
-    z[0] = ra * ca;
-    z[1] = ra * sa;
-    z[2] = rb * cb;
-    z[3] = rb * sb;
+    __sincosf(two_pi * (u1 - 0.5f), &sa, &ca);
+    __sincosf(two_pi * (u3 - 0.5f), &sb, &cb);
+    z[0] = -ra * ca;
+    z[1] = -ra * sa;
+    z[2] = -rb * cb;
+    z[3] = -rb * sb;
 }
 
 __global__ void __launch_bounds__(kWarps * 32)
@@ -192,8 +199,8 @@ k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
                                                       c.plane_id), c.key0, c.key1), z);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const float var = fmaxf(0.0f, v[e] * (1.0f - v[e] * inv_q));
-                            v[e] = fmaxf(0.0f, v[e] + sqrtf(var) * z[e]);
+                            const float var = v[e] * (1.0f - v[e] * inv_q);
+                            v[e] = fmaxf(0.0f, fmaf(sqrt_fast(var), z[e], v[e]));
                         }
                     }
                     float* dst = grid + r * c.n_ticks + kq;
