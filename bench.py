@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-event batched run (wcsim_batch_run vs 64 wcsim_run calls)")
     ap.add_argument("--soak-s", type=float, default=0.5,
                     help="untimed load before the timed loop, so the clock sampler sees the GPU busy")
     return ap.parse_args()
@@ -245,6 +247,58 @@ def cufft_comparison(g, reps=10):
     return out
 
 
+# ---------------------------------------------------------------- batched events
+def batch_comparison(args, wcsim, steps=5):
+    """64 independent events (planes 480/800/960 wires x 2000/6000/9600 ticks, depo counts
+    log-uniform in 1e3..5e5): one wcsim_batch_run replayed from a CUDA graph vs 64 plain
+    wcsim_run calls on the same planes, same stream, same GPU."""
+    import torch
+    wl = synth.make_workload("batch64")
+    planes, depos, seqp = {}, [], []
+    for e, (g, prm, kind, d) in enumerate(wl.planes):
+        key = (g.n_wires, g.n_ticks, kind)
+        if key not in planes:
+            planes[key] = wcsim.Plane(g, prm, synth.make_response(g, kind, backend="torch"))
+        seqp.append(planes[key])
+        depos.append(wcsim.DeviceDepos.from_host(d))
+    torch.cuda.empty_cache()
+    b = wcsim.Batch(seqp, depos)
+    n_depos = sum(len(d) for d in depos)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        b.run()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.run()
+    graph.replay()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        t = []
+        for _ in range(steps):
+            a = torch.cuda.Event(enable_timing=True); z = torch.cuda.Event(enable_timing=True)
+            a.record(stream); fn(); z.record(stream)
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(z))
+        return float(np.median(t))
+
+    def sequential():
+        for e, (pl, d, w) in enumerate(zip(seqp, depos, b.waves)):
+            pl.run(d, out=w)
+
+    sequential()
+    ms_batch = timed(graph.replay)
+    ms_seq = timed(sequential)
+    for p in planes.values():
+        p.close()
+    return {"events": len(seqp), "plane_types": len(planes), "depos": n_depos,
+            "batched_graph_ms": ms_batch, "sequential_ms": ms_seq,
+            "speedup": ms_seq / ms_batch, "batched_depos_per_s": n_depos / (ms_batch * 1e-3),
+            "note": "median of %d; the sequential arm runs each event with its plane's seed "
+                    "(the batch adds the event index), same kernels otherwise" % steps}
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -383,6 +437,10 @@ def run_gpu(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_ms / args.steps}
 
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_comparison(args, wcsim)
+
     cufft = None
     if rank == 0 and not args.no_cufft:
         cufft = cufft_comparison(g)
@@ -421,6 +479,7 @@ def run_gpu(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "cufft_comparison": cufft,
+        "batch64": batch,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

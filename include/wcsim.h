@@ -167,6 +167,24 @@ wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
                                 const float* grad_wave, wcsim_depo_grads* grads,
                                 void* grad_resp_c64, void* stream);
 
+/* Maximum events of one wcsim_batch_run call. */
+#define WCSIM_MAX_BATCH 64
+
+/* Batched simulation of independent events (the planned all-device flow of Fig. 4 applied
+ * to many events at once): event e runs wcsim_run on planes[e] with depos[e] (DEVICE SoA)
+ * into waves[e] (DEVICE float32 [n_wires][n_ticks] of that plane), with the fluctuation
+ * seed of planes[e] plus e.  Events that share a plane object are processed together: each
+ * stage is one launch over all of them, and the wire pass reads each response tile once
+ * for all of them.  A plane needs batch scratch for as many events as share it; it is grown
+ * on demand (allocating) or beforehand with wcsim_plane_reserve_batch, after which the call
+ * allocates nothing, synchronizes nothing and can be recorded in a stream capture.
+ * 0 <= n_events <= WCSIM_MAX_BATCH; all planes on one device. */
+wcsim_status wcsim_batch_run(int32_t n_events, wcsim_plane* const* planes,
+                             const wcsim_depos* depos, float* const* waves, void* stream);
+
+/* Reserve batch scratch for n_events (<= WCSIM_MAX_BATCH) events on this plane. */
+wcsim_status wcsim_plane_reserve_batch(wcsim_plane* plane, int32_t n_events);
+
 /* Wait for the plane's work on `stream`, then read and clear its device flags.
  * *flags (may be NULL) receives the bit set (bit 0: invalid depo values seen; bit 1: a
  * kernel's bounded wait for an asynchronous copy gave up, so its output is incomplete).

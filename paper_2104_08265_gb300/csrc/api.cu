@@ -70,6 +70,11 @@ struct wcsim_plane {
     float2* shat = nullptr;     // time-axis spectra, blocked [n_imp][nkb][n_wires][4]
     float2* mt = nullptr;       // wire-summed spectra, blocked [nkb][n_wires][4]
     int* flags = nullptr;       // device flag word
+    // scratch of batched runs: bcap events' grids, time-axis and wire-summed spectra
+    float* bgrid = nullptr;
+    float2* bshat = nullptr;
+    float2* bmt = nullptr;
+    int32_t bcap = 0;
     int device = 0;
     bool timing = false;
     cudaEvent_t ev[kStages + 1] = {};
@@ -175,6 +180,9 @@ void plane_free(wcsim_plane* pl)
     cudaFree(pl->shat);
     cudaFree(pl->mt);
     cudaFree(pl->flags);
+    cudaFree(pl->bgrid);
+    cudaFree(pl->bshat);
+    cudaFree(pl->bmt);
     if (pl->ev_valid)
         for (auto& e : pl->ev) cudaEventDestroy(e);
     delete pl;
@@ -200,6 +208,77 @@ wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaSt
     mark(pl, first_mark + 1, s);
     if ((e = launch_rows_c2r(pl->dims, pl->pt, pl->mt, wave, s))) return cuda_fail(e, "rows_c2r launch");
     mark(pl, first_mark + 2, s);
+    return WCSIM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+size_t ev_grid_elems(const ConvDims& d) { return (size_t)d.n_w * d.n_imp * d.n_t; }
+size_t ev_shat_elems(const ConvDims& d) { return (size_t)d.n_w * d.n_imp * d.nkb * kBlockCols; }
+size_t ev_mt_elems(const ConvDims& d) { return (size_t)d.n_w * d.nkb * kBlockCols; }
+
+wcsim_status reserve_batch(wcsim_plane* pl, int32_t n)
+{
+    if (n <= pl->bcap) return WCSIM_OK;
+    cudaFree(pl->bgrid);
+    cudaFree(pl->bshat);
+    cudaFree(pl->bmt);
+    pl->bgrid = nullptr;
+    pl->bshat = nullptr;
+    pl->bmt = nullptr;
+    pl->bcap = 0;
+    const ConvDims& d = pl->dims;
+    cudaError_t e = cudaMalloc(&pl->bgrid, (size_t)n * ev_grid_elems(d) * sizeof(float));
+    if (!e) e = cudaMalloc(&pl->bshat, (size_t)n * ev_shat_elems(d) * sizeof(float2));
+    if (!e) e = cudaMalloc(&pl->bmt, (size_t)n * ev_mt_elems(d) * sizeof(float2));
+    if (e) return cuda_fail(e, "batch scratch allocation");
+    pl->bcap = n;
+    return WCSIM_OK;
+}
+
+// Events ev[0..k) of one plane (global batch indices idx[] for the seeds), k <= kMaxBatch.
+wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_depos* depos,
+                       float* const* waves, cudaStream_t s)
+{
+    wcsim_status st = reserve_batch(pl, k);
+    if (st) return st;
+    const ConvDims& d0 = pl->dims;
+    ConvDims d = d0;
+    d.ev_grid = (int64_t)ev_grid_elems(d0);
+    d.ev_shat = (int64_t)ev_shat_elems(d0);
+    d.ev_mt = (int64_t)ev_mt_elems(d0);
+    cudaError_t e = cudaMemsetAsync(pl->bgrid, 0, (size_t)k * ev_grid_elems(d0) * sizeof(float), s);
+    if (e) return cuda_fail(e, "batch grid reset");
+    RasterConsts c = make_consts(pl);
+    BatchEvents ev;
+    ev.n = k;
+    ev.block_start[0] = 0;
+    for (int i = 0; i < k; ++i) {
+        const wcsim_depos* dp = &depos[idx[i]];
+        ev.d[i] = depo_arrays(dp);
+        ev.grid[i] = pl->bgrid + (size_t)i * ev_grid_elems(d0);
+        const uint64_t seed = pl->prm.seed + (uint64_t)idx[i];     // per-event stream
+        ev.key0[i] = (uint32_t)seed;
+        ev.key1[i] = (uint32_t)(seed >> 32);
+        ev.block_start[i + 1] = ev.block_start[i] + rasterize_blocks(dp->n);
+    }
+    if ((e = launch_rasterize_batch(c, ev, pl->flags, s))) return cuda_fail(e, "batch rasterize launch");
+    if ((e = launch_rows_r2c_batch(d, pl->pt, pl->bgrid, pl->bshat, k, s)))
+        return cuda_fail(e, "batch rows_r2c launch");
+    if (pl->tw_warp) {
+        if ((e = launch_wire_warp(d, pl->tw_warp, pl->bshat, pl->H, pl->bmt, s, k)))
+            return cuda_fail(e, "batch wire launch");
+    } else {
+        for (int i = 0; i < k; ++i)
+            if ((e = launch_wire_pass(d0, pl->pw, pl->bshat + i * d.ev_shat, pl->H, pl->bmt + i * d.ev_mt,
+                                      pl->flags, s)))
+                return cuda_fail(e, "batch wire launch");
+    }
+    WavePtrs w;
+    for (int i = 0; i < k; ++i) w.p[i] = waves[idx[i]];
+    if ((e = launch_rows_c2r_batch(d, pl->pt, pl->bmt, w, k, s))) return cuda_fail(e, "batch rows_c2r launch");
     return WCSIM_OK;
 }
 
@@ -426,6 +505,50 @@ wcsim_status wcsim_run_backward(wcsim_plane* pl, const wcsim_depos* depos, const
         return cuda_fail(e, "rasterize launch");
     if ((st = wcsim_convolve_adjoint(pl, grad_wave, pl->grid, pl->grid, grad_resp_c64, stream))) return st;
     return wcsim_rasterize_adjoint(pl, depos, pl->grid, grads, stream);
+}
+
+wcsim_status wcsim_plane_reserve_batch(wcsim_plane* pl, int32_t n_events)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (n_events < 0 || n_events > kMaxBatch)
+        return fail(WCSIM_ESHAPE, "n_events must be in [0, %d]", kMaxBatch);
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    return reserve_batch(pl, n_events);
+}
+
+wcsim_status wcsim_batch_run(int32_t n_events, wcsim_plane* const* planes,
+                                        const wcsim_depos* depos, float* const* waves, void* stream)
+{
+    if (n_events < 0 || n_events > kMaxBatch)
+        return fail(WCSIM_ESHAPE, "n_events must be in [0, %d]", kMaxBatch);
+    if (n_events == 0) return WCSIM_OK;
+    if (!planes || !depos || !waves) return fail(WCSIM_EINVAL, "planes, depos or waves is NULL");
+    for (int i = 0; i < n_events; ++i) {
+        if (!planes[i] || !waves[i]) return fail(WCSIM_EINVAL, "event %d: plane or wave is NULL", i);
+        wcsim_status st = check_depos(&depos[i]);
+        if (st) return st;
+        if (planes[i]->device != planes[0]->device)
+            return fail(WCSIM_EINVAL, "all planes of a batch must live on one device");
+    }
+    DeviceGuard dg(planes[0]->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    // group events by plane, in order of first appearance
+    bool done[kMaxBatch] = {};
+    int32_t idx[kMaxBatch];
+    for (int i = 0; i < n_events; ++i) {
+        if (done[i]) continue;
+        int k = 0;
+        for (int j = i; j < n_events; ++j)
+            if (!done[j] && planes[j] == planes[i]) {
+                idx[k++] = j;
+                done[j] = true;
+            }
+        wcsim_status st = run_group(planes[i], k, idx, depos, waves, s);
+        if (st) return st;
+    }
+    return WCSIM_OK;
 }
 
 wcsim_status wcsim_windows(wcsim_plane* pl, const wcsim_depos* depos, int32_t* out, void* stream)

@@ -159,16 +159,20 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
     const int64_t n_rows = (int64_t)d.n_w * d.n_imp;
     const int64_t r0 = 2 * (int64_t)blockIdx.x;
     const bool has1 = r0 + 1 < n_rows;
+    grid += blockIdx.y * d.ev_grid;          // event of a batched launch (0 otherwise)
+    shat += blockIdx.y * d.ev_shat;
     const RealPairLd src{grid + r0 * d.n_t, has1 ? grid + (r0 + 1) * d.n_t : nullptr, d.n_t};
     const float2* z = run_plan<false, 0>(p, src, X, Y);
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
 
 __global__ void __launch_bounds__(kDirectThreads, 2)
-k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, float* __restrict__ wave)
+k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     const int N = p.n;
+    mt += blockIdx.y * d.ev_mt;              // event of a batched launch (0 otherwise)
+    float* __restrict__ wave = waves.p[blockIdx.y];
     float2* X = reinterpret_cast<float2*>(smraw);
     float2* Y = X + padded_len(N);
     const int w0 = 2 * blockIdx.x, w1 = w0 + 1;
@@ -221,9 +225,29 @@ cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* g
 cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* mt,
                             float* wave, cudaStream_t s)
 {
+    WavePtrs w;
+    w.p[0] = wave;
+    return launch_rows_c2r_batch(d, pt, mt, w, 1, s);
+}
+
+cudaError_t launch_rows_c2r_batch(const ConvDims& d, const FftPlan& pt, const float2* mt,
+                                  const WavePtrs& waves, int n_ev, cudaStream_t s)
+{
     cudaError_t e = attrs();
     if (e) return e;
-    k_rows_c2r<<<(unsigned)((d.n_w + 1) / 2), kDirectThreads, direct_smem(pt.n), s>>>(d, pt, mt, wave);
+    const dim3 grid((unsigned)((d.n_w + 1) / 2), (unsigned)n_ev);
+    k_rows_c2r<<<grid, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, mt, waves);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_r2c_batch(const ConvDims& d, const FftPlan& pt, const float* grid,
+                                  float2* shat, int n_ev, cudaStream_t s)
+{
+    cudaError_t e = attrs();
+    if (e) return e;
+    const int64_t n_pairs = ((int64_t)d.n_w * d.n_imp + 1) / 2;
+    const dim3 g((unsigned)n_pairs, (unsigned)n_ev);
+    k_rows_r2c_direct<<<g, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, grid, shat);
     return cudaGetLastError();
 }
 

@@ -38,7 +38,10 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kb = blockIdx.x, c = warp;
+    // grid (events, blocks): the events of one block run side by side and share H's tiles
+    const int kb = blockIdx.y, c = warp;
+    shat += blockIdx.x * d.ev_shat;
+    mt += blockIdx.x * d.ev_mt;
     float2* tr = s_tr[warp];
     float2 acc[32];
 #pragma unroll
@@ -131,11 +134,12 @@ cudaError_t wire_warp_twiddles(int n_fw, float2** dev)
 }
 
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
-                             const float2* H, float2* mt, cudaStream_t s)
+                             const float2* H, float2* mt, cudaStream_t s, int n_ev)
 {
+    const dim3 grid((unsigned)n_ev, (unsigned)d.nkb);
     switch (d.n_fw / 32) {
 #define WCSIM_CASE(MM) \
-    case MM: k_wire_warp<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, shat, H, mt); break;
+    case MM: k_wire_warp<MM><<<grid, kWarps * 32, 0, s>>>(d, tw2, shat, H, mt); break;
         WCSIM_WARP_M(WCSIM_CASE)
 #undef WCSIM_CASE
         default: return cudaErrorInvalidValue;

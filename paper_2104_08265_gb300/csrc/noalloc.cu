@@ -82,7 +82,7 @@ extern "C" wcsim_status wcsim_convolve_noalloc(const wcsim_geometry* geom, const
     if (n_fw < geom->n_wires || n_ft < geom->n_ticks || n_ft > kMaxFftN || n_fw > kMaxWireN)
         return report_error(WCSIM_ESHAPE, "spectrum size smaller than the frame or too large");
 
-    ConvDims d;
+    ConvDims d{};
     d.n_w = geom->n_wires;
     d.n_imp = geom->n_imp;
     d.n_t = geom->n_ticks;

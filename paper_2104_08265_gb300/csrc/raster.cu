@@ -134,14 +134,15 @@ __device__ __forceinline__ void box_muller4(uint4 x, float z[4])
     z[3] = -rb * sb;
 }
 
-__global__ void __launch_bounds__(kWarps * 32)
-k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
+// The depos [blk * 64, blk * 64 + 64) of one event, by one CTA.
+__device__ __forceinline__ void rasterize_block(const RasterConsts& c, const DepoArrays& d,
+                                                float* __restrict__ grid, int* flags, int64_t blk)
 {
     __shared__ Decision s_dec[kDepos];
     __shared__ float s_wp[kWarps][kWmax];
     __shared__ float s_wt[kWarps][kWmax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kDepos;
+    const int64_t base = blk * kDepos;
     if (threadIdx.x < kDepos) {
         Decision r;
         r.ok = 0;
@@ -218,6 +219,23 @@ k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(kWarps * 32)
+k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
+{
+    rasterize_block(c, d, grid, flags, blockIdx.x);
+}
+
+// Several events of one plane: CTA b belongs to the event whose block range holds b.
+__global__ void __launch_bounds__(kWarps * 32)
+k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
+{
+    int e = 0;
+    while (e + 1 < ev.n && ev.block_start[e + 1] <= (int)blockIdx.x) ++e;
+    c.key0 = ev.key0[e];
+    c.key1 = ev.key1[e];
+    rasterize_block(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
 }
 
 // Derivatives of the bin weight w = Phi(b') - Phi(a') (a', b' = edge offsets / sigma) with
@@ -379,6 +397,17 @@ cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* 
     if (d.n <= 0) return cudaSuccess;
     const int64_t blocks = (d.n + kDepos - 1) / kDepos;
     k_rasterize<<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, grid, flags);
+    return cudaGetLastError();
+}
+
+int rasterize_blocks(int64_t n_depos) { return (int)((n_depos + kDepos - 1) / kDepos); }
+
+cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev, int* flags,
+                                   cudaStream_t s)
+{
+    const int blocks = ev.block_start[ev.n];
+    if (blocks <= 0) return cudaSuccess;
+    k_rasterize_batch<<<blocks, kWarps * 32, 0, s>>>(c, ev, flags);
     return cudaGetLastError();
 }
 

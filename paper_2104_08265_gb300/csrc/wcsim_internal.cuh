@@ -39,10 +39,29 @@ struct DepoArrays {
     int64_t n;
 };
 
+constexpr int kMaxBatch = 64;          // events per batched launch
+
+// Per-event inputs of a batched rasterization, passed by value.
+struct BatchEvents {
+    int32_t n;
+    int32_t block_start[kMaxBatch + 1];  // first CTA of each event (prefix sum)
+    DepoArrays d[kMaxBatch];
+    float* grid[kMaxBatch];
+    uint32_t key0[kMaxBatch], key1[kMaxBatch];
+};
+
+struct WavePtrs {
+    float* p[kMaxBatch];
+};
+
 cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* grid,
                              int* flags, cudaStream_t s);
 cudaError_t launch_windows(const RasterConsts& c, const DepoArrays& d, int32_t* out,
                            int* flags, cudaStream_t s);
+// Rasterize several events of one plane in one launch (c.key0/key1 ignored: per event).
+cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev, int* flags,
+                                   cudaStream_t s);
+int rasterize_blocks(int64_t n_depos);
 // Adjoint of drift + rasterization (mean path, windows fixed): dgrid -> per-depo and global
 // gradients (dglobal must be zeroed by the caller).
 cudaError_t launch_depo_adjoint(const RasterConsts& c, const DepoArrays& d, const float* dgrid,
@@ -90,7 +109,11 @@ struct ConvDims {
     int32_t nh;                // n_ft / 2 + 1
     int32_t nkb;               // ceil(nh / kBlockCols)
     int32_t rows_variant;      // time-axis forward kernel: 0 direct loads, 1 bulk-staged
+    // Batched runs: event e's grid, time-axis spectra and wire-summed spectra start
+    // e * ev_grid, e * ev_shat and e * ev_mt elements after the first event's.
+    int64_t ev_grid, ev_shat, ev_mt;
 };
+
 
 __host__ __device__ inline int64_t blk_index(int kt, int w, int n)
 {
@@ -104,6 +127,9 @@ cudaError_t launch_make_hermitian(const ConvDims& d, const float2* resp, float2*
 // [n_imp][nkb][n_w][4].
 cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* grid,
                             float2* shat, int* flags, cudaStream_t s);
+// Same for n_ev events laid out with the ConvDims event strides (direct kernel).
+cudaError_t launch_rows_r2c_batch(const ConvDims& d, const FftPlan& pt, const float* grid,
+                                  float2* shat, int n_ev, cudaStream_t s);
 // Per block of time frequencies: wire FFT of each S_j, times H_j, summed over j, inverse
 // wire FFT; writes Mt blocked [nkb][n_w][4].
 cudaError_t launch_wire_pass(const ConvDims& d, const FftPlan& pw, const float2* shat,
@@ -115,7 +141,7 @@ bool wire_warp_supported(int n_fw);
 // b < 32) and at b * M + a, FP64 rounded to FP32.  Device allocation owned by the caller.
 cudaError_t wire_warp_twiddles(int n_fw, float2** dev);
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
-                             const float2* H, float2* mt, cudaStream_t s);
+                             const float2* H, float2* mt, cudaStream_t s, int n_ev = 1);
 // Adjoint of the wire pass (n_fw = 32 M): reads the time-axis spectra of the forward grid
 // (shat) and of G (gt, blocked [nkb][n_w][4]); overwrites shat with the time-axis spectra
 // of dL/dS and, if dR is not null, writes dL/dR_j (full [n_imp][n_fw][n_ft] layout).
@@ -128,6 +154,8 @@ cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const flo
 // Time-axis complex-to-real inverse FFT of the Hermitian half rows of Mt -> wave.
 cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* mt,
                             float* wave, cudaStream_t s);
+cudaError_t launch_rows_c2r_batch(const ConvDims& d, const FftPlan& pt, const float2* mt,
+                                  const WavePtrs& waves, int n_ev, cudaStream_t s);
 
 // Streaming multiprocessors of the current device (cached).
 int sm_count();

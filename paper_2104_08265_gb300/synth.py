@@ -159,7 +159,7 @@ def _electronics(tick_us: float, n: int, tau_s: float = 0.5) -> np.ndarray:
 
 def make_response(geom: Geometry, kind: str = "collection", n_fw: int | None = None,
                   n_ft: int | None = None, span_wires: int = 10, span_ticks: int = 200,
-                  sigma_f_us: float = 1.0, t_c_us: float = 10.0) -> np.ndarray:
+                  sigma_f_us: float = 1.0, t_c_us: float = 10.0, backend: str = "numpy"):
     """Synthetic response spectra R_j(omega_x, omega_t), complex64 [n_imp][n_fw][n_ft].
 
     Field response per impact row j and wire offset dw in [-span, span]:
@@ -169,6 +169,8 @@ def make_response(geom: Geometry, kind: str = "collection", n_fw: int | None = N
     4th-order semi-Gaussian shaper (t/tau)^4 exp(-t/tau), tau = 0.5 us (2 us peaking),
     normalised to unit sum, truncated to ``span_ticks`` ticks, placed at
     (dw mod n_fw, tick) and transformed with a float64 2D FFT, then rounded to complex64.
+    backend="torch" does the float64 FFT with torch on the current CUDA device and returns
+    a CUDA complex64 tensor (same values up to float64 rounding; for large benchmark planes).
     """
     n_fw = geom.n_wires if n_fw is None else n_fw
     n_ft = geom.n_ticks if n_ft is None else n_ft
@@ -183,14 +185,21 @@ def make_response(geom: Geometry, kind: str = "collection", n_fw: int | None = N
     else:
         raise ValueError(kind)
     ft = np.convolve(ft, h)[:nt]
-    out = np.empty((geom.n_imp, n_fw, n_ft), dtype=np.complex64)
+    if backend == "torch":
+        import torch
+        out = torch.empty((geom.n_imp, n_fw, n_ft), dtype=torch.complex64, device="cuda")
+    else:
+        out = np.empty((geom.n_imp, n_fw, n_ft), dtype=np.complex64)
     for j in range(geom.n_imp):
         off = ((j + 0.5) / geom.n_imp - 0.5) * geom.pitch_mm
         real = np.zeros((n_fw, n_ft), dtype=np.float64)
         for dw in range(-span_wires, span_wires + 1):
             x = dw * geom.pitch_mm - off
             real[dw % n_fw, :nt] += ft * math.exp(-abs(x) / geom.pitch_mm)
-        out[j] = np.fft.fft2(real).astype(np.complex64)
+        if backend == "torch":
+            out[j] = torch.fft.fft2(torch.from_numpy(real).cuda()).to(torch.complex64)
+        else:
+            out[j] = np.fft.fft2(real).astype(np.complex64)
     return out
 
 
@@ -202,12 +211,33 @@ class Workload:
     description: str
 
 
+def batch_events(rng: np.random.Generator, n_events: int = 64, lo: float = 1e3, hi: float = 5e5,
+                 wires=(480, 800, 960), ticks=(2000, 6000, 9600), scale: float = 1.0):
+    """Independent events for a batched run: each draws a plane (wires x ticks uniform from
+    the lists, 4.7 mm pitch, 10 impacts, collection or induction response) and a
+    log-uniform depo count in [lo, hi] (times `scale`) on tracks of up to 2500 depos with
+    drift time uniform in [0, 0.75 n_ticks tick]."""
+    events = []
+    for _ in range(n_events):
+        g = Geometry(n_wires=int(rng.choice(wires)), n_imp=10, n_ticks=int(rng.choice(ticks)),
+                     pitch_mm=4.7)
+        kind = "collection" if rng.uniform() < 0.5 else "induction"
+        n = max(1, int(round(math.exp(rng.uniform(math.log(lo), math.log(hi))) * scale)))
+        n_tracks = max(1, -(-n // 2500))
+        d = track_depos(rng, n_tracks, -(-n // n_tracks), g.n_wires * g.pitch_mm,
+                        0.75 * g.n_ticks * g.tick_us)
+        d = d.subset(slice(0, n))
+        events.append((g, kind, d))
+    return events
+
+
 # Workload table.  Index i is seeded with 1000 + i (depos) and 0x5EED0000 + i (fluctuation).
 WORKLOADS: Dict[str, int] = {
     "plane128-2k": 0,          # 128 wires x 1024 ticks, 2,000 depos, fluctuation off
     "plane960-100k": 1,        # 960 wires x 6000 ticks, 100,000 depos, fluctuation on
     "event3p-1m": 2,           # 800 + 800 + 960 wires x 6000 ticks, 1,000,000 depos
     "fit960-100k": 3,          # 960 x 6000 plane, 100,000 depos, fluctuation off (fit target)
+    "batch64": 4,              # 64 events, mixed planes, log-uniform 1e3..5e5 depos
 }
 
 
@@ -246,4 +276,8 @@ def make_workload(name: str, n_depos: int | None = None) -> Workload:
             prm = DriftParams(fluctuate=1, seed=fseed, plane_id=pid)
             planes.append((g, prm, kind, d))
         return Workload(name, planes, "3 planes (800 U, 800 V, 960 W) x 6000 ticks")
+    if name == "batch64":
+        evs = batch_events(rng, 64, scale=1.0 if n_depos is None else n_depos / 5.1e6)
+        planes = [(g, DriftParams(fluctuate=1, seed=fseed), kind, d) for g, kind, d in evs]
+        return Workload(name, planes, "64 events, planes 480/800/960 wires x 2000/6000/9600 ticks")
     raise KeyError(name)

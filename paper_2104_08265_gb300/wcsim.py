@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         "wcsim_convolve_adjoint": [vp, vp, vp, vp, vp, vp],
         "wcsim_rasterize_adjoint": [vp, P(CDepos), vp, P(CDepoGrads), vp],
         "wcsim_run_backward": [vp, P(CDepos), vp, P(CDepoGrads), vp, vp],
+        "wcsim_batch_run": [i32, P(vp), P(CDepos), P(vp), vp],
+        "wcsim_plane_reserve_batch": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -318,3 +320,35 @@ def convolve_noalloc(geom: Geometry, response, grid, out=None, n_fw: int = 0, n_
                                        grid.contiguous().data_ptr(), out.data_ptr(),
                                        _stream_handle(stream)))
     return out
+
+
+MAX_BATCH = 64
+
+
+class Batch:
+    """A fixed list of events (plane, device depos, output waveform) run with one
+    wcsim_batch_run call.  Holds the marshalled C arrays so that the call can be repeated
+    (or recorded in a CUDA graph) without rebuilding them."""
+
+    def __init__(self, planes, depos, waves=None):
+        import torch
+        assert len(planes) == len(depos) <= MAX_BATCH
+        self.planes, self.depos = list(planes), list(depos)
+        if waves is None:
+            waves = [torch.empty((p.geom.n_wires, p.geom.n_ticks), dtype=torch.float32,
+                                 device="cuda") for p in self.planes]
+        self.waves = list(waves)
+        n = len(self.planes)
+        self._p = (ctypes.c_void_p * n)(*[p.handle.value for p in self.planes])
+        self._d = (CDepos * n)(*[d.c for d in self.depos])
+        self._w = (ctypes.c_void_p * n)(*[w.data_ptr() for w in self.waves])
+        counts = {}
+        for p in self.planes:
+            counts[id(p)] = counts.get(id(p), 0) + 1
+        for p in {id(p): p for p in self.planes}.values():
+            check(lib().wcsim_plane_reserve_batch(p.handle, counts[id(p)]))
+
+    def run(self, stream=None):
+        check(lib().wcsim_batch_run(len(self.planes), self._p, self._d, self._w,
+                                    _stream_handle(stream)))
+        return self.waves
