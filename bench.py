@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-event batched run (wcsim_batch_run vs 64 wcsim_run calls)")
     ap.add_argument("--soak-s", type=float, default=0.5,
@@ -322,6 +323,7 @@ def run_gpu(args):
 
     plane = wcsim.Plane(g, prm, torch.from_numpy(R).cuda())
     dd = wcsim.DeviceDepos.from_host(d)
+    tune = None if args.no_autotune else plane.autotune(dd)
     wave = torch.empty((g.n_wires, g.n_ticks), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -480,6 +482,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "cufft_comparison": cufft,
         "batch64": batch,
+        "autotune": tune,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

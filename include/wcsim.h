@@ -167,6 +167,24 @@ wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
                                 const float* grad_wave, wcsim_depo_grads* grads,
                                 void* grad_resp_c64, void* stream);
 
+/* Choices and best times (ms) found by wcsim_plane_autotune. */
+typedef struct {
+    int32_t time_radix[8];     /* radices of the time-axis FFT plan, in pass order, 0-padded */
+    int32_t rows_variant;      /* time-axis forward kernel: 0 direct loads, 1 bulk-staged */
+    int32_t wire_variant;      /* wire pass: 0 one warp per time frequency, 1 block-level */
+    int32_t depos_per_block;   /* rasterization CTA size: 32, 64 or 128 depos */
+    int32_t candidates_timed;  /* configurations timed */
+    float ms_rasterize, ms_rows, ms_wire;
+} wcsim_tune_report;
+
+/* Time the kernel variants of this plane on `depos` (DEVICE) and keep the fastest: the
+ * rasterization CTA size, the radices and order of the time-axis FFT plan (the cheapest
+ * plans with the fewest passes), the time-axis forward kernel and the wire-pass kernel.
+ * Results are unchanged up to floating-point rounding order.  Synchronizes `stream`,
+ * allocates temporary plan tables, overwrites the plane's scratch; report may be NULL. */
+wcsim_status wcsim_plane_autotune(wcsim_plane* plane, const wcsim_depos* depos, void* stream,
+                                  wcsim_tune_report* report);
+
 /* Maximum events of one wcsim_batch_run call. */
 #define WCSIM_MAX_BATCH 64
 

@@ -76,6 +76,9 @@ struct wcsim_plane {
     float2* bmt = nullptr;
     int32_t bcap = 0;
     int device = 0;
+    bool grid_clean = false;    // the plane's grid is all zero (consume-and-clear state)
+    bool wire_block = false;    // autotuned: use the block-level wire pass even if the warp one fits
+    int32_t kd = 64;            // autotuned: depos per rasterization CTA
     bool timing = false;
     cudaEvent_t ev[kStages + 1] = {};
     bool ev_valid = false;
@@ -150,6 +153,7 @@ RasterConsts make_consts(const wcsim_plane* pl)
     c.key0 = (uint32_t)p.seed;
     c.key1 = (uint32_t)(p.seed >> 32);
     c.plane_id = p.plane_id;
+    c.depos_per_block = pl->kd;
     c.DL = p.DL_cm2_s;
     c.DT = p.DT_cm2_s;
     c.v = p.v_mm_per_us;
@@ -200,7 +204,7 @@ wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaSt
     if ((e = launch_rows_r2c(pl->dims, pl->pt, grid, pl->shat, pl->flags, s)))
         return cuda_fail(e, "rows_r2c launch");
     mark(pl, first_mark, s);
-    if (pl->tw_warp)
+    if (pl->tw_warp && !pl->wire_block)
         e = launch_wire_warp(pl->dims, pl->tw_warp, pl->shat, pl->H, pl->mt, s);
     else
         e = launch_wire_pass(pl->dims, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s);
@@ -262,12 +266,12 @@ wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_d
         const uint64_t seed = pl->prm.seed + (uint64_t)idx[i];     // per-event stream
         ev.key0[i] = (uint32_t)seed;
         ev.key1[i] = (uint32_t)(seed >> 32);
-        ev.block_start[i + 1] = ev.block_start[i] + rasterize_blocks(dp->n);
+        ev.block_start[i + 1] = ev.block_start[i] + rasterize_blocks(dp->n, c.depos_per_block);
     }
     if ((e = launch_rasterize_batch(c, ev, pl->flags, s))) return cuda_fail(e, "batch rasterize launch");
     if ((e = launch_rows_r2c_batch(d, pl->pt, pl->bgrid, pl->bshat, k, s)))
         return cuda_fail(e, "batch rows_r2c launch");
-    if (pl->tw_warp) {
+    if (pl->tw_warp && !pl->wire_block) {
         if ((e = launch_wire_warp(d, pl->tw_warp, pl->bshat, pl->H, pl->bmt, s, k)))
             return cuda_fail(e, "batch wire launch");
     } else {
@@ -431,13 +435,23 @@ wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, v
     cudaStream_t s = (cudaStream_t)stream;
     const ConvDims& d = pl->dims;
     mark(pl, 0, s);
-    cudaError_t e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
-    if (e) return cuda_fail(e, "grid reset");
+    cudaError_t e = cudaSuccess;
+    if (!pl->grid_clean) {
+        e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
+        if (e) return cuda_fail(e, "grid reset");
+    }
+    pl->grid_clean = false;
     mark(pl, 1, s);
     e = launch_rasterize(make_consts(pl), depo_arrays(depos), pl->grid, pl->flags, s);
     if (e) return cuda_fail(e, "rasterize launch");
     mark(pl, 2, s);
-    return do_convolve(pl, pl->grid, wave, s, 3);
+    // the time-axis transform reads the plane's own grid once: it clears it as it goes
+    // (the direct kernel; the staged one reads through bulk copies and leaves it as is)
+    pl->dims.clear_input = (pl->dims.rows_variant == 0);
+    st = do_convolve(pl, pl->grid, wave, s, 3);
+    pl->dims.clear_input = 0;
+    if (st == WCSIM_OK && pl->dims.rows_variant == 0) pl->grid_clean = true;
+    return st;
 }
 
 wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, const float* grid,
@@ -497,8 +511,12 @@ wcsim_status wcsim_run_backward(wcsim_plane* pl, const wcsim_depos* depos, const
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
     const ConvDims& d = pl->dims;
-    cudaError_t e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
-    if (e) return cuda_fail(e, "grid reset");
+    cudaError_t e = cudaSuccess;
+    if (!pl->grid_clean) {
+        e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
+        if (e) return cuda_fail(e, "grid reset");
+    }
+    pl->grid_clean = false;             // the grid ends up holding dL/dS
     RasterConsts c = make_consts(pl);
     c.fluctuate = 0;                    // the gradient is that of the mean waveform
     if ((e = launch_rasterize(c, depo_arrays(depos), pl->grid, pl->flags, s)))
@@ -548,6 +566,126 @@ wcsim_status wcsim_batch_run(int32_t n_events, wcsim_plane* const* planes,
         wcsim_status st = run_group(planes[i], k, idx, depos, waves, s);
         if (st) return st;
     }
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_autotune(wcsim_plane* pl, const wcsim_depos* depos, void* stream,
+                                  wcsim_tune_report* report)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    wcsim_status st = check_depos(depos);
+    if (st) return st;
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    ConvDims& d = pl->dims;
+    const size_t grid_bytes = (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return fail(WCSIM_ECUDA, "event creation failed");
+    cudaError_t err = cudaSuccess;
+    int timed = 0;
+    // best of 5 after 2 warm-ups, in ms; sets err on a launch failure
+    auto time_it = [&](auto fn) -> float {
+        for (int i = 0; i < 2 && !err; ++i) err = fn();
+        float best = 1e30f;
+        for (int i = 0; i < 5 && !err; ++i) {
+            cudaEventRecord(e0, s);
+            err = fn();
+            cudaEventRecord(e1, s);
+            if (!err) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (!err) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) best = ms;
+        }
+        ++timed;
+        return best;
+    };
+    wcsim_tune_report rep{};
+    // 1. rasterization CTA size
+    {
+        const int kds[3] = {32, 64, 128};
+        float best = 1e30f;
+        for (int kd : kds) {
+            pl->kd = kd;
+            RasterConsts c = make_consts(pl);
+            const float ms = time_it([&] { return launch_rasterize(c, depo_arrays(depos), pl->grid, pl->flags, s); });
+            if (ms < best) { best = ms; rep.depos_per_block = kd; }
+        }
+        pl->kd = rep.depos_per_block;
+        rep.ms_rasterize = best;
+        // a representative grid for the FFT stages
+        if (!err) err = cudaMemsetAsync(pl->grid, 0, grid_bytes, s);
+        if (!err) err = launch_rasterize(make_consts(pl), depo_arrays(depos), pl->grid, pl->flags, s);
+    }
+    // 2. time-axis plan: forward over the grid + inverse (into the grid's first rows)
+    int32_t cand[8][kMaxPasses], cnp[8];
+    const int nc = err ? 0 : fft_plan_candidates(d.n_ft, cand, cnp, 8);
+    {
+        float best = 1e30f;
+        int bi = -1;
+        FftPlan bp{};
+        float2* btw = nullptr;
+        const int keep_variant = d.rows_variant;
+        d.rows_variant = 0;
+        for (int ci = 0; ci < nc && !err; ++ci) {
+            FftPlan p;
+            float2* tw = nullptr;
+            if ((err = fft_plan_create_radices(d.n_ft, cand[ci], cnp[ci], &p, &tw))) break;
+            const float ms = time_it([&] { return launch_rows_r2c(d, p, pl->grid, pl->shat, pl->flags, s); }) +
+                             time_it([&] { return launch_rows_c2r(d, p, pl->mt, pl->grid, s); });
+            if (!err && ms < best) {
+                best = ms;
+                bi = ci;
+                cudaFree(btw);
+                bp = p;
+                btw = tw;
+            } else {
+                cudaFree(tw);
+            }
+        }
+        d.rows_variant = keep_variant;
+        if (bi >= 0 && !err) {
+            cudaFree(pl->tw_t);
+            pl->pt = bp;
+            pl->tw_t = btw;
+        } else {
+            cudaFree(btw);
+        }
+        for (int i = 0; i < pl->pt.npass && i < 8; ++i) rep.time_radix[i] = pl->pt.radix[i];
+        rep.ms_rows = best;
+    }
+    // 3. time-axis forward kernel: direct (clears its input) vs staged (+ a grid reset)
+    if (!err) {
+        if (!err) err = cudaMemsetAsync(pl->grid, 0, grid_bytes, s);
+        if (!err) err = launch_rasterize(make_consts(pl), depo_arrays(depos), pl->grid, pl->flags, s);
+        const int keep = d.rows_variant;
+        d.rows_variant = 0;
+        const float direct = time_it([&] { return launch_rows_r2c(d, pl->pt, pl->grid, pl->shat, pl->flags, s); });
+        d.rows_variant = 1;
+        const float staged = time_it([&] {
+            cudaError_t x = cudaMemsetAsync(pl->grid, 0, grid_bytes, s);
+            return x ? x : launch_rows_r2c(d, pl->pt, pl->grid, pl->shat, pl->flags, s);
+        });
+        d.rows_variant = (staged < direct) ? 1 : 0;
+        (void)keep;
+        rep.rows_variant = d.rows_variant;
+    }
+    // 4. wire pass: warp-per-column vs block-level
+    if (!err) {
+        float warp = 1e30f, block;
+        if (pl->tw_warp)
+            warp = time_it([&] { return launch_wire_warp(d, pl->tw_warp, pl->shat, pl->H, pl->mt, s); });
+        block = time_it([&] { return launch_wire_pass(d, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s); });
+        pl->wire_block = !(warp <= block);
+        rep.wire_variant = pl->wire_block ? 1 : 0;
+        rep.ms_wire = pl->wire_block ? block : warp;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    pl->grid_clean = false;
+    if (err) return cuda_fail(err, "autotune");
+    rep.candidates_timed = timed;
+    if (report) *report = rep;
     return WCSIM_OK;
 }
 

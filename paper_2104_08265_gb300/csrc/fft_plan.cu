@@ -143,3 +143,117 @@ int fft_plan_describe(int n, FftPlan* plan)
 }
 
 }  // namespace wcsim
+
+namespace wcsim {
+
+namespace {
+
+void collect(int n, int depth, int max_depth, int* cur, double cost, int (*out)[kMaxPasses],
+             int* lens, double* costs, int* count, int cap)
+{
+    if (n == 1) {
+        // keep the `cap` cheapest (insertion into a short sorted list)
+        int pos = *count < cap ? (*count)++ : cap - 1;
+        if (pos == cap - 1 && *count == cap && costs[pos] <= cost && lens[pos] > 0) return;
+        while (pos > 0 && costs[pos - 1] > cost) {
+            costs[pos] = costs[pos - 1];
+            lens[pos] = lens[pos - 1];
+            for (int i = 0; i < kMaxPasses; ++i) out[pos][i] = out[pos - 1][i];
+            --pos;
+        }
+        costs[pos] = cost;
+        lens[pos] = depth;
+        for (int i = 0; i < depth; ++i) out[pos][i] = cur[i];
+        return;
+    }
+    if (depth >= max_depth) return;
+    const int nr = (int)(sizeof(kRadices) / sizeof(kRadices[0]));
+    // non-increasing radices: each multiset once
+    for (int i = nr - 1; i >= 0; --i) {
+        const int r = kRadices[i].r;
+        if (n % r || (depth > 0 && r > cur[depth - 1])) continue;
+        cur[depth] = r;
+        collect(n / r, depth + 1, max_depth, cur, cost + kRadices[i].cost, out, lens, costs, count, cap);
+    }
+}
+
+}  // namespace
+
+int fft_plan_candidates(int n, int32_t (*radix)[kMaxPasses], int32_t* npass, int max_out)
+{
+    int32_t best[kMaxPasses], nb;
+    if (!fft_factor(n, best, &nb)) return 0;
+    int count = 0;
+    for (int i = 0; i < nb && count < max_out; ++i) radix[count][i] = best[i];
+    npass[count++] = nb;
+    if (nb <= 1) return count;
+    // other radix sets with the same number of passes, cheapest first, each tried with its
+    // radices in decreasing order and, where it has one, a radix-16 first pass
+    const int cap = 8;
+    int out[cap][kMaxPasses], lens[cap];
+    double costs[cap];
+    int cnt = 0, cur[kMaxPasses];
+    for (int i = 0; i < cap; ++i) { lens[i] = 0; costs[i] = 1e300; }
+    collect(n, 0, nb, cur, 0.0, out, lens, costs, &cnt, cap);
+    for (int c = 0; c < cnt && count < max_out; ++c) {
+        for (int variant = 0; variant < 2 && count < max_out; ++variant) {
+            int32_t r[kMaxPasses];
+            for (int i = 0; i < lens[c]; ++i) r[i] = out[c][i];     // decreasing already
+            if (variant == 1) {
+                int k = -1;
+                for (int i = 0; i < lens[c]; ++i) if (r[i] == 16) k = i;
+                if (k <= 0) continue;
+                for (int i = k; i > 0; --i) r[i] = r[i - 1];
+                r[0] = 16;
+            }
+            bool dup = false;
+            for (int q = 0; q < count && !dup; ++q) {
+                if (npass[q] != lens[c]) continue;
+                bool same = true;
+                for (int i = 0; i < lens[c]; ++i) same = same && radix[q][i] == r[i];
+                dup = same;
+            }
+            if (dup) continue;
+            for (int i = 0; i < lens[c]; ++i) radix[count][i] = r[i];
+            npass[count++] = lens[c];
+        }
+    }
+    return count;
+}
+
+cudaError_t fft_plan_create_radices(int n, const int32_t* radices, int npass, FftPlan* plan,
+                                    float2** dev_tw)
+{
+    FftPlan p{};
+    p.n = n;
+    p.npass = npass;
+    int prod = 1;
+    for (int i = 0; i < npass; ++i) { p.radix[i] = radices[i]; prod *= radices[i]; }
+    if (prod != n || npass < 1 || npass > kMaxPasses) return cudaErrorInvalidValue;
+    std::vector<float2> tw;
+    int ns = 1;
+    for (int i = 0; i < p.npass; ++i) {
+        const int R = p.radix[i];
+        p.ns[i] = ns;
+        p.tw_off[i] = (int32_t)tw.size();
+        p.ns_magic[i] = magic_for(ns);
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < ns; ++k) {
+                const double a = -2.0 * M_PI * (double)r * (double)k / ((double)ns * R);
+                tw.push_back(make_float2((float)cos(a), (float)sin(a)));
+            }
+        ns *= R;
+    }
+    if (tw.empty()) tw.push_back(make_float2(1.f, 0.f));
+    float2* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, tw.size() * sizeof(float2));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(d, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return e; }
+    p.tw = d;
+    *plan = p;
+    *dev_tw = d;
+    return cudaSuccess;
+}
+
+}  // namespace wcsim

@@ -163,6 +163,13 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
     shat += blockIdx.y * d.ev_shat;
     const RealPairLd src{grid + r0 * d.n_t, has1 ? grid + (r0 + 1) * d.n_t : nullptr, d.n_t};
     const float2* z = run_plan<false, 0>(p, src, X, Y);
+    if (d.clear_input) {
+        // the first pass (inside run_plan, before its barrier) has read both rows: leave
+        // the grid zero for the next rasterization (consume and clear)
+        float* g0 = const_cast<float*>(grid) + r0 * d.n_t;
+        const int len = (has1 ? 2 : 1) * d.n_t;
+        for (int n = threadIdx.x; n < len; n += blockDim.x) g0[n] = 0.f;
+    }
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
 

@@ -134,16 +134,18 @@ __device__ __forceinline__ void box_muller4(uint4 x, float z[4])
     z[3] = -rb * sb;
 }
 
-// The depos [blk * 64, blk * 64 + 64) of one event, by one CTA.
+// The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps.
+template <int KD>
 __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const DepoArrays& d,
                                                 float* __restrict__ grid, int* flags, int64_t blk)
 {
-    __shared__ Decision s_dec[kDepos];
+    static_assert(KD <= kWarps * 32, "one deciding thread per depo");
+    __shared__ Decision s_dec[KD];
     __shared__ float s_wp[kWarps][kWmax];
     __shared__ float s_wt[kWarps][kWmax];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = blk * kDepos;
-    if (threadIdx.x < kDepos) {
+    const int64_t base = blk * KD;
+    if (threadIdx.x < KD) {
         Decision r;
         r.ok = 0;
         const int64_t i = base + threadIdx.x;
@@ -159,7 +161,7 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     float* wp = s_wp[warp];
     float* wt = s_wt[warp];
 
-    for (int i = warp; i < kDepos; i += kWarps) {
+    for (int i = warp; i < KD; i += kWarps) {
         const Decision dd = s_dec[i];
         if (!dd.ok || !(dd.qatt > 0.0f)) continue;    // nothing, or Q' underflowed
         // u = offset_in_bins * bin / (sqrt(2) sigma); sigma == 0 puts all weight in the
@@ -221,13 +223,15 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     }
 }
 
+template <int KD>
 __global__ void __launch_bounds__(kWarps * 32)
 k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
 {
-    rasterize_block(c, d, grid, flags, blockIdx.x);
+    rasterize_block<KD>(c, d, grid, flags, blockIdx.x);
 }
 
 // Several events of one plane: CTA b belongs to the event whose block range holds b.
+template <int KD>
 __global__ void __launch_bounds__(kWarps * 32)
 k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
 {
@@ -235,7 +239,7 @@ k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
     while (e + 1 < ev.n && ev.block_start[e + 1] <= (int)blockIdx.x) ++e;
     c.key0 = ev.key0[e];
     c.key1 = ev.key1[e];
-    rasterize_block(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
+    rasterize_block<KD>(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
 }
 
 // Derivatives of the bin weight w = Phi(b') - Phi(a') (a', b' = edge offsets / sigma) with
@@ -395,19 +399,31 @@ cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* 
                              int* flags, cudaStream_t s)
 {
     if (d.n <= 0) return cudaSuccess;
-    const int64_t blocks = (d.n + kDepos - 1) / kDepos;
-    k_rasterize<<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, grid, flags);
+    const unsigned blocks = (unsigned)rasterize_blocks(d.n, c.depos_per_block);
+    switch (c.depos_per_block) {
+        case 32: k_rasterize<32><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+        case 128: k_rasterize<128><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+        default: k_rasterize<64><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+    }
     return cudaGetLastError();
 }
 
-int rasterize_blocks(int64_t n_depos) { return (int)((n_depos + kDepos - 1) / kDepos); }
+int rasterize_blocks(int64_t n_depos, int depos_per_block)
+{
+    const int kd = (depos_per_block == 32 || depos_per_block == 128) ? depos_per_block : 64;
+    return (int)((n_depos + kd - 1) / kd);
+}
 
 cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev, int* flags,
                                    cudaStream_t s)
 {
     const int blocks = ev.block_start[ev.n];
     if (blocks <= 0) return cudaSuccess;
-    k_rasterize_batch<<<blocks, kWarps * 32, 0, s>>>(c, ev, flags);
+    switch (c.depos_per_block) {
+        case 32: k_rasterize_batch<32><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+        case 128: k_rasterize_batch<128><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+        default: k_rasterize_batch<64><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+    }
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ struct RasterConsts {
     int32_t fluctuate;
     uint32_t key0, key1, plane_id;
     double DL, DT, v, tau;                  // FP64 parameters for the global gradients
+    int32_t depos_per_block;                // rasterization CTA size: 32, 64 or 128 depos
 };
 
 struct DepoGrads {
@@ -61,7 +62,7 @@ cudaError_t launch_windows(const RasterConsts& c, const DepoArrays& d, int32_t* 
 // Rasterize several events of one plane in one launch (c.key0/key1 ignored: per event).
 cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev, int* flags,
                                    cudaStream_t s);
-int rasterize_blocks(int64_t n_depos);
+int rasterize_blocks(int64_t n_depos, int depos_per_block);
 // Adjoint of drift + rasterization (mean path, windows fixed): dgrid -> per-depo and global
 // gradients (dglobal must be zeroed by the caller).
 cudaError_t launch_depo_adjoint(const RasterConsts& c, const DepoArrays& d, const float* dgrid,
@@ -91,6 +92,12 @@ struct FftPlan {
 bool fft_factor(int n, int32_t* radix, int32_t* npass);
 // Build the plan and upload its twiddle table (FP64 host values rounded to FP32).
 cudaError_t fft_plan_create(int n, FftPlan* plan, float2** dev_tw);
+// Alternative plans for autotuning: the default first, then other radix sets with the
+// same pass count (decreasing order, and radix 16 first where present).  Returns the count.
+int fft_plan_candidates(int n, int32_t (*radix)[kMaxPasses], int32_t* npass, int max_out);
+// A plan with the given radices (in pass order) and its uploaded twiddle table.
+cudaError_t fft_plan_create_radices(int n, const int32_t* radices, int npass, FftPlan* plan,
+                                    float2** dev_tw);
 // The plan without its table (plan->tw left NULL); returns the table length in entries,
 // or -1 if n does not factor.  Allocates nothing.
 int fft_plan_describe(int n, FftPlan* plan);
@@ -109,6 +116,7 @@ struct ConvDims {
     int32_t nh;                // n_ft / 2 + 1
     int32_t nkb;               // ceil(nh / kBlockCols)
     int32_t rows_variant;      // time-axis forward kernel: 0 direct loads, 1 bulk-staged
+    int32_t clear_input;       // time-axis forward: write zeros over the rows it has read
     // Batched runs: event e's grid, time-axis spectra and wire-summed spectra start
     // e * ev_grid, e * ev_shat and e * ev_mt elements after the first event's.
     int64_t ev_grid, ev_shat, ev_mt;

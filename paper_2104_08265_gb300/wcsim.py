@@ -59,6 +59,13 @@ class CDepoGrads(ctypes.Structure):
 
 GRAD_NAMES = ("q", "p", "t", "sigma_L", "sigma_T")
 
+
+class CTuneReport(ctypes.Structure):
+    _fields_ = [("time_radix", ctypes.c_int32 * 8), ("rows_variant", ctypes.c_int32),
+                ("wire_variant", ctypes.c_int32), ("depos_per_block", ctypes.c_int32),
+                ("candidates_timed", ctypes.c_int32), ("ms_rasterize", ctypes.c_float),
+                ("ms_rows", ctypes.c_float), ("ms_wire", ctypes.c_float)]
+
 _lib = None
 
 
@@ -88,6 +95,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_rasterize_adjoint": [vp, P(CDepos), vp, P(CDepoGrads), vp],
         "wcsim_run_backward": [vp, P(CDepos), vp, P(CDepoGrads), vp, vp],
         "wcsim_batch_run": [i32, P(vp), P(CDepos), P(vp), vp],
+        "wcsim_plane_autotune": [vp, P(CDepos), vp, P(CTuneReport)],
         "wcsim_plane_reserve_batch": [vp, i32],
     }
     for name, args in sig.items():
@@ -281,6 +289,16 @@ class Plane:
         out = self._split_global(out)
         out["response"] = dR
         return out
+
+    def autotune(self, depos: DeviceDepos, stream=None) -> dict:
+        """Time kernel variants on `depos` and keep the fastest (see wcsim_plane_autotune)."""
+        r = CTuneReport()
+        check(lib().wcsim_plane_autotune(self._h, ctypes.byref(depos.c), _stream_handle(stream),
+                                         ctypes.byref(r)))
+        return {"time_radix": [x for x in r.time_radix if x], "rows_variant": r.rows_variant,
+                "wire_variant": r.wire_variant, "depos_per_block": r.depos_per_block,
+                "candidates_timed": r.candidates_timed, "ms_rasterize": r.ms_rasterize,
+                "ms_rows": r.ms_rows, "ms_wire": r.ms_wire}
 
     def windows(self, depos: DeviceDepos, stream=None):
         import torch

@@ -284,3 +284,35 @@ def test_stage_timing_reports_every_stage(W):
     t = pl.stage_times()
     assert set(t) == {"zero", "rasterize", "rows_r2c", "wire_pass", "rows_c2r"}
     assert all(v >= 0 for v in t.values()) and sum(t.values()) > 0
+
+
+def test_repeated_runs_leave_a_clean_grid(W):
+    """wcsim_run clears its grid while transforming it; a backward pass leaves it dirty and
+    the next run must reset it: every run of the same depos gives the same frame."""
+    import torch
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    pl = plane_for(W, g, prm, S.make_response(g, kind))
+    dd = to_dev(W, d)
+    ref = O.run(g, prm, S.make_response(g, kind), d)
+    outs = [pl.run(dd).cpu().numpy() for _ in range(3)]
+    pl.backward(dd, torch.ones((g.n_wires, g.n_ticks), device="cuda"))
+    outs.append(pl.run(dd).cpu().numpy())
+    for o in outs:
+        assert_close(o, ref, what="repeat")
+
+
+def test_autotune_picks_variants_without_changing_results(W):
+    wl = S.make_workload("plane960-100k", n_depos=20000)
+    g, prm, kind, d = wl.planes[0]
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    dd = to_dev(W, d)
+    rep = pl.autotune(dd)
+    prod = 1
+    for r in rep["time_radix"]:
+        prod *= r
+    assert prod == g.n_ticks and rep["depos_per_block"] in (32, 64, 128)
+    assert rep["candidates_timed"] >= 6 and rep["ms_rows"] > 0
+    got = pl.run(dd).cpu().numpy()
+    assert_close(got, O.run(g, prm, R, d), what="after autotune %s" % rep)
