@@ -375,6 +375,7 @@ def run_gpu(args):
     # ---- forward + backward (loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10,
     # lifetime 8 ms; the backward runs on the mean path and includes dL/dR)
     fb_ms = None
+    bwd_stages = None
     if not args.no_backward:
         import dataclasses
         tgt = dataclasses.replace(prm, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0, fluctuate=0)
@@ -393,13 +394,20 @@ def run_gpu(args):
         torch.cuda.synchronize()
         fs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         fe = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        plane.set_timing(True)
+        bwd_stage_ms = {k: [] for k in wcsim.BWD_STAGES}
         for i in range(args.steps):
             flush.zero_()
             fs[i].record(stream)
             fb_step()
             fe[i].record(stream)
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            for k, v in plane.stage_times(backward=True).items():
+                if k in bwd_stage_ms:
+                    bwd_stage_ms[k].append(v)
+        plane.set_timing(False)
         fb_ms = sum(s.elapsed_time(e) for s, e in zip(fs, fe)) / args.steps
+        bwd_stages = {k: float(np.mean(v)) for k, v in bwd_stage_ms.items()}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -465,6 +473,7 @@ def run_gpu(args):
         "plane_frames_per_s": {"fwd": ws * 1e3 / per_step,
                                "fwd_bwd": (ws * 1e3 / fb_ms) if fb_ms else None},
         "fwd_bwd_ms_per_step": fb_ms,
+        "backward_stages_ms": bwd_stages,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm,
                      "unit": "GB/s", "frac": ach / hbm, "traffic": ncu_traffic(dom),
                      "alg_bytes": sb[dom],

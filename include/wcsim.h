@@ -210,10 +210,13 @@ wcsim_status wcsim_plane_reserve_batch(wcsim_plane* plane, int32_t n_events);
  * WCSIM_OK. */
 wcsim_status wcsim_plane_check(wcsim_plane* plane, void* stream, int32_t* flags);
 
-/* Per-stage device time of the last compute call on this plane (CUDA events), when
- * enabled with wcsim_plane_set_timing(plane, 1).  ms[0..n) receives, in order: zero grid,
- * rasterize+scatter, time-axis forward FFT, wire-axis FFT x response x sum x inverse,
- * time-axis inverse FFT.  Synchronizes on the recorded events. */
+/* Per-stage device time of the last compute calls on this plane (CUDA events), when
+ * enabled with wcsim_plane_set_timing(plane, 1).  ms[0..n) receives, in order, the forward
+ * stages of the last wcsim_run / rasterize / convolve: zero grid, rasterize+scatter,
+ * time-axis forward FFT, wire-axis FFT x response x sum x inverse, time-axis inverse FFT;
+ * then (n up to 12) the stages of the last wcsim_run_backward: zero grid, mean-path
+ * rasterize, time-axis FFT of S, time-axis FFT of G, wire-axis adjoint, inverse time FFT of
+ * dL/dS, per-depo adjoint (zeros if none was recorded).  Synchronizes on the events. */
 wcsim_status wcsim_plane_set_timing(wcsim_plane* plane, int32_t enable);
 wcsim_status wcsim_plane_stage_times(wcsim_plane* plane, float* ms, int32_t n);
 

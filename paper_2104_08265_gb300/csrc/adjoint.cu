@@ -4,10 +4,10 @@
 // (scaled by 1/(n_fw n_ft)).  For a loss L with G = dL/dM:
 //   dL/dS_j = IFFT2(conj(H_j) FFT2(G))                (same unnormalised inverse, same scale)
 //   dL/dR_j = conj(FFT2(S_j)) FFT2(G) / (n_fw n_ft)    (complex-gradient convention dRe + i dIm)
-// wire_adjoint_warp: one warp per time frequency kt (n_fw = 32 M, the layout of the forward
-// warp kernel).  It transforms the column of G's time-axis spectrum along the wires once,
-// then for every j transforms S_j's column, writes dL/dR_j at (kw, kt) and its Hermitian
-// mirror (-kw, -kt), forms conj(H_j) G^ and transforms it back along the wires, overwriting
+// The wire-axis adjoint runs as two one-warp-per-time-frequency kernels (n_fw = 32 M, the
+// layout of the forward warp kernel), each doing one wire FFT per impact position: part A
+// transforms G's column once and, per j, S_j's column, writing dL/dR_j at (kw, kt) and its
+// Hermitian mirror (-kw, -kt); part B forms conj(H_j) G^ and transforms it back, overwriting
 // S_j's column with the time-axis spectrum of dL/dS_j.
 // rows_c2r_grid: the inverse time-axis FFT of those spectra for every grid row.
 #include <cuda_runtime.h>
@@ -49,59 +49,129 @@ __device__ __forceinline__ void warp_wire_fft(const float2* __restrict__ col, in
 }
 
 template <int M>
-__global__ void __launch_bounds__(kWarps * 32, 2)
-k_wire_adjoint_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ gt,
-                    float2* __restrict__ shat, const float2* __restrict__ H, float2* __restrict__ dR,
-                    float inv_n)
+__device__ __forceinline__ void load_twiddles(const float2* __restrict__ tw2, float2* s_twf,
+                                              float2* s_twi)
 {
     constexpr int N = 32 * M;
-    constexpr int TR = (33 * M > 32 * (M + 1)) ? 33 * M : 32 * (M + 1);
-    __shared__ float2 s_twf[N];
-    __shared__ float2 s_twi[N];
-    __shared__ float2 s_tr[kWarps][TR];
     for (int e = threadIdx.x; e < N; e += blockDim.x) {
         s_twf[e] = tw2[e];
-        s_twi[e] = tw2[N + e];
+        if (s_twi) s_twi[e] = tw2[N + e];
     }
     __syncthreads();
+}
+
+// Adjoint part A, one warp per time frequency kt: G^ = wire FFT of G's time-axis spectrum
+// (kept for part B in g2d, blocked [nkb][n_fw][4]); for every j, the wire FFT of S_j and
+// dL/dR_j(kw, kt) = conj(S^_j) G^ / n with its Hermitian mirror (-kw, -kt).  The four
+// columns of the CTA are staged in shared memory and written row by row (kw), so that each
+// row of dL/dR_j gets 4 adjacent values per store request group.
+template <int M>
+__global__ void __launch_bounds__(kWarps * 32, 3)
+k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ gt,
+                 const float2* __restrict__ shat, float2* __restrict__ g2d, float2* __restrict__ dR,
+                 float inv_n)
+{
+    constexpr int N = 32 * M;
+    __shared__ float2 s_twf[N];
+    __shared__ float2 s_tr[kWarps][33 * M];
+    // the CTA's output tile [kw][4], dynamic: N * kBlockCols float2
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float2* s_out = reinterpret_cast<float2*>(smraw);
+    load_twiddles<M>(tw2, s_twf, nullptr);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kb = blockIdx.x, c = warp, kt = kb * kBlockCols + c;
+    const int kb = blockIdx.x, c = warp, kt0 = kb * kBlockCols;
     float2* tr = s_tr[warp];
-
-    float2 g[32];                           // G^(kw = lane + M k1, kt), lanes < M
+    float2 g[32];
     warp_wire_fft<M>(gt + (int64_t)kb * d.n_w * kBlockCols + c, d.n_w, s_twf, tr, lane, g);
-    const bool dr_here = (dR != nullptr) && (kt < d.nh);
-    const bool mirror = dr_here && kt >= 1 && (d.n_ft - kt) >= d.nh;
-
+    if (lane < M) {
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) s_out[(lane + M * k1) * kBlockCols + c] = g[k1];
+    }
+    __syncthreads();
+    {   // the block of G's 2D spectrum, contiguous 16-byte stores
+        const float4* src = reinterpret_cast<const float4*>(s_out);
+        float4* dst = reinterpret_cast<float4*>(g2d + (int64_t)kb * N * kBlockCols);
+        for (int e = threadIdx.x; e < N * kBlockCols / 2; e += blockDim.x) dst[e] = src[e];
+    }
+    if (dR == nullptr || kt0 >= d.nh) return;            // uniform per CTA
+    const bool vec = (d.n_ft % 2) == 0 && (reinterpret_cast<uintptr_t>(dR) & 15) == 0;
     for (int j = 0; j < d.n_imp; ++j) {
         const int64_t blk = (int64_t)j * d.nkb + kb;
-        float2* col = shat + blk * d.n_w * kBlockCols + c;
         float2 u[32];
-        warp_wire_fft<M>(col, d.n_w, s_twf, tr, lane, u);
+        __syncthreads();                                  // the output tile is read out
+        warp_wire_fft<M>(shat + blk * d.n_w * kBlockCols + c, d.n_w, s_twf, tr, lane, u);
         if (lane < M) {
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1)
+                s_out[(lane + M * k1) * kBlockCols + c] =
+                    make_float2(inv_n * (u[k1].x * g[k1].x + u[k1].y * g[k1].y),
+                                inv_n * (u[k1].x * g[k1].y - u[k1].y * g[k1].x));
+        }
+        __syncthreads();
+        float2* dRj = dR + (int64_t)j * N * d.n_ft;
+        // direct values (kw, kt0 + cc), kt < nh: pairs of columns as 16-byte stores
+        for (int e = threadIdx.x; e < N * 2; e += blockDim.x) {
+            const int kw = e >> 1, cc = (e & 1) * 2, kt = kt0 + cc;
+            const float2 a = s_out[kw * kBlockCols + cc], b = s_out[kw * kBlockCols + cc + 1];
+            float2* row = dRj + (int64_t)kw * d.n_ft;
+            if (vec && kt + 1 < d.nh) {
+                *reinterpret_cast<float4*>(row + kt) = make_float4(a.x, a.y, b.x, b.y);
+            } else {
+                if (kt < d.nh) row[kt] = a;
+                if (kt + 1 < d.nh) row[kt + 1] = b;
+            }
+        }
+        // mirrors (-kw, n_ft - kt) for 1 <= kt <= n_ft - nh
+        for (int e = threadIdx.x; e < N * kBlockCols; e += blockDim.x) {
+            const int kw = e >> 2, cc = e & 3, kt = kt0 + cc;
+            if (kt >= 1 && d.n_ft - kt >= d.nh) {
+                const float2 a = s_out[kw * kBlockCols + cc];
+                dRj[(int64_t)((N - kw) % N) * d.n_ft + (d.n_ft - kt)] = make_float2(a.x, -a.y);
+            }
+        }
+    }
+}
+
+// Adjoint part B, one warp per time frequency: for every j, conj(H_j) G^ transformed back
+// along the wires, written over S_j's block of shat (the time-axis spectrum of dL/dS_j); the
+// block is staged in shared memory and written as contiguous 16-byte stores.
+template <int M>
+__global__ void __launch_bounds__(kWarps * 32, 3)
+k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ g2d,
+                 float2* __restrict__ shat, const float2* __restrict__ H)
+{
+    constexpr int N = 32 * M;
+    constexpr int TR = 32 * (M + 1);
+    static_assert(kWarps * TR >= N * kBlockCols, "output tile must fit the transpose space");
+    __shared__ float2 s_twi[N];
+    // the warps' transpose buffers, reused between transforms as the CTA's output tile [w][4]
+    __shared__ __align__(16) float2 s_tr[kWarps * TR];
+    float2* s_out = s_tr;
+    for (int e = threadIdx.x; e < N; e += blockDim.x) s_twi[e] = tw2[N + e];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kb = blockIdx.x, c = warp;
+    float2* tr = s_tr + warp * TR;
+    float2 g[32];
+    if (lane < M) {
+        const float2* gc = g2d + (int64_t)kb * N * kBlockCols + c;
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) g[k1] = __ldg(gc + (int64_t)(lane + M * k1) * kBlockCols);
+    }
+    const int tile4 = d.n_w * kBlockCols / 2;             // float4 per block of n_w wires
+    for (int j = 0; j < d.n_imp; ++j) {
+        const int64_t blk = (int64_t)j * d.nkb + kb;
+        if (lane < M) {
+            float2 u[32];
             const float2* hj = H + blk * N * kBlockCols + c;
 #pragma unroll
             for (int k1 = 0; k1 < 32; ++k1) {
-                const int kw = lane + M * k1;
-                if (dr_here) {
-                    // conj(S^) G^ / n
-                    const float2 val = make_float2(inv_n * (u[k1].x * g[k1].x + u[k1].y * g[k1].y),
-                                                   inv_n * (u[k1].x * g[k1].y - u[k1].y * g[k1].x));
-                    float2* dRj = dR + (int64_t)j * N * d.n_ft;
-                    dRj[(int64_t)kw * d.n_ft + kt] = val;
-                    if (mirror)
-                        dRj[(int64_t)((N - kw) % N) * d.n_ft + (d.n_ft - kt)] = make_float2(val.x, -val.y);
-                }
-                // conj(H_j) G^
-                const float2 h = __ldg(hj + (int64_t)kw * kBlockCols);
+                const float2 h = __ldg(hj + (int64_t)(lane + M * k1) * kBlockCols);
                 u[k1] = make_float2(h.x * g[k1].x + h.y * g[k1].y, h.x * g[k1].y - h.y * g[k1].x);
             }
             dft<32, true>(u);
 #pragma unroll
             for (int n2 = 1; n2 < 32; ++n2) u[n2] = twiddle<true>(u[n2], s_twi[n2 * M + lane]);
-        }
-        __syncwarp();
-        if (lane < M) {
 #pragma unroll
             for (int n2 = 0; n2 < 32; ++n2) tr[n2 * (M + 1) + lane] = u[n2];
         }
@@ -109,12 +179,19 @@ k_wire_adjoint_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __
         float2 v[M];
 #pragma unroll
         for (int k2 = 0; k2 < M; ++k2) v[k2] = tr[lane * (M + 1) + k2];
+        __syncwarp();
         dft<M, true>(v);
+        __syncthreads();                                  // every warp is done with its buffer
 #pragma unroll
         for (int n1 = 0; n1 < M; ++n1) {
             const int w = lane + 32 * n1;
-            if (w < d.n_w) col[(int64_t)w * kBlockCols] = v[n1];
+            if (w < d.n_w) s_out[w * kBlockCols + c] = v[n1];
         }
+        __syncthreads();
+        float4* dst = reinterpret_cast<float4*>(shat + blk * d.n_w * kBlockCols);
+        const float4* src = reinterpret_cast<const float4*>(s_out);
+        for (int e = threadIdx.x; e < tile4; e += blockDim.x) dst[e] = src[e];
+        __syncthreads();
     }
 }
 
@@ -146,16 +223,16 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
     const int N = p.n;
     float2* X = reinterpret_cast<float2*>(smraw);
     float2* Y = X + padded_len(N);
-    const int64_t n_rows = (int64_t)d.n_w * d.n_imp;
-    const int64_t r0 = 2 * (int64_t)blockIdx.x, r1 = r0 + 1;
-    const bool has1 = r1 < n_rows;
-    const int w0 = (int)(r0 / d.n_imp), j0 = (int)(r0 % d.n_imp);
-    const int w1 = has1 ? (int)(r1 / d.n_imp) : w0, j1 = has1 ? (int)(r1 % d.n_imp) : j0;
+    // CTA b: impact j = b / npw, wires 2 (b mod npw) and the next one.  Adjacent wires of one
+    // impact read adjacent 32-byte chunks of the blocked spectra.
+    const int npw = (d.n_w + 1) / 2;
+    const int j = blockIdx.x / npw, w0 = 2 * (blockIdx.x % npw), w1 = w0 + 1;
+    const bool has1 = w1 < d.n_w;
     const int64_t slab = (int64_t)d.nkb * d.n_w * kBlockCols;
-    const GridHermPairLd src{shat + j0 * slab, shat + j1 * slab, w0, w1, d.n_w, d.nh, N, has1};
+    const GridHermPairLd src{shat + j * slab, shat + j * slab, w0, has1 ? w1 : w0, d.n_w, d.nh, N, has1};
     const float2* z = run_plan<true, 0>(p, src, X, Y);
-    float* o0 = grid + r0 * d.n_t;
-    float* o1 = grid + r1 * d.n_t;
+    float* o0 = grid + ((int64_t)w0 * d.n_imp + j) * d.n_t;
+    float* o1 = grid + ((int64_t)w1 * d.n_imp + j) * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
         const float2 v = z[pad16(t)];
         o0[t] = v.x;
@@ -170,14 +247,26 @@ bool g_attr = false;
 }  // namespace
 
 cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const float2* gt,
-                                     float2* shat, const float2* H, float2* dR, float inv_n,
-                                     cudaStream_t s)
+                                     float2* shat, const float2* H, float2* g2d, float2* dR,
+                                     float inv_n, cudaStream_t s)
 {
     switch (d.n_fw / 32) {
-#define WCSIM_CASE(MM)                                                                       \
-    case MM:                                                                                 \
-        k_wire_adjoint_warp<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, gt, shat, H, dR, inv_n); \
-        break;
+#define WCSIM_CASE(MM)                                                                           \
+    case MM: {                                                                                   \
+        const size_t smem_a = (size_t)32 * MM * kBlockCols * sizeof(float2);                    \
+        static bool attr_set = false;                                                            \
+        if (!attr_set) {                                                                         \
+            cudaError_t e = cudaFuncSetAttribute(k_wire_adjoint_a<MM>,                           \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                                 (int)smem_a);                                   \
+            if (e) return e;                                                                     \
+            attr_set = true;                                                                     \
+        }                                                                                        \
+        k_wire_adjoint_a<MM><<<d.nkb, kWarps * 32, smem_a, s>>>(d, tw2, gt, shat, g2d, dR,      \
+                                                                inv_n);                          \
+        k_wire_adjoint_b<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, g2d, shat, H);               \
+        break;                                                                                   \
+    }
         WCSIM_ADJ_M(WCSIM_CASE)
 #undef WCSIM_CASE
         default: return cudaErrorInvalidValue;
@@ -194,8 +283,8 @@ cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const flo
         if (e) return e;
         g_attr = true;
     }
-    const int64_t n_rows = (int64_t)d.n_w * d.n_imp;
-    k_rows_c2r_grid<<<(unsigned)((n_rows + 1) / 2), 256, 2 * (size_t)padded_len(pt.n) * sizeof(float2), s>>>(
+    const int64_t n_ctas = (int64_t)d.n_imp * ((d.n_w + 1) / 2);
+    k_rows_c2r_grid<<<(unsigned)n_ctas, 256, 2 * (size_t)padded_len(pt.n) * sizeof(float2), s>>>(
         d, pt, shat, grid);
     return cudaGetLastError();
 }

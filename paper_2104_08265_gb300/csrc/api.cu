@@ -55,7 +55,9 @@ bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
 }  // namespace
 
-constexpr int kStages = 5;
+constexpr int kStages = 5;       // forward: zero, rasterize, rows_r2c, wire_pass, rows_c2r
+constexpr int kBwdStages = 7;    // backward: zero, rasterize, r2c(S), r2c(G), wire adjoint,
+                                 // c2r of dL/dS, depo adjoint
 
 struct wcsim_plane {
     wcsim_geometry g;
@@ -69,6 +71,7 @@ struct wcsim_plane {
     float* grid = nullptr;      // [n_rows][n_ticks]
     float2* shat = nullptr;     // time-axis spectra, blocked [n_imp][nkb][n_wires][4]
     float2* mt = nullptr;       // wire-summed spectra, blocked [nkb][n_wires][4]
+    float2* g2d = nullptr;      // adjoint: 2D spectrum of G, blocked [nkb][n_fw][4]
     int* flags = nullptr;       // device flag word
     // scratch of batched runs: bcap events' grids, time-axis and wire-summed spectra
     float* bgrid = nullptr;
@@ -81,7 +84,9 @@ struct wcsim_plane {
     int32_t kd = 64;            // autotuned: depos per rasterization CTA
     bool timing = false;
     cudaEvent_t ev[kStages + 1] = {};
+    cudaEvent_t evb[kBwdStages + 1] = {};
     bool ev_valid = false;
+    bool bwd_recorded = false;
 };
 
 namespace {
@@ -183,18 +188,29 @@ void plane_free(wcsim_plane* pl)
     cudaFree(pl->grid);
     cudaFree(pl->shat);
     cudaFree(pl->mt);
+    cudaFree(pl->g2d);
     cudaFree(pl->flags);
     cudaFree(pl->bgrid);
     cudaFree(pl->bshat);
     cudaFree(pl->bmt);
-    if (pl->ev_valid)
+    if (pl->ev_valid) {
         for (auto& e : pl->ev) cudaEventDestroy(e);
+        for (auto& e : pl->evb) cudaEventDestroy(e);
+    }
     delete pl;
 }
 
 inline void mark(wcsim_plane* pl, int i, cudaStream_t s)
 {
     if (pl->timing) cudaEventRecord(pl->ev[i], s);
+}
+
+inline void markb(wcsim_plane* pl, int i, cudaStream_t s)
+{
+    if (pl->timing) {
+        cudaEventRecord(pl->evb[i], s);
+        pl->bwd_recorded = true;
+    }
 }
 
 wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaStream_t s,
@@ -351,8 +367,11 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     {
         const char* v = getenv("WCSIM_WIRE_KERNEL");
         const bool block = v && strcmp(v, "block") == 0;
-        if (!block && wire_warp_supported(n_fw) && geom->n_wires <= n_fw)
+        if (!block && wire_warp_supported(n_fw) && geom->n_wires <= n_fw) {
             WC_TRY(wire_warp_twiddles(n_fw, &pl->tw_warp), "wire-axis twiddles");
+            const size_t g2d = (size_t)((n_ft / 2 + 1 + kBlockCols - 1) / kBlockCols) * kBlockCols * n_fw;
+            WC_TRY(cudaMalloc(&pl->g2d, g2d * sizeof(float2)), "adjoint scratch allocation");
+        }
     }
     const size_t cols = (size_t)d.nkb * kBlockCols;
     WC_TRY(cudaMalloc(&pl->H, (size_t)d.n_imp * d.n_fw * cols * sizeof(float2)), "response allocation");
@@ -366,6 +385,7 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
            "response preparation");
     WC_TRY(cudaStreamSynchronize(s), "response preparation");
     for (auto& ev : pl->ev) WC_TRY(cudaEventCreate(&ev), "event creation");
+    for (auto& ev : pl->evb) WC_TRY(cudaEventCreate(&ev), "event creation");
     pl->ev_valid = true;
 #undef WC_TRY
     *out = pl;
@@ -470,11 +490,16 @@ wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, con
     dG.n_imp = 1;
     cudaError_t e;
     if ((e = launch_rows_r2c(d, pl->pt, grid, pl->shat, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
+    markb(pl, 3, s);
     if ((e = launch_rows_r2c(dG, pl->pt, grad_wave, pl->mt, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
-    if ((e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, (float2*)grad_resp_c64,
+    markb(pl, 4, s);
+    if ((e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, pl->g2d,
+                                      (float2*)grad_resp_c64,
                                       (float)(1.0 / ((double)d.n_fw * (double)d.n_ft)), s)))
         return cuda_fail(e, "wire adjoint launch");
+    markb(pl, 5, s);
     if ((e = launch_rows_c2r_grid(d, pl->pt, pl->shat, dgrid, s))) return cuda_fail(e, "rows_c2r_grid launch");
+    markb(pl, 6, s);
     return WCSIM_OK;
 }
 
@@ -494,6 +519,7 @@ wcsim_status wcsim_rasterize_adjoint(wcsim_plane* pl, const wcsim_depos* depos, 
     DepoGrads g{grads->dq, grads->dp, grads->dt, grads->dsigma_L, grads->dsigma_T, grads->dglobal};
     if ((e = launch_depo_adjoint(make_consts(pl), depo_arrays(depos), dgrid, g, pl->flags, s)))
         return cuda_fail(e, "depo adjoint launch");
+    markb(pl, 7, s);
     return WCSIM_OK;
 }
 
@@ -512,15 +538,18 @@ wcsim_status wcsim_run_backward(wcsim_plane* pl, const wcsim_depos* depos, const
     cudaStream_t s = (cudaStream_t)stream;
     const ConvDims& d = pl->dims;
     cudaError_t e = cudaSuccess;
+    markb(pl, 0, s);
     if (!pl->grid_clean) {
         e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
         if (e) return cuda_fail(e, "grid reset");
     }
     pl->grid_clean = false;             // the grid ends up holding dL/dS
+    markb(pl, 1, s);
     RasterConsts c = make_consts(pl);
     c.fluctuate = 0;                    // the gradient is that of the mean waveform
     if ((e = launch_rasterize(c, depo_arrays(depos), pl->grid, pl->flags, s)))
         return cuda_fail(e, "rasterize launch");
+    markb(pl, 2, s);
     if ((st = wcsim_convolve_adjoint(pl, grad_wave, pl->grid, pl->grid, grad_resp_c64, stream))) return st;
     return wcsim_rasterize_adjoint(pl, depos, pl->grid, grads, stream);
 }
@@ -741,6 +770,14 @@ wcsim_status wcsim_plane_stage_times(wcsim_plane* pl, float* ms, int32_t n)
         e = cudaEventElapsedTime(&t, pl->ev[i], pl->ev[i + 1]);
         if (e) return cuda_fail(e, "event elapsed time");
         ms[i] = t;
+    }
+    for (int i = 0; i < kBwdStages && kStages + i < n; ++i) {
+        float t = 0.f;
+        if (pl->bwd_recorded) {
+            if (i == 0 && (e = cudaEventSynchronize(pl->evb[kBwdStages]))) return cuda_fail(e, "event synchronize");
+            if ((e = cudaEventElapsedTime(&t, pl->evb[i], pl->evb[i + 1]))) return cuda_fail(e, "event elapsed time");
+        }
+        ms[kStages + i] = t;
     }
     return WCSIM_OK;
 }

@@ -271,7 +271,10 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                int* flags)
 {
     __shared__ Decision s_dec[kDepos];
-    __shared__ float s_w[kWarps][6][kWmax];      // wp, dwp/dmu, dwp/dsig, wt, dwt/dmu, dwt/dsig
+    // wp, dwp/dmu, dwp/dsig per row; wt, dwt/dmu, dwt/dsig per tick with 4 zero slots on
+    // either side, so that a 4-tick group hanging over the tile edge reads zero weights
+    __shared__ float s_w[kWarps][3][kWmax];
+    __shared__ float s_t[kWarps][3][kWmax + 8];
     __shared__ double s_glob[kWarps][3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kDepos;
@@ -290,9 +293,10 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
     float* wp = s_w[warp][0];
     float* wpm = s_w[warp][1];
     float* wps = s_w[warp][2];
-    float* wt = s_w[warp][3];
-    float* wtm = s_w[warp][4];
-    float* wts = s_w[warp][5];
+    float* wt = s_t[warp][0] + 4;
+    float* wtm = s_t[warp][1] + 4;
+    float* wts = s_t[warp][2] + 4;
+    const bool vec4 = ((c.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(dgrid) & 15) == 0);
 
     for (int i = warp; i < kDepos; i += kWarps) {
         const int64_t gi = base + i;
@@ -320,30 +324,60 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                         wpm[e] = m * isp;
                         wps[e] = sg * isp;
                     }
-                    for (int e = lane; e < nt; e += 32) {
-                        const int64_t ko = (int64_t)(k0 + e) - dd.i0t;
-                        float m = 0.f, sg = 0.f;
-                        if (dd.st > 0.0f) {
-                            wt[e] = bin_weight(ko, dd.frac_t, s_t);
-                            bin_weight_derivs(ko, dd.frac_t, s_t, m, sg);
-                        } else {
-                            wt[e] = 1.0f;
+                    for (int e = lane - 4; e < nt + 4; e += 32) {
+                        float w = 0.f, m = 0.f, sg = 0.f;
+                        if (e >= 0 && e < nt) {
+                            const int64_t ko = (int64_t)(k0 + e) - dd.i0t;
+                            if (dd.st > 0.0f) {
+                                w = bin_weight(ko, dd.frac_t, s_t);
+                                bin_weight_derivs(ko, dd.frac_t, s_t, m, sg);
+                            } else {
+                                w = 1.0f;
+                            }
                         }
+                        wt[e] = w;
                         wtm[e] = m * ist;
                         wts[e] = sg * ist;
                     }
                     __syncwarp();
-                    const float inv_nt = 1.0f / (float)nt;
-                    for (int b = lane; b < nr * nt; b += 32) {
-                        const int ir = (int)(((float)b + 0.5f) * inv_nt);
-                        const int ik = b - ir * nt;
-                        const float sv = __ldg(dgrid + (int64_t)(r0 + ir) * c.n_ticks + (k0 + ik));
-                        const float pw = wp[ir], tw = wt[ik];
-                        a_q += sv * pw * tw;
-                        a_pm += sv * wpm[ir] * tw;
-                        a_ps += sv * wps[ir] * tw;
-                        a_tm += sv * pw * wtm[ik];
-                        a_ts += sv * pw * wts[ik];
+                    if (vec4) {
+                        // (row, 4-tick group) items: one 16-byte load of dL/dS per item
+                        const int q_lo = k0 >> 2, q_hi = (k0 + nt - 1) >> 2, nq = q_hi - q_lo + 1;
+                        const float inv_nq = 1.0f / (float)nq;
+                        for (int item = lane; item < nr * nq; item += 32) {
+                            const int ir = (int)(((float)item + 0.5f) * inv_nq);
+                            const int kq = (q_lo + item - ir * nq) * 4;
+                            const float4 sv = __ldg(reinterpret_cast<const float4*>(
+                                dgrid + (int64_t)(r0 + ir) * c.n_ticks + kq));
+                            const int ik = kq - k0;                // -3 .. nt - 1
+                            const float s4[4] = {sv.x, sv.y, sv.z, sv.w};
+                            float A = 0.f, B = 0.f, C = 0.f;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                A += s4[e] * wt[ik + e];
+                                B += s4[e] * wtm[ik + e];
+                                C += s4[e] * wts[ik + e];
+                            }
+                            const float pw = wp[ir];
+                            a_q += pw * A;
+                            a_pm += wpm[ir] * A;
+                            a_ps += wps[ir] * A;
+                            a_tm += pw * B;
+                            a_ts += pw * C;
+                        }
+                    } else {
+                        const float inv_nt = 1.0f / (float)nt;
+                        for (int b = lane; b < nr * nt; b += 32) {
+                            const int ir = (int)(((float)b + 0.5f) * inv_nt);
+                            const int ik = b - ir * nt;
+                            const float sv = __ldg(dgrid + (int64_t)(r0 + ir) * c.n_ticks + (k0 + ik));
+                            const float pw = wp[ir], tw = wt[ik];
+                            a_q += sv * pw * tw;
+                            a_pm += sv * wpm[ir] * tw;
+                            a_ps += sv * wps[ir] * tw;
+                            a_tm += sv * pw * wtm[ik];
+                            a_ts += sv * pw * wts[ik];
+                        }
                     }
                     __syncwarp();
                 }

@@ -152,10 +152,11 @@ cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2*
                              const float2* H, float2* mt, cudaStream_t s, int n_ev = 1);
 // Adjoint of the wire pass (n_fw = 32 M): reads the time-axis spectra of the forward grid
 // (shat) and of G (gt, blocked [nkb][n_w][4]); overwrites shat with the time-axis spectra
-// of dL/dS and, if dR is not null, writes dL/dR_j (full [n_imp][n_fw][n_ft] layout).
+// of dL/dS and, if dR is not null, writes dL/dR_j (full [n_imp][n_fw][n_ft] layout).  g2d
+// (blocked [nkb][n_fw][4]) receives the 2D spectrum of G on the way.
 cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const float2* gt,
-                                     float2* shat, const float2* H, float2* dR, float inv_n,
-                                     cudaStream_t s);
+                                     float2* shat, const float2* H, float2* g2d, float2* dR,
+                                     float inv_n, cudaStream_t s);
 // Inverse time-axis FFT of every grid row from blocked spectra [n_imp][nkb][n_w][4].
 cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const float2* shat,
                                  float* grid, cudaStream_t s);

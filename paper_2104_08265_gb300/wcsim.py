@@ -23,6 +23,8 @@ OK, EINVAL, ESHAPE, ENOMEM, ECUDA, ETIMEOUT, EDEVICE_CHECK = range(7)
 STATUS_NAMES = {0: "WCSIM_OK", 1: "WCSIM_EINVAL", 2: "WCSIM_ESHAPE", 3: "WCSIM_ENOMEM",
                 4: "WCSIM_ECUDA", 5: "WCSIM_ETIMEOUT", 6: "WCSIM_EDEVICE_CHECK"}
 STAGES = ("zero", "rasterize", "rows_r2c", "wire_pass", "rows_c2r")
+BWD_STAGES = ("bwd_zero", "bwd_rasterize", "bwd_r2c_S", "bwd_r2c_G", "bwd_wire_adjoint",
+              "bwd_c2r_dS", "bwd_depo_adjoint")
 
 
 class WcsimError(RuntimeError):
@@ -317,10 +319,11 @@ class Plane:
     def set_timing(self, enable: bool = True):
         check(lib().wcsim_plane_set_timing(self._h, 1 if enable else 0))
 
-    def stage_times(self) -> dict:
-        arr = (ctypes.c_float * len(STAGES))()
-        check(lib().wcsim_plane_stage_times(self._h, arr, len(STAGES)))
-        return dict(zip(STAGES, [float(x) for x in arr]))
+    def stage_times(self, backward: bool = False) -> dict:
+        names = STAGES + (BWD_STAGES if backward else ())
+        arr = (ctypes.c_float * len(names))()
+        check(lib().wcsim_plane_stage_times(self._h, arr, len(names)))
+        return dict(zip(names, [float(x) for x in arr]))
 
 
 def convolve_noalloc(geom: Geometry, response, grid, out=None, n_fw: int = 0, n_ft: int = 0,
