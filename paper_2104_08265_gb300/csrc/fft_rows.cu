@@ -149,8 +149,11 @@ k_rows_r2c_staged(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
     }
 }
 
+// pf_ahead > 0: CTA b first asks L2 for the rows of pair b + pf_ahead (the CTA that will
+// most likely take over its slot once it retires), so that pair's first pass reads L2.
 __global__ void __launch_bounds__(kDirectThreads, 2)
-k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2* __restrict__ shat)
+k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2* __restrict__ shat,
+                  int pf_ahead)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     const int N = p.n;
@@ -161,6 +164,13 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
     const bool has1 = r0 + 1 < n_rows;
     grid += blockIdx.y * d.ev_grid;          // event of a batched launch (0 otherwise)
     shat += blockIdx.y * d.ev_shat;
+    if (pf_ahead > 0 && threadIdx.x == 0) {
+        const int64_t q0 = r0 + 2 * (int64_t)pf_ahead;
+        if (q0 < n_rows) {
+            const int nq = (q0 + 1 < n_rows) ? 2 : 1;
+            bulk_prefetch_l2(grid + q0 * d.n_t, (uint32_t)(nq * d.n_t * sizeof(float)));
+        }
+    }
     const RealPairLd src{grid + r0 * d.n_t, has1 ? grid + (r0 + 1) * d.n_t : nullptr, d.n_t};
     const float2* z = run_plan<false, 0>(p, src, X, Y);
     if (d.clear_input) {
@@ -197,6 +207,21 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
 
 size_t direct_smem(int n) { return 2 * (size_t)padded_len(n) * sizeof(float2); }
 
+// CTAs of k_rows_r2c_direct resident on the whole GPU for transform length n, when its rows
+// may be prefetched with bulk copies (16-byte aligned rows); 0 otherwise.
+int r2c_prefetch_ahead(const ConvDims& d, const float* grid, int n)
+{
+    if ((d.n_t % 4) != 0 || (reinterpret_cast<uintptr_t>(grid) & 15) != 0) return 0;
+    if (d.ev_grid % 4 != 0) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_r2c_direct, kDirectThreads,
+                                                      direct_smem(n)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sm_count();
+}
+
 bool g_attr = false;
 cudaError_t attrs()
 {
@@ -224,7 +249,8 @@ cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* g
         const int grid_n = n_pairs < sm_count() ? (int)n_pairs : sm_count();
         k_rows_r2c_staged<<<grid_n, kStagedThreads, smem, s>>>(d, pt, grid, shat, flags);
     } else {
-        k_rows_r2c_direct<<<(unsigned)n_pairs, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, grid, shat);
+        k_rows_r2c_direct<<<(unsigned)n_pairs, kDirectThreads, direct_smem(pt.n), s>>>(
+            d, pt, grid, shat, r2c_prefetch_ahead(d, grid, pt.n));
     }
     return cudaGetLastError();
 }
@@ -254,7 +280,8 @@ cudaError_t launch_rows_r2c_batch(const ConvDims& d, const FftPlan& pt, const fl
     if (e) return e;
     const int64_t n_pairs = ((int64_t)d.n_w * d.n_imp + 1) / 2;
     const dim3 g((unsigned)n_pairs, (unsigned)n_ev);
-    k_rows_r2c_direct<<<g, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, grid, shat);
+    k_rows_r2c_direct<<<g, kDirectThreads, direct_smem(pt.n), s>>>(
+        d, pt, grid, shat, r2c_prefetch_ahead(d, grid, pt.n));
     return cudaGetLastError();
 }
 

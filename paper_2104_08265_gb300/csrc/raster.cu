@@ -84,17 +84,6 @@ __device__ __forceinline__ Decision decide(const RasterConsts& c, const DepoArra
     return r;
 }
 
-// Gaussian mass of bin k: Phi(b) - Phi(a), in units where u = offset / (sqrt(2) sigma);
-// the erfc forms keep relative precision in the tails.  koff = k - floor(position).
-__device__ __forceinline__ float bin_weight(int64_t koff, float frac, float s)
-{
-    const float ua = ((float)koff - frac) * s;
-    const float ub = ((float)(koff + 1) - frac) * s;
-    if (ua >= 0.0f) return 0.5f * (erfcf(ua) - erfcf(ub));
-    if (ub <= 0.0f) return 0.5f * (erfcf(-ub) - erfcf(-ua));
-    return 0.5f * (erff(ub) - erff(ua));
-}
-
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the multiply-xor bijection with a
 // Weyl-sequence key schedule.
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
@@ -134,6 +123,25 @@ __device__ __forceinline__ void box_muller4(uint4 x, float z[4])
     z[3] = -rb * sb;
 }
 
+// erfc(|u|) at bin edge u = (koff - frac) s: the edge term of the bin masses below.
+__device__ __forceinline__ float edge_erfc(int64_t koff, float frac, float s)
+{
+    return erfcf(fabsf(((float)koff - frac) * s));
+}
+
+// Mass of the bin between edges a < b from their edge terms ea = erfc|ua|, eb = erfc|ub|:
+// 0.5 (erfc ua - erfc ub) on the upper side of the mean, 0.5 (erfc -ub - erfc -ua) on the
+// lower side (both keep relative precision in the tails), 1 - 0.5 (ea + eb) for the bin
+// holding the mean.  u = offset / (sqrt(2) sigma), so that erfc gives the normal tail mass.
+__device__ __forceinline__ float bin_mass(int64_t koff, float frac, float s, float ea, float eb)
+{
+    const float ua = ((float)koff - frac) * s;
+    const float ub = ((float)(koff + 1) - frac) * s;
+    if (ua >= 0.0f) return 0.5f * (ea - eb);
+    if (ub <= 0.0f) return 0.5f * (eb - ea);
+    return 1.0f - 0.5f * (ea + eb);
+}
+
 // The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps.
 template <int KD>
 __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const DepoArrays& d,
@@ -142,7 +150,10 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     static_assert(KD <= kWarps * 32, "one deciding thread per depo");
     __shared__ Decision s_dec[KD];
     __shared__ float s_wp[kWarps][kWmax];
-    __shared__ float s_wt[kWarps][kWmax];
+    // tick weights of a tile laid out on 4-tick groups: slot p is tick 4 q_lo + p (zero
+    // outside the window), so that an item reads its four weights with one 16-byte load
+    __shared__ __align__(16) float s_wt[kWarps][kWmax + 8];
+    __shared__ float s_edge[kWarps][2 * (kWmax + 1)];    // row edges, then tick edges
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = blk * KD;
     if (threadIdx.x < KD) {
@@ -160,6 +171,7 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     const bool vec4 = ((c.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
     float* wp = s_wp[warp];
     float* wt = s_wt[warp];
+    float* ed = s_edge[warp];
 
     for (int i = warp; i < KD; i += kWarps) {
         const Decision dd = s_dec[i];
@@ -174,13 +186,33 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
             const int nr = min(kWmax, dd.r_hi - r0 + 1);
             for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kWmax) {
                 const int nt = min(kWmax, dd.k_hi - k0 + 1);
-                for (int e = lane; e < nr; e += 32)
-                    wp[e] = dd.qatt * ((dd.sp > 0.0f) ? bin_weight((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p) : 1.0f);
-                for (int e = lane; e < nt; e += 32)
-                    wt[e] = (dd.st > 0.0f) ? bin_weight((int64_t)(k0 + e) - dd.i0t, dd.frac_t, s_t) : 1.0f;
-                __syncwarp();
+                // one erfc per bin edge: nr + 1 row edges and nt + 1 tick edges
+                for (int e = lane; e < nr + nt + 2; e += 32) {
+                    float v;
+                    if (e <= nr) v = edge_erfc((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p);
+                    else v = edge_erfc((int64_t)(k0 + e - nr - 1) - dd.i0t, dd.frac_t, s_t);
+                    ed[e] = v;
+                }
                 const int q_lo = k0 >> 2, q_hi = (k0 + nt - 1) >> 2;
                 const int nq = q_hi - q_lo + 1;
+                const int koff = k0 - 4 * q_lo;            // slot of tick k0
+                __syncwarp();
+                for (int e = lane; e < nr + 4 * nq; e += 32) {
+                    if (e < nr) {
+                        wp[e] = dd.qatt * ((dd.sp > 0.0f)
+                                    ? bin_mass((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p, ed[e], ed[e + 1])
+                                    : 1.0f);
+                    } else {
+                        const int k = e - nr - koff;
+                        float w = 0.0f;
+                        if (k >= 0 && k < nt)
+                            w = (dd.st > 0.0f) ? bin_mass((int64_t)(k0 + k) - dd.i0t, dd.frac_t, s_t,
+                                                          ed[nr + 1 + k], ed[nr + 2 + k])
+                                               : 1.0f;
+                        wt[e - nr] = w;
+                    }
+                }
+                __syncwarp();
                 const float inv_nq = 1.0f / (float)nq;
                 for (int item = lane; item < nr * nq; item += 32) {
                     const int ir = (int)(((float)item + 0.5f) * inv_nq);
@@ -188,12 +220,8 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                     const int64_t r = r0 + ir;
                     const int kq = (q_lo + iq) * 4;
                     const float w = wp[ir];
-                    float v[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int ik = kq + e - k0;
-                        v[e] = (ik >= 0 && ik < nt) ? w * wt[ik] : 0.0f;
-                    }
+                    const float4 t4 = reinterpret_cast<const float4*>(wt)[iq];
+                    float v[4] = {w * t4.x, w * t4.y, w * t4.z, w * t4.w};
                     if (c.fluctuate) {
                         // normal approximation to Binomial(Q', mean / Q'); zero-mean bins
                         // (outside the window) stay zero
@@ -242,20 +270,6 @@ k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
     rasterize_block<KD>(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
 }
 
-// Derivatives of the bin weight w = Phi(b') - Phi(a') (a', b' = edge offsets / sigma) with
-// respect to mu and sigma, in units of 1/sigma:  -(phi(b') - phi(a')) and
-// -(b' phi(b') - a' phi(a')), with u = offset / (sqrt(2) sigma) = a' / sqrt(2).
-__device__ __forceinline__ void bin_weight_derivs(int64_t koff, float frac, float s, float& dmu,
-                                                  float& dsig)
-{
-    const float ua = ((float)koff - frac) * s;
-    const float ub = ((float)(koff + 1) - frac) * s;
-    const float inv_sqrt_2pi = 0.398942280401432678f;
-    const float pa = inv_sqrt_2pi * expf(-ua * ua), pb = inv_sqrt_2pi * expf(-ub * ub);
-    dmu = -(pb - pa);
-    dsig = -1.41421356237309505f * (ub * pb - ua * pa);
-}
-
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -271,10 +285,12 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                int* flags)
 {
     __shared__ Decision s_dec[kDepos];
-    // wp, dwp/dmu, dwp/dsig per row; wt, dwt/dmu, dwt/dsig per tick with 4 zero slots on
-    // either side, so that a 4-tick group hanging over the tile edge reads zero weights
+    // wp, dwp/dmu, dwp/dsig per row; wt, dwt/dmu, dwt/dsig per tick laid out on 4-tick
+    // groups (slot p is tick 4 q_lo + p, zero outside the window)
     __shared__ float s_w[kWarps][3][kWmax];
-    __shared__ float s_t[kWarps][3][kWmax + 8];
+    __shared__ __align__(16) float s_t[kWarps][3][kWmax + 8];
+    // per bin edge u: erfc|u|, phi(u) = exp(-u^2) / sqrt(2 pi) and u phi(u); rows then ticks
+    __shared__ float s_e[kWarps][3][2 * (kWmax + 1)];
     __shared__ double s_glob[kWarps][3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kDepos;
@@ -293,9 +309,12 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
     float* wp = s_w[warp][0];
     float* wpm = s_w[warp][1];
     float* wps = s_w[warp][2];
-    float* wt = s_t[warp][0] + 4;
-    float* wtm = s_t[warp][1] + 4;
-    float* wts = s_t[warp][2] + 4;
+    float* wt = s_t[warp][0];
+    float* wtm = s_t[warp][1];
+    float* wts = s_t[warp][2];
+    float* eE = s_e[warp][0];
+    float* eP = s_e[warp][1];
+    float* eU = s_e[warp][2];
     const bool vec4 = ((c.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(dgrid) & 15) == 0);
 
     for (int i = warp; i < kDepos; i += kWarps) {
@@ -312,52 +331,64 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                 const int nr = min(kWmax, dd.r_hi - r0 + 1);
                 for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kWmax) {
                     const int nt = min(kWmax, dd.k_hi - k0 + 1);
-                    for (int e = lane; e < nr; e += 32) {
-                        const int64_t ko = (int64_t)(r0 + e) - dd.i0p;
-                        float m = 0.f, sg = 0.f;
-                        if (dd.sp > 0.0f) {
-                            wp[e] = bin_weight(ko, dd.frac_p, s_p);
-                            bin_weight_derivs(ko, dd.frac_p, s_p, m, sg);
-                        } else {
-                            wp[e] = 1.0f;
-                        }
-                        wpm[e] = m * isp;
-                        wps[e] = sg * isp;
+                    const int q_lo = k0 >> 2, q_hi = (k0 + nt - 1) >> 2, nq = q_hi - q_lo + 1;
+                    const int koff = k0 - 4 * q_lo;        // slot of tick k0
+                    // edge terms: nr + 1 row edges, nt + 1 tick edges
+                    for (int e = lane; e < nr + nt + 2; e += 32) {
+                        const float u = (e <= nr) ? ((float)((int64_t)(r0 + e) - dd.i0p) - dd.frac_p) * s_p
+                                                  : ((float)((int64_t)(k0 + e - nr - 1) - dd.i0t) - dd.frac_t) * s_t;
+                        const float ph = 0.398942280401432678f * expf(-u * u);
+                        eE[e] = erfcf(fabsf(u));
+                        eP[e] = ph;
+                        eU[e] = u * ph;
                     }
-                    for (int e = lane - 4; e < nt + 4; e += 32) {
-                        float w = 0.f, m = 0.f, sg = 0.f;
-                        if (e >= 0 && e < nt) {
-                            const int64_t ko = (int64_t)(k0 + e) - dd.i0t;
-                            if (dd.st > 0.0f) {
-                                w = bin_weight(ko, dd.frac_t, s_t);
-                                bin_weight_derivs(ko, dd.frac_t, s_t, m, sg);
-                            } else {
-                                w = 1.0f;
+                    __syncwarp();
+                    // w = Phi(b') - Phi(a'); dw/dmu = -(phi(b') - phi(a')) / sigma;
+                    // dw/dsigma = -(b' phi(b') - a' phi(a')) / sigma, with b' = sqrt(2) ub
+                    for (int e = lane; e < nr + 4 * nq; e += 32) {
+                        if (e < nr) {
+                            float w = 1.0f, m = 0.0f, sg = 0.0f;
+                            if (dd.sp > 0.0f) {
+                                w = bin_mass((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p, eE[e], eE[e + 1]);
+                                m = -(eP[e + 1] - eP[e]);
+                                sg = -1.41421356237309505f * (eU[e + 1] - eU[e]);
                             }
+                            wp[e] = w;
+                            wpm[e] = m * isp;
+                            wps[e] = sg * isp;
+                        } else {
+                            const int k = e - nr - koff, a = nr + 1 + k;
+                            float w = 0.0f, m = 0.0f, sg = 0.0f;
+                            if (k >= 0 && k < nt) {
+                                if (dd.st > 0.0f) {
+                                    w = bin_mass((int64_t)(k0 + k) - dd.i0t, dd.frac_t, s_t, eE[a], eE[a + 1]);
+                                    m = -(eP[a + 1] - eP[a]);
+                                    sg = -1.41421356237309505f * (eU[a + 1] - eU[a]);
+                                } else {
+                                    w = 1.0f;
+                                }
+                            }
+                            wt[e - nr] = w;
+                            wtm[e - nr] = m * ist;
+                            wts[e - nr] = sg * ist;
                         }
-                        wt[e] = w;
-                        wtm[e] = m * ist;
-                        wts[e] = sg * ist;
                     }
                     __syncwarp();
                     if (vec4) {
                         // (row, 4-tick group) items: one 16-byte load of dL/dS per item
-                        const int q_lo = k0 >> 2, q_hi = (k0 + nt - 1) >> 2, nq = q_hi - q_lo + 1;
                         const float inv_nq = 1.0f / (float)nq;
                         for (int item = lane; item < nr * nq; item += 32) {
                             const int ir = (int)(((float)item + 0.5f) * inv_nq);
-                            const int kq = (q_lo + item - ir * nq) * 4;
+                            const int iq = item - ir * nq;
+                            const int kq = (q_lo + iq) * 4;
                             const float4 sv = __ldg(reinterpret_cast<const float4*>(
                                 dgrid + (int64_t)(r0 + ir) * c.n_ticks + kq));
-                            const int ik = kq - k0;                // -3 .. nt - 1
-                            const float s4[4] = {sv.x, sv.y, sv.z, sv.w};
-                            float A = 0.f, B = 0.f, C = 0.f;
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                A += s4[e] * wt[ik + e];
-                                B += s4[e] * wtm[ik + e];
-                                C += s4[e] * wts[ik + e];
-                            }
+                            const float4 w4 = reinterpret_cast<const float4*>(wt)[iq];
+                            const float4 m4 = reinterpret_cast<const float4*>(wtm)[iq];
+                            const float4 g4 = reinterpret_cast<const float4*>(wts)[iq];
+                            const float A = sv.x * w4.x + sv.y * w4.y + sv.z * w4.z + sv.w * w4.w;
+                            const float B = sv.x * m4.x + sv.y * m4.y + sv.z * m4.z + sv.w * m4.w;
+                            const float C = sv.x * g4.x + sv.y * g4.y + sv.z * g4.z + sv.w * g4.w;
                             const float pw = wp[ir];
                             a_q += pw * A;
                             a_pm += wpm[ir] * A;
@@ -371,12 +402,12 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                             const int ir = (int)(((float)b + 0.5f) * inv_nt);
                             const int ik = b - ir * nt;
                             const float sv = __ldg(dgrid + (int64_t)(r0 + ir) * c.n_ticks + (k0 + ik));
-                            const float pw = wp[ir], tw = wt[ik];
+                            const float pw = wp[ir], tw = wt[ik + koff];
                             a_q += sv * pw * tw;
                             a_pm += sv * wpm[ir] * tw;
                             a_ps += sv * wps[ir] * tw;
-                            a_tm += sv * pw * wtm[ik];
-                            a_ts += sv * pw * wts[ik];
+                            a_tm += sv * pw * wtm[ik + koff];
+                            a_ts += sv * pw * wts[ik + koff];
                         }
                     }
                     __syncwarp();
