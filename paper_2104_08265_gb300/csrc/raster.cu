@@ -280,7 +280,7 @@ __device__ __forceinline__ float warp_sum(float v)
 // Per depo: recompute the patch weights and their mu / sigma derivatives, gather dL/dS over
 // the patch and apply the chain rule through Q' = Q exp(-t_d / tau), t_a = t + t_d and
 // sigma = sqrt(2 D t_d).  The global sums are reduced per block in FP64.
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 3)
 k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, DepoGrads g,
                int* flags)
 {
@@ -291,7 +291,9 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
     __shared__ __align__(16) float s_t[kWarps][3][kWmax + 8];
     // per bin edge u: erfc|u|, phi(u) = exp(-u^2) / sqrt(2 pi) and u phi(u); rows then ticks
     __shared__ float s_e[kWarps][3][2 * (kWmax + 1)];
-    __shared__ double s_glob[kWarps][3];
+    // per depo, the FP32 factors of its terms in the three global sums (dL/dsigma_L,
+    // sigma_L; dL/dsigma_T, sigma_T; dL/dQ', Q'), zero for depos that add nothing
+    __shared__ float s_gt[kDepos][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * kDepos;
     if (threadIdx.x < kDepos) {
@@ -303,9 +305,10 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
             r.id = d.id[i];
         }
         s_dec[threadIdx.x] = r;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_gt[threadIdx.x][k] = 0.0f;
     }
     __syncthreads();
-    double gl0 = 0.0, gl1 = 0.0, gl2 = 0.0;       // lane 0 of each warp
     float* wp = s_w[warp][0];
     float* wpm = s_w[warp][1];
     float* wps = s_w[warp][2];
@@ -429,23 +432,39 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
             if (g.dsl) g.dsl[gi] = dsl;
             if (g.dst) g.dst[gi] = dst;
             if (dd.ok && qa > 0.0f) {
-                // sigma = sqrt(2 D t_d): dsigma / dD = sigma / (2 D);  dQ'/dtau = Q' t_d / tau^2
-                if (c.DL > 0.0) gl0 += (double)dsl * ((double)dd.st * c.v) / (2.0 * c.DL);
-                if (c.DT > 0.0) gl1 += (double)dst * (double)dd.sp / (2.0 * c.DT);
-                gl2 += (double)a_q * (double)qa * d.td[gi] / (c.tau * c.tau);
+                s_gt[i][0] = dsl;
+                s_gt[i][1] = dd.st;
+                s_gt[i][2] = dst;
+                s_gt[i][3] = dd.sp;
+                s_gt[i][4] = a_q;
+                s_gt[i][5] = qa;
             }
         }
     }
-    if (lane == 0) {
-        s_glob[warp][0] = gl0;
-        s_glob[warp][1] = gl1;
-        s_glob[warp][2] = gl2;
-    }
     __syncthreads();
-    if (threadIdx.x < 3 && g.dglobal) {
-        double acc = 0.0;
-        for (int w = 0; w < kWarps; ++w) acc += s_glob[w][threadIdx.x];
-        atomicAdd(g.dglobal + threadIdx.x, acc);
+    // The global sums, by one warp for the whole block (FP64 is scarce on this part: one
+    // warp instruction per 32 depos).  sigma = sqrt(2 D t_d) gives dsigma/dD = sigma / (2 D)
+    // (sigma_L = v sigma_t in mm); dQ'/dtau = Q' t_d / tau^2.  Products of two FP32 values
+    // are exact in FP64.
+    if (warp == 0 && g.dglobal) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int i = lane; i < kDepos; i += 32) {
+            if (!(s_gt[i][5] > 0.0f)) continue;
+            a0 += (double)s_gt[i][0] * (double)s_gt[i][1];
+            a1 += (double)s_gt[i][2] * (double)s_gt[i][3];
+            a2 += (double)s_gt[i][4] * (double)s_gt[i][5] * d.td[base + i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) {
+            if (c.DL > 0.0) atomicAdd(g.dglobal + 0, a0 * c.v / (2.0 * c.DL));
+            if (c.DT > 0.0) atomicAdd(g.dglobal + 1, a1 / (2.0 * c.DT));
+            atomicAdd(g.dglobal + 2, a2 / (c.tau * c.tau));
+        }
     }
 }
 
