@@ -195,27 +195,6 @@ k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __res
     }
 }
 
-// First-pass source of the inverse time FFT of grid rows r0, r1 (wire w, impact j each):
-// z[k] = X0[k] + i X1[k] from the blocked half spectra.
-struct GridHermPairLd {
-    const float2* s0;     // blocked slab of row r0's impact position
-    const float2* s1;
-    int w0, w1, n_w, nh, n;
-    bool has1;
-    __device__ __forceinline__ float2 operator()(int, int k) const
-    {
-        const bool lo = k < nh;
-        const int kk = lo ? k : n - k;
-        float2 a = __ldg(s0 + blk_index(kk, w0, n_w));
-        float2 b = has1 ? __ldg(s1 + blk_index(kk, w1, n_w)) : make_float2(0.f, 0.f);
-        if (!lo) {
-            a.y = -a.y;
-            b.y = -b.y;
-        }
-        return make_float2(a.x - b.y, a.y + b.x);
-    }
-};
-
 __global__ void __launch_bounds__(256, 2)
 k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* __restrict__ grid)
 {
@@ -229,8 +208,9 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
     const int j = blockIdx.x / npw, w0 = 2 * (blockIdx.x % npw), w1 = w0 + 1;
     const bool has1 = w1 < d.n_w;
     const int64_t slab = (int64_t)d.nkb * d.n_w * kBlockCols;
-    const GridHermPairLd src{shat + j * slab, shat + j * slab, w0, has1 ? w1 : w0, d.n_w, d.nh, N, has1};
-    const float2* z = run_plan<true, 0>(p, src, X, Y);
+    stage_herm_pair(shat + j * slab, shat + j * slab, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
+    __syncthreads();
+    const float2* z = run_plan<true, 0>(p, SmemLd<0>{X}, Y, X);
     float* o0 = grid + ((int64_t)w0 * d.n_imp + j) * d.n_t;
     float* o1 = grid + ((int64_t)w1 * d.n_imp + j) * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {

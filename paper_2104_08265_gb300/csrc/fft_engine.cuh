@@ -330,6 +330,38 @@ __device__ __forceinline__ void pass_any(int R, const Ld& ld, const St& st, cons
     }
 }
 
+// Stage the input of an inverse real-pair transform: z[k] = X0[k] + i X1[k], k < n, for two
+// Hermitian spectra given by their halves k < nh at columns w0, w1 of blocked slabs s0, s1
+// (X1 = 0 when !has1), into the padded shared buffer z.  Each stored element is read once
+// and also gives the mirror z[n - k] (conj X0 + i conj X1); loads are issued in batches of
+// kU per thread before their stores.  Ends without a barrier.
+__device__ __forceinline__ void stage_herm_pair(const float2* __restrict__ s0,
+                                                const float2* __restrict__ s1, int w0, int w1,
+                                                bool has1, int n_w, int nh, int n, float2* z)
+{
+    constexpr int kU = 6;
+    for (int base = threadIdx.x; base < nh; base += kU * blockDim.x) {
+        float2 a[kU], b[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int kk = base + u * blockDim.x;
+            a[u] = b[u] = make_float2(0.f, 0.f);
+            if (kk < nh) {
+                a[u] = __ldg(s0 + blk_index(kk, w0, n_w));
+                if (has1) b[u] = __ldg(s1 + blk_index(kk, w1, n_w));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int kk = base + u * blockDim.x;
+            if (kk < nh) {
+                z[pad16(kk)] = make_float2(a[u].x - b[u].y, a[u].y + b[u].x);
+                if (kk > 0 && n - kk >= nh) z[pad16(n - kk)] = make_float2(a[u].x + b[u].y, b[u].x - a[u].y);
+            }
+        }
+    }
+}
+
 // All passes of plan p.  The first pass reads through `first` (global memory or a shared
 // buffer outside X/Y), later passes ping-pong between X and Y.  Returns the buffer holding
 // the transform; ends with a block barrier.

@@ -3,11 +3,13 @@
 // (z = x0 + i x1); their spectra are separated with X0 = (Z[k] + conj Z[-k]) / 2,
 // X1 = (Z[k] - conj Z[-k]) / 2i.
 //
-// rows_r2c (staged) is persistent: one CTA per SM walks pairs of rows; the two rows of a
-// pair are adjacent in the grid, so one bulk copy brings both into a two-stage shared
-// buffer while the previous pair is transformed.  Planes whose rows are not a multiple of
-// 16 bytes, or too long for the staging buffers, use the direct kernel, whose first pass
-// reads global memory.
+// rows_r2c (direct, the default) takes one pair of rows per CTA: both rows are loaded into
+// shared memory with batched 16-byte loads (scalar loads when rows are not 16-byte aligned)
+// and every pass of the plan runs in shared memory; the CTA also asks L2 for the rows of the
+// CTA expected to follow it on the SM.  rows_r2c (staged, chosen by the autotuner or
+// WCSIM_ROWS_KERNEL) is persistent: one CTA per SM walks pairs of rows, and one bulk copy
+// brings both rows of the next pair into a two-stage shared buffer while the previous pair
+// is transformed.  The inverse kernels stage their Hermitian inputs the same way.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,19 +24,8 @@ constexpr int kStagedThreads = 512;
 constexpr int kDirectThreads = 256;
 constexpr size_t kMaxSmem = 227 * 1024;
 
-// First-pass source: element i of z = x0 + i x1 (zero beyond the frame).
-struct RealPairLd {
-    const float* g0;
-    const float* g1;      // nullptr: second row absent
-    int n_t;
-    __device__ __forceinline__ float2 operator()(int, int i) const
-    {
-        if (i >= n_t) return make_float2(0.f, 0.f);
-        return make_float2(__ldg(g0 + i), g1 ? __ldg(g1 + i) : 0.f);
-    }
-};
-
-// Same, from a staged pair (row 0 then row 1) in shared memory.
+// First-pass source: element i of z = x0 + i x1 (zero beyond the frame), from a pair of rows
+// (row 0 then row 1) staged in shared memory.
 struct StagedPairLd {
     const float* t;
     int n_t;
@@ -46,25 +37,47 @@ struct StagedPairLd {
     }
 };
 
-// First-pass source of the inverse: z[k] = X0[k] + i X1[k], both Hermitian, from the
-// blocked half spectra of wires w0, w1 (k < nh), conj(X[N - k]) above.
-struct HermPairLd {
-    const float2* mt;     // blocked [nkb][n_w][4]
-    int w0, w1, n_w, nh, n;
-    bool has1;
-    __device__ __forceinline__ float2 operator()(int, int k) const
-    {
-        const bool lo = k < nh;
-        const int kk = lo ? k : n - k;
-        float2 a = __ldg(mt + blk_index(kk, w0, n_w));
-        float2 b = has1 ? __ldg(mt + blk_index(kk, w1, n_w)) : make_float2(0.f, 0.f);
-        if (!lo) {
-            a.y = -a.y;
-            b.y = -b.y;
+// Stage z[i] = x0[i] + i x1[i], i < n (zero beyond n_t, x1 = 0 when g1 is null), into the
+// padded shared buffer z.  With vec (rows 16-byte aligned, n_t a multiple of 4) each thread
+// issues its 16-byte loads in batches of kU per row before storing them.  Ends without a
+// barrier.
+__device__ __forceinline__ void stage_real_pair(const float* __restrict__ g0,
+                                                const float* __restrict__ g1, int n_t, int n,
+                                                bool vec, float2* z)
+{
+    for (int i = n_t + threadIdx.x; i < n; i += blockDim.x) z[pad16(i)] = make_float2(0.f, 0.f);
+    if (vec) {
+        constexpr int kU = 6;
+        const int nq = n_t >> 2;
+        const float4* q0 = reinterpret_cast<const float4*>(g0);
+        const float4* q1 = reinterpret_cast<const float4*>(g1);
+        for (int base = threadIdx.x; base < nq; base += kU * blockDim.x) {
+            float4 a[kU], b[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = base + u * blockDim.x;
+                a[u] = b[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < nq) {
+                    a[u] = __ldg(q0 + q);
+                    if (g1) b[u] = __ldg(q1 + q);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = base + u * blockDim.x;
+                if (q < nq) {
+                    z[pad16(4 * q + 0)] = make_float2(a[u].x, b[u].x);
+                    z[pad16(4 * q + 1)] = make_float2(a[u].y, b[u].y);
+                    z[pad16(4 * q + 2)] = make_float2(a[u].z, b[u].z);
+                    z[pad16(4 * q + 3)] = make_float2(a[u].w, b[u].w);
+                }
+            }
         }
-        return make_float2(a.x - b.y, a.y + b.x);
+    } else {
+        for (int i = threadIdx.x; i < n_t; i += blockDim.x)
+            z[pad16(i)] = make_float2(__ldg(g0 + i), g1 ? __ldg(g1 + i) : 0.f);
     }
-};
+}
 
 // Separate the two real rows' half spectra and store them in the blocked layout (zeros in
 // the padding columns nh .. 4 nkb - 1).
@@ -171,15 +184,22 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
             bulk_prefetch_l2(grid + q0 * d.n_t, (uint32_t)(nq * d.n_t * sizeof(float)));
         }
     }
-    const RealPairLd src{grid + r0 * d.n_t, has1 ? grid + (r0 + 1) * d.n_t : nullptr, d.n_t};
-    const float2* z = run_plan<false, 0>(p, src, X, Y);
+    const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
+    stage_real_pair(grid + r0 * d.n_t, has1 ? grid + (r0 + 1) * d.n_t : nullptr, d.n_t, N, vec, X);
+    __syncthreads();
     if (d.clear_input) {
-        // the first pass (inside run_plan, before its barrier) has read both rows: leave
-        // the grid zero for the next rasterization (consume and clear)
+        // both rows are staged: leave the grid zero for the next rasterization (consume and
+        // clear)
         float* g0 = const_cast<float*>(grid) + r0 * d.n_t;
         const int len = (has1 ? 2 : 1) * d.n_t;
-        for (int n = threadIdx.x; n < len; n += blockDim.x) g0[n] = 0.f;
+        if (vec) {
+            float4* g4 = reinterpret_cast<float4*>(g0);
+            for (int n = threadIdx.x; n < (len >> 2); n += blockDim.x) g4[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            for (int n = threadIdx.x; n < len; n += blockDim.x) g0[n] = 0.f;
+        }
     }
+    const float2* z = run_plan<false, 0>(p, SmemLd<0>{X}, Y, X);
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
 
@@ -194,8 +214,9 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     float2* Y = X + padded_len(N);
     const int w0 = 2 * blockIdx.x, w1 = w0 + 1;
     const bool has1 = w1 < d.n_w;
-    const HermPairLd src{mt, w0, has1 ? w1 : w0, d.n_w, d.nh, N, has1};
-    const float2* z = run_plan<true, 0>(p, src, X, Y);
+    stage_herm_pair(mt, mt, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
+    __syncthreads();
+    const float2* z = run_plan<true, 0>(p, SmemLd<0>{X}, Y, X);
     float* o0 = wave + (int64_t)w0 * d.n_t;
     float* o1 = wave + (int64_t)w1 * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
