@@ -14,105 +14,68 @@
 #include <stdint.h>
 
 #include "fft_engine.cuh"
+#include "warp_fft.cuh"
 #include "wcsim_internal.cuh"
 
 namespace wcsim {
 namespace {
 
-constexpr int kWarps = 4;
-
-// Forward wire FFT of one column of a blocked spectrum: lane l loads wires l + 32 m; after
-// the call lanes k2 < M hold X[k2 + M k1] in u[k1].
-template <int M>
-__device__ __forceinline__ void warp_wire_fft(const float2* __restrict__ col, int n_w,
-                                              const float2* s_twf, float2* tr, int lane,
-                                              float2 (&u)[32])
-{
-    float2 v[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const int w = lane + 32 * m;
-        v[m] = (w < n_w) ? __ldg(col + (int64_t)w * kBlockCols) : make_float2(0.f, 0.f);
-    }
-    dft<M, false>(v);
-#pragma unroll
-    for (int k2 = 1; k2 < M; ++k2) v[k2] = cmul(v[k2], s_twf[k2 * 32 + lane]);
-    __syncwarp();
-#pragma unroll
-    for (int k2 = 0; k2 < M; ++k2) tr[k2 * 33 + lane] = v[k2];
-    __syncwarp();
-    if (lane < M) {
-#pragma unroll
-        for (int l = 0; l < 32; ++l) u[l] = tr[lane * 33 + l];
-        dft<32, false>(u);
-    }
-}
-
-template <int M>
-__device__ __forceinline__ void load_twiddles(const float2* __restrict__ tw2, float2* s_twf,
-                                              float2* s_twi)
-{
-    constexpr int N = 32 * M;
-    for (int e = threadIdx.x; e < N; e += blockDim.x) {
-        s_twf[e] = tw2[e];
-        if (s_twi) s_twi[e] = tw2[N + e];
-    }
-    __syncthreads();
-}
+constexpr int kWarps = 4;     // = kBlockCols: warp c takes column c of a block
 
 // Adjoint part A, one warp per time frequency kt: G^ = wire FFT of G's time-axis spectrum
 // (kept for part B in g2d, blocked [nkb][n_fw][4]); for every j, the wire FFT of S_j and
-// dL/dR_j(kw, kt) = conj(S^_j) G^ / n with its Hermitian mirror (-kw, -kt).  The four
-// columns of the CTA are staged in shared memory and written row by row (kw), so that each
-// row of dL/dR_j gets 4 adjacent values per store request group.
+// dL/dR_j(kw, kt) = conj(S^_j) G^ / n with its Hermitian mirror (-kw, -kt).  Each warp
+// leaves its output column in its own transpose buffer (column c at c * 33 M), from which the
+// rows of dL/dR_j are written 4 adjacent values at a time.
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ gt,
                  const float2* __restrict__ shat, float2* __restrict__ g2d, float2* __restrict__ dR,
                  float inv_n)
 {
-    constexpr int N = 32 * M;
+    constexpr int N = 32 * M, TR = 33 * M;
     __shared__ float2 s_twf[N];
-    __shared__ float2 s_tr[kWarps][33 * M];
-    // the CTA's output tile [kw][4], dynamic: N * kBlockCols float2
-    extern __shared__ __align__(128) unsigned char smraw[];
-    float2* s_out = reinterpret_cast<float2*>(smraw);
-    load_twiddles<M>(tw2, s_twf, nullptr);
+    __shared__ __align__(16) float2 s_tr[kWarps * TR];
+    load_wire_twiddles<M>(tw2, s_twf, nullptr);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb = blockIdx.x, c = warp, kt0 = kb * kBlockCols;
-    float2* tr = s_tr[warp];
+    float2* tr = s_tr + warp * TR;
+
     float2 g[32];
-    warp_wire_fft<M>(gt + (int64_t)kb * d.n_w * kBlockCols + c, d.n_w, s_twf, tr, lane, g);
+    {
+        float2 v[M];
+        load_col<M>(gt + (int64_t)kb * d.n_w * kBlockCols, c, d.n_w, lane, v);
+        warp_fft_fwd<M>(v, s_twf, tr, lane, g);
+    }
     if (lane < M) {
 #pragma unroll
-        for (int k1 = 0; k1 < 32; ++k1) s_out[(lane + M * k1) * kBlockCols + c] = g[k1];
+        for (int k1 = 0; k1 < 32; ++k1) tr[lane + M * k1] = g[k1];
     }
     __syncthreads();
-    {   // the block of G's 2D spectrum, contiguous 16-byte stores
-        const float4* src = reinterpret_cast<const float4*>(s_out);
-        float4* dst = reinterpret_cast<float4*>(g2d + (int64_t)kb * N * kBlockCols);
-        for (int e = threadIdx.x; e < N * kBlockCols / 2; e += blockDim.x) dst[e] = src[e];
-    }
+    store_tile_cols(s_tr, N, TR, g2d + (int64_t)kb * N * kBlockCols);
     if (dR == nullptr || kt0 >= d.nh) return;            // uniform per CTA
     const bool vec = (d.n_ft % 2) == 0 && (reinterpret_cast<uintptr_t>(dR) & 15) == 0;
     for (int j = 0; j < d.n_imp; ++j) {
         const int64_t blk = (int64_t)j * d.nkb + kb;
         float2 u[32];
-        __syncthreads();                                  // the output tile is read out
-        warp_wire_fft<M>(shat + blk * d.n_w * kBlockCols + c, d.n_w, s_twf, tr, lane, u);
+        {
+            float2 v[M];
+            load_col<M>(shat + blk * d.n_w * kBlockCols, c, d.n_w, lane, v);
+            __syncthreads();                              // s_tr is read out
+            warp_fft_fwd<M>(v, s_twf, tr, lane, u);
+        }
         if (lane < M) {
 #pragma unroll
             for (int k1 = 0; k1 < 32; ++k1)
-                s_out[(lane + M * k1) * kBlockCols + c] =
-                    make_float2(inv_n * (u[k1].x * g[k1].x + u[k1].y * g[k1].y),
-                                inv_n * (u[k1].x * g[k1].y - u[k1].y * g[k1].x));
+                tr[lane + M * k1] = make_float2(inv_n * (u[k1].x * g[k1].x + u[k1].y * g[k1].y),
+                                                inv_n * (u[k1].x * g[k1].y - u[k1].y * g[k1].x));
         }
         __syncthreads();
         float2* dRj = dR + (int64_t)j * N * d.n_ft;
         // direct values (kw, kt0 + cc), kt < nh: pairs of columns as 16-byte stores
         for (int e = threadIdx.x; e < N * 2; e += blockDim.x) {
             const int kw = e >> 1, cc = (e & 1) * 2, kt = kt0 + cc;
-            const float2 a = s_out[kw * kBlockCols + cc], b = s_out[kw * kBlockCols + cc + 1];
+            const float2 a = s_tr[cc * TR + kw], b = s_tr[(cc + 1) * TR + kw];
             float2* row = dRj + (int64_t)kw * d.n_ft;
             if (vec && kt + 1 < d.nh) {
                 *reinterpret_cast<float4*>(row + kt) = make_float4(a.x, a.y, b.x, b.y);
@@ -121,11 +84,12 @@ k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __res
                 if (kt + 1 < d.nh) row[kt + 1] = b;
             }
         }
-        // mirrors (-kw, n_ft - kt) for 1 <= kt <= n_ft - nh
+        // mirrors (-kw, n_ft - kt) for 1 <= kt <= n_ft - nh, adjacent threads on adjacent
+        // columns of one row
         for (int e = threadIdx.x; e < N * kBlockCols; e += blockDim.x) {
-            const int kw = e >> 2, cc = e & 3, kt = kt0 + cc;
+            const int kw = e >> 2, cc = 3 - (e & 3), kt = kt0 + cc;
             if (kt >= 1 && d.n_ft - kt >= d.nh) {
-                const float2 a = s_out[kw * kBlockCols + cc];
+                const float2 a = s_tr[cc * TR + kw];
                 dRj[(int64_t)((N - kw) % N) * d.n_ft + (d.n_ft - kt)] = make_float2(a.x, -a.y);
             }
         }
@@ -133,65 +97,52 @@ k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __res
 }
 
 // Adjoint part B, one warp per time frequency: for every j, conj(H_j) G^ transformed back
-// along the wires, written over S_j's block of shat (the time-axis spectrum of dL/dS_j); the
-// block is staged in shared memory and written as contiguous 16-byte stores.
+// along the wires, written over S_j's block of shat (the time-axis spectrum of dL/dS_j).
+// The warps' transpose buffers double as the CTA's output columns ([4][ld]).
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ g2d,
                  float2* __restrict__ shat, const float2* __restrict__ H)
 {
-    constexpr int N = 32 * M;
+    constexpr int N = 32 * M, LD = tile_ld(N);
     constexpr int TR = 32 * (M + 1);
-    static_assert(kWarps * TR >= N * kBlockCols, "output tile must fit the transpose space");
+    static_assert(kWarps * TR >= kBlockCols * LD, "output columns must fit the transpose space");
     __shared__ float2 s_twi[N];
-    // the warps' transpose buffers, reused between transforms as the CTA's output tile [w][4]
     __shared__ __align__(16) float2 s_tr[kWarps * TR];
     float2* s_out = s_tr;
-    for (int e = threadIdx.x; e < N; e += blockDim.x) s_twi[e] = tw2[N + e];
-    __syncthreads();
+    load_wire_twiddles<M>(tw2, nullptr, s_twi);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb = blockIdx.x, c = warp;
     float2* tr = s_tr + warp * TR;
+
     float2 g[32];
     if (lane < M) {
         const float2* gc = g2d + (int64_t)kb * N * kBlockCols + c;
 #pragma unroll
         for (int k1 = 0; k1 < 32; ++k1) g[k1] = __ldg(gc + (int64_t)(lane + M * k1) * kBlockCols);
     }
-    const int tile4 = d.n_w * kBlockCols / 2;             // float4 per block of n_w wires
     for (int j = 0; j < d.n_imp; ++j) {
         const int64_t blk = (int64_t)j * d.nkb + kb;
+        float2 u[32];
         if (lane < M) {
-            float2 u[32];
             const float2* hj = H + blk * N * kBlockCols + c;
 #pragma unroll
             for (int k1 = 0; k1 < 32; ++k1) {
                 const float2 h = __ldg(hj + (int64_t)(lane + M * k1) * kBlockCols);
                 u[k1] = make_float2(h.x * g[k1].x + h.y * g[k1].y, h.x * g[k1].y - h.y * g[k1].x);
             }
-            dft<32, true>(u);
-#pragma unroll
-            for (int n2 = 1; n2 < 32; ++n2) u[n2] = twiddle<true>(u[n2], s_twi[n2 * M + lane]);
-#pragma unroll
-            for (int n2 = 0; n2 < 32; ++n2) tr[n2 * (M + 1) + lane] = u[n2];
         }
-        __syncwarp();
         float2 v[M];
-#pragma unroll
-        for (int k2 = 0; k2 < M; ++k2) v[k2] = tr[lane * (M + 1) + k2];
-        __syncwarp();
-        dft<M, true>(v);
-        __syncthreads();                                  // every warp is done with its buffer
+        warp_fft_inv<M>(u, s_twi, tr, lane, v);
+        __syncthreads();                                  // every warp is done with tr
 #pragma unroll
         for (int n1 = 0; n1 < M; ++n1) {
             const int w = lane + 32 * n1;
-            if (w < d.n_w) s_out[w * kBlockCols + c] = v[n1];
+            if (w < d.n_w) s_out[c * LD + w] = v[n1];
         }
         __syncthreads();
-        float4* dst = reinterpret_cast<float4*>(shat + blk * d.n_w * kBlockCols);
-        const float4* src = reinterpret_cast<const float4*>(s_out);
-        for (int e = threadIdx.x; e < tile4; e += blockDim.x) dst[e] = src[e];
-        __syncthreads();
+        store_tile_cols(s_out, d.n_w, LD, shat + blk * d.n_w * kBlockCols);
+        __syncthreads();                                  // s_out is read out
     }
 }
 
@@ -233,17 +184,7 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
     switch (d.n_fw / 32) {
 #define WCSIM_CASE(MM)                                                                           \
     case MM: {                                                                                   \
-        const size_t smem_a = (size_t)32 * MM * kBlockCols * sizeof(float2);                    \
-        static bool attr_set = false;                                                            \
-        if (!attr_set) {                                                                         \
-            cudaError_t e = cudaFuncSetAttribute(k_wire_adjoint_a<MM>,                           \
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                                 (int)smem_a);                                   \
-            if (e) return e;                                                                     \
-            attr_set = true;                                                                     \
-        }                                                                                        \
-        k_wire_adjoint_a<MM><<<d.nkb, kWarps * 32, smem_a, s>>>(d, tw2, gt, shat, g2d, dR,      \
-                                                                inv_n);                          \
+        k_wire_adjoint_a<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, gt, shat, g2d, dR, inv_n);    \
         k_wire_adjoint_b<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, g2d, shat, H);               \
         break;                                                                                   \
     }

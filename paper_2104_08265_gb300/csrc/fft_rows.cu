@@ -39,27 +39,29 @@ struct StagedPairLd {
 
 // Stage z[i] = x0[i] + i x1[i], i < n (zero beyond n_t, x1 = 0 when g1 is null), into the
 // padded shared buffer z.  With vec (rows 16-byte aligned, n_t a multiple of 4) each thread
-// issues its 16-byte loads in batches of kU per row before storing them.  Ends without a
-// barrier.
-__device__ __forceinline__ void stage_real_pair(const float* __restrict__ g0,
-                                                const float* __restrict__ g1, int n_t, int n,
-                                                bool vec, float2* z)
+// issues its 16-byte loads in batches of kU per row before storing them.  With clear the
+// rows are left zero (consume and clear): only the groups that hold a nonzero value are
+// written, so the untouched part of a sparse grid costs no writes.  Ends without a barrier.
+__device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, int n, bool vec,
+                                                bool clear, float2* z)
 {
     for (int i = n_t + threadIdx.x; i < n; i += blockDim.x) z[pad16(i)] = make_float2(0.f, 0.f);
     if (vec) {
         constexpr int kU = 6;
         const int nq = n_t >> 2;
-        const float4* q0 = reinterpret_cast<const float4*>(g0);
-        const float4* q1 = reinterpret_cast<const float4*>(g1);
+        float4* q0 = reinterpret_cast<float4*>(g0);
+        float4* q1 = reinterpret_cast<float4*>(g1);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto nz = [](const float4& v) { return v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f; };
         for (int base = threadIdx.x; base < nq; base += kU * blockDim.x) {
             float4 a[kU], b[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int q = base + u * blockDim.x;
-                a[u] = b[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                a[u] = b[u] = zero;
                 if (q < nq) {
-                    a[u] = __ldg(q0 + q);
-                    if (g1) b[u] = __ldg(q1 + q);
+                    a[u] = q0[q];
+                    if (g1) b[u] = q1[q];
                 }
             }
 #pragma unroll
@@ -70,12 +72,22 @@ __device__ __forceinline__ void stage_real_pair(const float* __restrict__ g0,
                     z[pad16(4 * q + 1)] = make_float2(a[u].y, b[u].y);
                     z[pad16(4 * q + 2)] = make_float2(a[u].z, b[u].z);
                     z[pad16(4 * q + 3)] = make_float2(a[u].w, b[u].w);
+                    if (clear) {
+                        if (nz(a[u])) q0[q] = zero;
+                        if (g1 && nz(b[u])) q1[q] = zero;
+                    }
                 }
             }
         }
     } else {
-        for (int i = threadIdx.x; i < n_t; i += blockDim.x)
-            z[pad16(i)] = make_float2(__ldg(g0 + i), g1 ? __ldg(g1 + i) : 0.f);
+        for (int i = threadIdx.x; i < n_t; i += blockDim.x) {
+            const float x0 = g0[i], x1 = g1 ? g1[i] : 0.f;
+            z[pad16(i)] = make_float2(x0, x1);
+            if (clear) {
+                if (x0 != 0.f) g0[i] = 0.f;
+                if (x1 != 0.f) g1[i] = 0.f;
+            }
+        }
     }
 }
 
@@ -165,7 +177,7 @@ k_rows_r2c_staged(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
 // pf_ahead > 0: CTA b first asks L2 for the rows of pair b + pf_ahead (the CTA that will
 // most likely take over its slot once it retires), so that pair's first pass reads L2.
 __global__ void __launch_bounds__(kDirectThreads, 2)
-k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2* __restrict__ shat,
+k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __restrict__ shat,
                   int pf_ahead)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -185,20 +197,9 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
         }
     }
     const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
-    stage_real_pair(grid + r0 * d.n_t, has1 ? grid + (r0 + 1) * d.n_t : nullptr, d.n_t, N, vec, X);
+    float* g0 = grid + r0 * d.n_t;
+    stage_real_pair(g0, has1 ? g0 + d.n_t : nullptr, d.n_t, N, vec, d.clear_input != 0, X);
     __syncthreads();
-    if (d.clear_input) {
-        // both rows are staged: leave the grid zero for the next rasterization (consume and
-        // clear)
-        float* g0 = const_cast<float*>(grid) + r0 * d.n_t;
-        const int len = (has1 ? 2 : 1) * d.n_t;
-        if (vec) {
-            float4* g4 = reinterpret_cast<float4*>(g0);
-            for (int n = threadIdx.x; n < (len >> 2); n += blockDim.x) g4[n] = make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-            for (int n = threadIdx.x; n < len; n += blockDim.x) g0[n] = 0.f;
-        }
-    }
     const float2* z = run_plan<false, 0>(p, SmemLd<0>{X}, Y, X);
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
@@ -270,8 +271,9 @@ cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* g
         const int grid_n = n_pairs < sm_count() ? (int)n_pairs : sm_count();
         k_rows_r2c_staged<<<grid_n, kStagedThreads, smem, s>>>(d, pt, grid, shat, flags);
     } else {
+        // the kernel writes the grid only with d.clear_input (consume and clear)
         k_rows_r2c_direct<<<(unsigned)n_pairs, kDirectThreads, direct_smem(pt.n), s>>>(
-            d, pt, grid, shat, r2c_prefetch_ahead(d, grid, pt.n));
+            d, pt, const_cast<float*>(grid), shat, r2c_prefetch_ahead(d, grid, pt.n));
     }
     return cudaGetLastError();
 }
@@ -302,7 +304,7 @@ cudaError_t launch_rows_r2c_batch(const ConvDims& d, const FftPlan& pt, const fl
     const int64_t n_pairs = ((int64_t)d.n_w * d.n_imp + 1) / 2;
     const dim3 g((unsigned)n_pairs, (unsigned)n_ev);
     k_rows_r2c_direct<<<g, kDirectThreads, direct_smem(pt.n), s>>>(
-        d, pt, grid, shat, r2c_prefetch_ahead(d, grid, pt.n));
+        d, pt, const_cast<float*>(grid), shat, r2c_prefetch_ahead(d, grid, pt.n));
     return cudaGetLastError();
 }
 
