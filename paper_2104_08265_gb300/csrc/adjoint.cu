@@ -161,7 +161,7 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
     const int64_t slab = (int64_t)d.nkb * d.n_w * kBlockCols;
     stage_herm_pair(shat + j * slab, shat + j * slab, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
     __syncthreads();
-    const float2* z = run_plan<true, 0>(p, SmemLd<0>{X}, Y, X);
+    const float2* z = run_plan<true, 0>(p, FlatLd<0>{X}, Y, X);
     float* o0 = grid + ((int64_t)w0 * d.n_imp + j) * d.n_t;
     float* o1 = grid + ((int64_t)w1 * d.n_imp + j) * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {

@@ -81,7 +81,7 @@ struct wcsim_plane {
     int device = 0;
     bool grid_clean = false;    // the plane's grid is all zero (consume-and-clear state)
     bool wire_block = false;    // autotuned: use the block-level wire pass even if the warp one fits
-    int32_t kd = 64;            // autotuned: depos per rasterization CTA
+    int32_t kd = 32;            // depos per rasterization CTA (the autotuner may change it)
     bool timing = false;
     cudaEvent_t ev[kStages + 1] = {};
     cudaEvent_t evb[kBwdStages + 1] = {};

@@ -248,6 +248,15 @@ struct SmemSt {
     __device__ __forceinline__ void at(int c, int pi, float2 v) const { p[(pi << LOGB) + c] = v; }
 };
 
+// First-pass source over an unpadded shared buffer (a staged input): element (c, i) at
+// p[(i << LOGB) + c].  The first pass reads x[j + r N/R] with consecutive j on consecutive
+// lanes, which needs no padding to stay free of bank conflicts.
+template <int LOGB>
+struct FlatLd {
+    const float2* p;
+    __device__ __forceinline__ float2 operator()(int c, int i) const { return p[(i << LOGB) + c]; }
+};
+
 template <class T, class = void>
 struct IsShared { static constexpr bool value = false; };
 template <class T>
@@ -332,7 +341,7 @@ __device__ __forceinline__ void pass_any(int R, const Ld& ld, const St& st, cons
 
 // Stage the input of an inverse real-pair transform: z[k] = X0[k] + i X1[k], k < n, for two
 // Hermitian spectra given by their halves k < nh at columns w0, w1 of blocked slabs s0, s1
-// (X1 = 0 when !has1), into the padded shared buffer z.  Each stored element is read once
+// (X1 = 0 when !has1), into the unpadded shared buffer z (read back through FlatLd).  Each stored element is read once
 // and also gives the mirror z[n - k] (conj X0 + i conj X1); loads are issued in batches of
 // kU per thread before their stores.  Ends without a barrier.
 __device__ __forceinline__ void stage_herm_pair(const float2* __restrict__ s0,
@@ -355,8 +364,8 @@ __device__ __forceinline__ void stage_herm_pair(const float2* __restrict__ s0,
         for (int u = 0; u < kU; ++u) {
             const int kk = base + u * blockDim.x;
             if (kk < nh) {
-                z[pad16(kk)] = make_float2(a[u].x - b[u].y, a[u].y + b[u].x);
-                if (kk > 0 && n - kk >= nh) z[pad16(n - kk)] = make_float2(a[u].x + b[u].y, b[u].x - a[u].y);
+                z[kk] = make_float2(a[u].x - b[u].y, a[u].y + b[u].x);
+                if (kk > 0 && n - kk >= nh) z[n - kk] = make_float2(a[u].x + b[u].y, b[u].x - a[u].y);
             }
         }
     }

@@ -38,14 +38,16 @@ struct StagedPairLd {
 };
 
 // Stage z[i] = x0[i] + i x1[i], i < n (zero beyond n_t, x1 = 0 when g1 is null), into the
-// padded shared buffer z.  With vec (rows 16-byte aligned, n_t a multiple of 4) each thread
-// issues its 16-byte loads in batches of kU per row before storing them.  With clear the
+// unpadded shared buffer z (16-byte aligned; read back through FlatLd).  With vec (rows
+// 16-byte aligned, n_t a multiple of 4) each thread issues its 16-byte loads in batches of
+// kU per row before storing them.  With clear the
 // rows are left zero (consume and clear): only the groups that hold a nonzero value are
 // written, so the untouched part of a sparse grid costs no writes.  Ends without a barrier.
 __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, int n, bool vec,
                                                 bool clear, float2* z)
 {
-    for (int i = n_t + threadIdx.x; i < n; i += blockDim.x) z[pad16(i)] = make_float2(0.f, 0.f);
+    for (int i = n_t + threadIdx.x; i < n; i += blockDim.x) z[i] = make_float2(0.f, 0.f);
+    float4* z4 = reinterpret_cast<float4*>(z);
     if (vec) {
         constexpr int kU = 6;
         const int nq = n_t >> 2;
@@ -68,10 +70,8 @@ __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, i
             for (int u = 0; u < kU; ++u) {
                 const int q = base + u * blockDim.x;
                 if (q < nq) {
-                    z[pad16(4 * q + 0)] = make_float2(a[u].x, b[u].x);
-                    z[pad16(4 * q + 1)] = make_float2(a[u].y, b[u].y);
-                    z[pad16(4 * q + 2)] = make_float2(a[u].z, b[u].z);
-                    z[pad16(4 * q + 3)] = make_float2(a[u].w, b[u].w);
+                    z4[2 * q] = make_float4(a[u].x, b[u].x, a[u].y, b[u].y);
+                    z4[2 * q + 1] = make_float4(a[u].z, b[u].z, a[u].w, b[u].w);
                     if (clear) {
                         if (nz(a[u])) q0[q] = zero;
                         if (g1 && nz(b[u])) q1[q] = zero;
@@ -82,7 +82,7 @@ __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, i
     } else {
         for (int i = threadIdx.x; i < n_t; i += blockDim.x) {
             const float x0 = g0[i], x1 = g1 ? g1[i] : 0.f;
-            z[pad16(i)] = make_float2(x0, x1);
+            z[i] = make_float2(x0, x1);
             if (clear) {
                 if (x0 != 0.f) g0[i] = 0.f;
                 if (x1 != 0.f) g1[i] = 0.f;
@@ -92,7 +92,8 @@ __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, i
 }
 
 // Separate the two real rows' half spectra and store them in the blocked layout (zeros in
-// the padding columns nh .. 4 nkb - 1).
+// the padding columns nh .. 4 nkb - 1).  Consecutive lanes take consecutive frequencies, so
+// the shared reads are free of conflicts and every 4 lanes fill one 32-byte sector per row.
 __device__ __forceinline__ void store_pair_spectra(const ConvDims& d, const float2* z, int N,
                                                    int64_t r0, bool has1, float2* shat)
 {
@@ -200,7 +201,7 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __res
     float* g0 = grid + r0 * d.n_t;
     stage_real_pair(g0, has1 ? g0 + d.n_t : nullptr, d.n_t, N, vec, d.clear_input != 0, X);
     __syncthreads();
-    const float2* z = run_plan<false, 0>(p, SmemLd<0>{X}, Y, X);
+    const float2* z = run_plan<false, 0>(p, FlatLd<0>{X}, Y, X);
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
 
@@ -217,7 +218,7 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     const bool has1 = w1 < d.n_w;
     stage_herm_pair(mt, mt, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
     __syncthreads();
-    const float2* z = run_plan<true, 0>(p, SmemLd<0>{X}, Y, X);
+    const float2* z = run_plan<true, 0>(p, FlatLd<0>{X}, Y, X);
     float* o0 = wave + (int64_t)w0 * d.n_t;
     float* o1 = wave + (int64_t)w1 * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {

@@ -2,11 +2,13 @@
 // (Sec. 2.1.1 "rasterization" and "scatter adding"; drift and diffusion as in Fig. 2;
 // fluctuation with a Box-Muller normal as in Sec. 3.3.1).
 //
-// Work split.  A block owns 64 consecutive depos.  Threads 0..63 take the FP64 bin decision
-// of one depo each (one thread per depo: FP64 is scarce on this part, so it is never
-// evaluated redundantly by a whole warp) and park it in shared memory.  Each warp then walks
-// 8 of the block's depos: lanes compute the per-bin 1D weights of the patch into shared
-// memory (FP32 erf/erfc of bin-edge offsets) and stride over (row, 4-tick group) items.
+// Work split.  A block of 8 warps owns KD consecutive depos (32 by default; 64 or 128 when
+// the autotuner finds them faster; the adjoint uses 64).  Threads 0..KD-1 take the FP64 bin
+// decision of one depo each (one thread per depo: FP64 is scarce on this part, so it is
+// never evaluated redundantly by a whole warp) and park it in shared memory.  Each warp then
+// walks KD / 8 of the block's depos: lanes compute one erfc per bin edge of the patch (rows
+// and ticks together), difference them into the per-bin 1D weights in shared memory and
+// stride over (row, 4-tick group) items.
 // An item draws one Philox block for its four ticks when fluctuating (four Box-Muller
 // normals), forms Q' w_p w_t per bin and adds the four values into the grid with one
 // vector reduction.
