@@ -221,7 +221,7 @@ wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaSt
         return cuda_fail(e, "rows_r2c launch");
     mark(pl, first_mark, s);
     if (pl->tw_warp && !pl->wire_block)
-        e = launch_wire_warp(pl->dims, pl->tw_warp, pl->shat, pl->H, pl->mt, s);
+        e = launch_wire_warp(pl->dims, pl->tw_warp, pl->shat, pl->H, pl->mt, pl->flags, s);
     else
         e = launch_wire_pass(pl->dims, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s);
     if (e) return cuda_fail(e, "wire_pass launch");
@@ -288,7 +288,7 @@ wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_d
     if ((e = launch_rows_r2c_batch(d, pl->pt, pl->bgrid, pl->bshat, k, s)))
         return cuda_fail(e, "batch rows_r2c launch");
     if (pl->tw_warp && !pl->wire_block) {
-        if ((e = launch_wire_warp(d, pl->tw_warp, pl->bshat, pl->H, pl->bmt, s, k)))
+        if ((e = launch_wire_warp(d, pl->tw_warp, pl->bshat, pl->H, pl->bmt, pl->flags, s, k)))
             return cuda_fail(e, "batch wire launch");
     } else {
         for (int i = 0; i < k; ++i)
@@ -703,7 +703,7 @@ wcsim_status wcsim_plane_autotune(wcsim_plane* pl, const wcsim_depos* depos, voi
     if (!err) {
         float warp = 1e30f, block;
         if (pl->tw_warp)
-            warp = time_it([&] { return launch_wire_warp(d, pl->tw_warp, pl->shat, pl->H, pl->mt, s); });
+            warp = time_it([&] { return launch_wire_warp(d, pl->tw_warp, pl->shat, pl->H, pl->mt, pl->flags, s); });
         block = time_it([&] { return launch_wire_pass(d, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s); });
         pl->wire_block = !(warp <= block);
         rep.wire_variant = pl->wire_block ? 1 : 0;

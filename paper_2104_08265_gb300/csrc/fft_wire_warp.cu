@@ -6,15 +6,23 @@
 // padded per-warp shared tile, and a 32-point DFT in the registers of lanes k2 < M.  Lane k2
 // then holds X[k2 + M k1] for all 32 k1, multiplies by H_j and accumulates over j in
 // registers.  The inverse runs the same steps backwards (32-point DFT per lane, twiddle,
-// transpose, M-point DFT per lane) and leaves wire w = l + 32 n1 in lane l.  The only
-// synchronisation is __syncwarp around the transposes.
+// transpose, M-point DFT per lane) and leaves wire w = l + 32 n1 in lane l.
+//
+// Data movement.  S_j's column is loaded by each lane straight into registers (all M loads
+// in flight).  H_j's tile (the CTA's 4 columns, one contiguous 30 KB block for n_fw = 960)
+// is brought into shared memory by one bulk asynchronous copy on an mbarrier: the copy of
+// H_{j+1} is issued as soon as every warp has used H_j, so it lands while the warps load and
+// transform S_{j+1}.  Every wait is bounded in time; a wait that runs out raises the timeout
+// flag and the CTA leaves.  The result leaves through shared memory as 16-byte stores.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
 #include <vector>
 
+#include "async_copy.cuh"
 #include "fft_engine.cuh"
+#include "warp_fft.cuh"
 #include "wcsim_internal.cuh"
 
 namespace wcsim {
@@ -23,25 +31,36 @@ namespace {
 constexpr int kWarps = 4;            // = kBlockCols: warp c takes column c of a block
 
 template <int M>
+constexpr size_t warp_smem() { return (size_t)32 * M * kBlockCols * sizeof(float2) + 16; }
+
+template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ shat,
-            const float2* __restrict__ H, float2* __restrict__ mt)
+            const float2* __restrict__ H, float2* __restrict__ mt, int* flags)
 {
     constexpr int N = 32 * M;
     constexpr int TR = (33 * M > 32 * (M + 1)) ? 33 * M : 32 * (M + 1);
+    constexpr uint32_t kTileBytes = N * kBlockCols * sizeof(float2);
     __shared__ float2 s_twf[N];          // W^(l k2) at k2 * 32 + l
-    __shared__ float2 s_twi[N];          // W^(k2 n2) at n2 * M + k2
     __shared__ float2 s_tr[kWarps][TR];
-    for (int e = threadIdx.x; e < N; e += blockDim.x) {
-        s_twf[e] = tw2[e];
-        s_twi[e] = tw2[N + e];
-    }
-    __syncthreads();
+    // dynamic: H_j's tile [kw][4]; after the j loop the inverse twiddles, then the output
+    // columns [4][n]; an mbarrier behind it
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float2* s_h = reinterpret_cast<float2*>(smraw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(s_h + N * kBlockCols);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // grid (events, blocks): the events of one block run side by side and share H's tiles
     const int kb = blockIdx.y, c = warp;
     shat += blockIdx.x * d.ev_shat;
     mt += blockIdx.x * d.ev_mt;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(bar, kTileBytes);
+        bulk_g2s(s_h, H + (int64_t)kb * N * kBlockCols, kTileBytes, bar);
+    }
+    for (int e = threadIdx.x; e < N; e += blockDim.x) s_twf[e] = tw2[e];
+    __syncthreads();
     float2* tr = s_tr[warp];
     float2 acc[32];
 #pragma unroll
@@ -49,54 +68,51 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
 
     for (int j = 0; j < d.n_imp; ++j) {
         const int64_t blk = (int64_t)j * d.nkb + kb;
-        const float2* src = shat + blk * d.n_w * kBlockCols + c;
-        float2 v[M];
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const int w = lane + 32 * m;
-            v[m] = (w < d.n_w) ? __ldg(src + (int64_t)w * kBlockCols) : make_float2(0.f, 0.f);
+        float2 u[32];
+        bool landed;
+        {
+            float2 v[M];
+            load_col<M>(shat + blk * d.n_w * kBlockCols, c, d.n_w, lane, v);
+            landed = mbar_wait(bar, j & 1);      // H_j's tile, copied while S_j loads
+            warp_fft_fwd<M>(v, s_twf, tr, lane, u);
         }
-        dft<M, false>(v);
-#pragma unroll
-        for (int k2 = 1; k2 < M; ++k2) v[k2] = cmul(v[k2], s_twf[k2 * 32 + lane]);
-#pragma unroll
-        for (int k2 = 0; k2 < M; ++k2) tr[k2 * 33 + lane] = v[k2];
-        __syncwarp();
-        if (lane < M) {
-            float2 u[32];
-#pragma unroll
-            for (int l = 0; l < 32; ++l) u[l] = tr[lane * 33 + l];
-            dft<32, false>(u);
-            const float2* hj = H + blk * N * kBlockCols + c;
+        if (landed && lane < M) {
 #pragma unroll
             for (int k1 = 0; k1 < 32; ++k1) {
-                const float2 h = __ldg(hj + (int64_t)(lane + M * k1) * kBlockCols);
+                const float2 h = s_h[(lane + M * k1) * kBlockCols + c];
                 acc[k1].x += h.x * u[k1].x - h.y * u[k1].y;
                 acc[k1].y += h.x * u[k1].y + h.y * u[k1].x;
             }
         }
-        __syncwarp();
+        // every warp is done with s_h (and its transpose tile)
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) {
+                atomicOr(flags, kErrTimeout);
+                mbar_wait(bar, j & 1);           // the copy still in flight, bounded
+            }
+            return;
+        }
+        if (threadIdx.x == 0 && j + 1 < d.n_imp) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, kTileBytes);
+            bulk_g2s(s_h, H + (blk + d.nkb) * N * kBlockCols, kTileBytes, bar);
+        }
     }
 
     // inverse along the wire axis: lane k2 holds X[k2 + M k1]
-    if (lane < M) {
-        dft<32, true>(acc);
-#pragma unroll
-        for (int n2 = 1; n2 < 32; ++n2) acc[n2] = twiddle<true>(acc[n2], s_twi[n2 * M + lane]);
-#pragma unroll
-        for (int n2 = 0; n2 < 32; ++n2) tr[n2 * (M + 1) + lane] = acc[n2];
-    }
-    __syncwarp();
+    float2* s_twi = s_h;                         // W^(k2 n2) at n2 * M + k2
+    for (int e = threadIdx.x; e < N; e += blockDim.x) s_twi[e] = tw2[N + e];
+    __syncthreads();
     float2 v[M];
-#pragma unroll
-    for (int k2 = 0; k2 < M; ++k2) v[k2] = tr[lane * (M + 1) + k2];
-    dft<M, true>(v);
-    float2* out = mt + (int64_t)kb * d.n_w * kBlockCols + c;
+    warp_fft_inv<M>(acc, s_twi, tr, lane, v);
+    __syncthreads();                             // s_twi is read out
 #pragma unroll
     for (int n1 = 0; n1 < M; ++n1) {
         const int w = lane + 32 * n1;
-        if (w < d.n_w) out[(int64_t)w * kBlockCols] = v[n1];
+        if (w < d.n_w) s_h[c * N + w] = v[n1];
     }
+    __syncthreads();
+    store_tile_cols(s_h, d.n_w, N, mt + (int64_t)kb * d.n_w * kBlockCols);
 }
 
 #define WCSIM_WARP_M(X) X(4) X(8) X(15) X(16) X(20) X(24) X(25) X(30)
@@ -134,12 +150,23 @@ cudaError_t wire_warp_twiddles(int n_fw, float2** dev)
 }
 
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
-                             const float2* H, float2* mt, cudaStream_t s, int n_ev)
+                             const float2* H, float2* mt, int* flags, cudaStream_t s, int n_ev)
 {
     const dim3 grid((unsigned)n_ev, (unsigned)d.nkb);
     switch (d.n_fw / 32) {
-#define WCSIM_CASE(MM) \
-    case MM: k_wire_warp<MM><<<grid, kWarps * 32, 0, s>>>(d, tw2, shat, H, mt); break;
+#define WCSIM_CASE(MM)                                                                      \
+    case MM: {                                                                              \
+        static bool attr_set = false;                                                       \
+        if (!attr_set) {                                                                    \
+            cudaError_t e = cudaFuncSetAttribute(k_wire_warp<MM>,                           \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                 (int)warp_smem<MM>());                     \
+            if (e) return e;                                                                \
+            attr_set = true;                                                                \
+        }                                                                                   \
+        k_wire_warp<MM><<<grid, kWarps * 32, warp_smem<MM>(), s>>>(d, tw2, shat, H, mt, flags); \
+        break;                                                                              \
+    }
         WCSIM_WARP_M(WCSIM_CASE)
 #undef WCSIM_CASE
         default: return cudaErrorInvalidValue;

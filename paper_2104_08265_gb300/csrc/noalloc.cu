@@ -151,7 +151,7 @@ extern "C" wcsim_status wcsim_convolve_noalloc(const wcsim_geometry* geom, const
     if ((e = launch_make_hermitian(d, (const float2*)resp_c64, H,
                                    (float)(1.0 / ((double)n_fw * (double)n_ft)), s)) ||
         (e = launch_rows_r2c(d, pt, grid, shat, flags, s)) ||
-        (e = warp ? launch_wire_warp(d, tw_warp, shat, H, mt, s)
+        (e = warp ? launch_wire_warp(d, tw_warp, shat, H, mt, flags, s)
                   : launch_wire_pass(d, pw, shat, H, mt, flags, s)) ||
         (e = launch_rows_c2r(d, pt, mt, wave, s)))
         return report_error(WCSIM_ECUDA, cudaGetErrorString(e));

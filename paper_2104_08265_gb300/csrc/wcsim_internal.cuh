@@ -149,7 +149,8 @@ bool wire_warp_supported(int n_fw);
 // b < 32) and at b * M + a, FP64 rounded to FP32.  Device allocation owned by the caller.
 cudaError_t wire_warp_twiddles(int n_fw, float2** dev);
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
-                             const float2* H, float2* mt, cudaStream_t s, int n_ev = 1);
+                             const float2* H, float2* mt, int* flags, cudaStream_t s,
+                             int n_ev = 1);
 // Adjoint of the wire pass (n_fw = 32 M): reads the time-axis spectra of the forward grid
 // (shat) and of G (gt, blocked [nkb][n_w][4]); overwrites shat with the time-axis spectra
 // of dL/dS and, if dR is not null, writes dL/dR_j (full [n_imp][n_fw][n_ft] layout).  g2d
