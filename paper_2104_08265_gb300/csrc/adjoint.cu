@@ -146,6 +146,7 @@ k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __res
     }
 }
 
+template <int FIX>
 __global__ void __launch_bounds__(256, 2)
 k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* __restrict__ grid)
 {
@@ -161,7 +162,7 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
     const int64_t slab = (int64_t)d.nkb * d.n_w * kBlockCols;
     stage_herm_pair(shat + j * slab, shat + j * slab, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
     __syncthreads();
-    const float2* z = run_plan<true, 0>(p, FlatLd<0>{X}, Y, X);
+    const float2* z = run_row_plan<true, FIX>(p, FlatLd<0>{X}, Y, X);
     float* o0 = grid + ((int64_t)w0 * d.n_imp + j) * d.n_t;
     float* o1 = grid + ((int64_t)w1 * d.n_imp + j) * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
@@ -199,14 +200,16 @@ cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const flo
                                  float* grid, cudaStream_t s)
 {
     if (!g_attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_rows_c2r_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_rows_c2r_grid<kPlanRuntime>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (!e) e = cudaFuncSetAttribute(k_rows_c2r_grid<kPlan6000>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e) return e;
         g_attr = true;
     }
     const int64_t n_ctas = (int64_t)d.n_imp * ((d.n_w + 1) / 2);
-    k_rows_c2r_grid<<<(unsigned)n_ctas, 256, 2 * (size_t)padded_len(pt.n) * sizeof(float2), s>>>(
-        d, pt, shat, grid);
+    auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_c2r_grid<kPlan6000> : k_rows_c2r_grid<kPlanRuntime>;
+    k<<<(unsigned)n_ctas, 256, 2 * (size_t)padded_len(pt.n) * sizeof(float2), s>>>(d, pt, shat, grid);
     return cudaGetLastError();
 }
 

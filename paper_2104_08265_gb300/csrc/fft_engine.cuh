@@ -392,4 +392,80 @@ __device__ __forceinline__ float2* run_plan(const FftPlan& p, const FirstLd& fir
     return dst;
 }
 
+// ------------------------------------------------------------------ compile-time plans
+// One Stockham pass (single sequence) whose length N, radix R and stride NS are template
+// parameters, so that every divisor, stride and padded offset is a constant.  Same
+// arithmetic and twiddle table layout as pass_r.
+template <int R, bool INV, int N, int NS, class Ld, class St>
+__device__ __forceinline__ void pass_fixed(const Ld& ld, const St& st, const float2* __restrict__ tw)
+{
+    constexpr int NB = N / R;
+    for (int j = threadIdx.x; j < NB; j += blockDim.x) {
+        const int q = j / NS, k = j - q * NS;
+        float2 v[R];
+        if constexpr (IsShared<Ld>::value && NB % 16 == 0) {
+            const int p0 = pad16(j);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = ld.at(0, p0 + r * (NB + NB / 16));
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = ld(0, j + r * NB);
+        }
+        if constexpr (NS > 1) {
+            if (k > 0) {
+                const float2* t = tw + k;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], __ldg(t + (r - 1) * NS));
+            }
+        }
+        dft<R, INV>(v);
+        const int o = q * NS * R + k;
+        if constexpr (NS % 16 == 0 || (R == 16 && NS == 1)) {
+            constexpr int PS = (NS == 1) ? 1 : NS + NS / 16;
+            const int p0 = pad16(o);
+#pragma unroll
+            for (int r = 0; r < R; ++r) st.at(0, p0 + r * PS, v[r]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) st(0, o + r * NS, v[r]);
+        }
+    }
+}
+
+// The three passes of a plan with radices R0, R1, R2 (p's twiddle table): first -> X,
+// X -> Y, Y -> X.  Returns X; ends with a block barrier.
+template <bool INV, int R0, int R1, int R2, class FirstLd>
+__device__ __forceinline__ float2* run_plan_fixed(const FftPlan& p, const FirstLd& first,
+                                                  float2* X, float2* Y)
+{
+    constexpr int N = R0 * R1 * R2;
+    pass_fixed<R0, INV, N, 1>(first, SmemSt<0>{X}, p.tw + p.tw_off[0]);
+    __syncthreads();
+    pass_fixed<R1, INV, N, R0>(SmemLd<0>{X}, SmemSt<0>{Y}, p.tw + p.tw_off[1]);
+    __syncthreads();
+    pass_fixed<R2, INV, N, R0 * R1>(SmemLd<0>{Y}, SmemSt<0>{X}, p.tw + p.tw_off[2]);
+    __syncthreads();
+    return X;
+}
+
+// Plans with a compile-time variant: the 6000-point transform as radices 16, 25, 15.
+enum FixedPlan : int { kPlanRuntime = 0, kPlan6000 = 1 };
+
+__host__ inline int fixed_plan_of(const FftPlan& p)
+{
+    if (p.n == 6000 && p.npass == 3 && p.radix[0] == 16 && p.radix[1] == 25 && p.radix[2] == 15)
+        return kPlan6000;
+    return kPlanRuntime;
+}
+
+// All passes of a single-sequence plan, through the compile-time variant FIX when it
+// applies (FIX must equal fixed_plan_of(p)).  Same buffer convention as run_plan.
+template <bool INV, int FIX, class FirstLd>
+__device__ __forceinline__ float2* run_row_plan(const FftPlan& p, const FirstLd& first, float2* X,
+                                                float2* Y)
+{
+    if constexpr (FIX == kPlan6000) return run_plan_fixed<INV, 16, 25, 15>(p, first, X, Y);
+    else return run_plan<INV, 0>(p, first, X, Y);
+}
+
 }  // namespace wcsim

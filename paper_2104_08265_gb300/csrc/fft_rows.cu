@@ -177,6 +177,8 @@ k_rows_r2c_staged(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
 
 // pf_ahead > 0: CTA b first asks L2 for the rows of pair b + pf_ahead (the CTA that will
 // most likely take over its slot once it retires), so that pair's first pass reads L2.
+// FIX: compile-time plan variant (fixed_plan_of(p)).
+template <int FIX>
 __global__ void __launch_bounds__(kDirectThreads, 2)
 k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __restrict__ shat,
                   int pf_ahead)
@@ -201,10 +203,11 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __res
     float* g0 = grid + r0 * d.n_t;
     stage_real_pair(g0, has1 ? g0 + d.n_t : nullptr, d.n_t, N, vec, d.clear_input != 0, X);
     __syncthreads();
-    const float2* z = run_plan<false, 0>(p, FlatLd<0>{X}, Y, X);
+    const float2* z = run_row_plan<false, FIX>(p, FlatLd<0>{X}, Y, X);
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
 
+template <int FIX>
 __global__ void __launch_bounds__(kDirectThreads, 2)
 k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
 {
@@ -218,7 +221,7 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     const bool has1 = w1 < d.n_w;
     stage_herm_pair(mt, mt, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
     __syncthreads();
-    const float2* z = run_plan<true, 0>(p, FlatLd<0>{X}, Y, X);
+    const float2* z = run_row_plan<true, FIX>(p, FlatLd<0>{X}, Y, X);
     float* o0 = wave + (int64_t)w0 * d.n_t;
     float* o1 = wave + (int64_t)w1 * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
@@ -237,7 +240,7 @@ int r2c_prefetch_ahead(const ConvDims& d, const float* grid, int n)
     if ((d.n_t % 4) != 0 || (reinterpret_cast<uintptr_t>(grid) & 15) != 0) return 0;
     if (d.ev_grid % 4 != 0) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_r2c_direct, kDirectThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_r2c_direct<kPlanRuntime>, kDirectThreads,
                                                       direct_smem(n)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -251,8 +254,10 @@ cudaError_t attrs()
     if (g_attr) return cudaSuccess;
     const int mx = (int)kMaxSmem;
     cudaError_t e = cudaFuncSetAttribute(k_rows_r2c_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) e = cudaFuncSetAttribute(k_rows_r2c_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) e = cudaFuncSetAttribute(k_rows_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rows_r2c_direct<kPlanRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rows_r2c_direct<kPlan6000>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rows_c2r<kPlanRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rows_c2r<kPlan6000>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (!e) g_attr = true;
     return e;
 }
@@ -273,7 +278,9 @@ cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* g
         k_rows_r2c_staged<<<grid_n, kStagedThreads, smem, s>>>(d, pt, grid, shat, flags);
     } else {
         // the kernel writes the grid only with d.clear_input (consume and clear)
-        k_rows_r2c_direct<<<(unsigned)n_pairs, kDirectThreads, direct_smem(pt.n), s>>>(
+        auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_r2c_direct<kPlan6000>
+                                                : k_rows_r2c_direct<kPlanRuntime>;
+        k<<<(unsigned)n_pairs, kDirectThreads, direct_smem(pt.n), s>>>(
             d, pt, const_cast<float*>(grid), shat, r2c_prefetch_ahead(d, grid, pt.n));
     }
     return cudaGetLastError();
@@ -293,7 +300,8 @@ cudaError_t launch_rows_c2r_batch(const ConvDims& d, const FftPlan& pt, const fl
     cudaError_t e = attrs();
     if (e) return e;
     const dim3 grid((unsigned)((d.n_w + 1) / 2), (unsigned)n_ev);
-    k_rows_c2r<<<grid, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, mt, waves);
+    auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_c2r<kPlan6000> : k_rows_c2r<kPlanRuntime>;
+    k<<<grid, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, mt, waves);
     return cudaGetLastError();
 }
 
@@ -304,7 +312,9 @@ cudaError_t launch_rows_r2c_batch(const ConvDims& d, const FftPlan& pt, const fl
     if (e) return e;
     const int64_t n_pairs = ((int64_t)d.n_w * d.n_imp + 1) / 2;
     const dim3 g((unsigned)n_pairs, (unsigned)n_ev);
-    k_rows_r2c_direct<<<g, kDirectThreads, direct_smem(pt.n), s>>>(
+    auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_r2c_direct<kPlan6000>
+                                            : k_rows_r2c_direct<kPlanRuntime>;
+    k<<<g, kDirectThreads, direct_smem(pt.n), s>>>(
         d, pt, const_cast<float*>(grid), shat, r2c_prefetch_ahead(d, grid, pt.n));
     return cudaGetLastError();
 }
