@@ -125,10 +125,10 @@ k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __res
         const int64_t blk = (int64_t)j * d.nkb + kb;
         float2 u[32];
         if (lane < M) {
-            const float2* hj = H + blk * N * kBlockCols + c;
+            const float2* hj = H + (blk * kBlockCols + c) * N;   // column kt of H_j
 #pragma unroll
             for (int k1 = 0; k1 < 32; ++k1) {
-                const float2 h = __ldg(hj + (int64_t)(lane + M * k1) * kBlockCols);
+                const float2 h = __ldg(hj + lane + M * k1);
                 u[k1] = make_float2(h.x * g[k1].x + h.y * g[k1].y, h.x * g[k1].y - h.y * g[k1].x);
             }
         }

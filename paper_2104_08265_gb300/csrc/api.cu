@@ -67,7 +67,7 @@ struct wcsim_plane {
     float2* tw_t = nullptr;
     float2* tw_w = nullptr;
     float2* tw_warp = nullptr;  // twiddles of the one-warp-per-column wire pass (or NULL)
-    float2* H = nullptr;        // Hermitian part of R / (n_fw n_ft), blocked [n_imp][nkb][n_fw][4]
+    float2* H = nullptr;        // Hermitian part of R / (n_fw n_ft), [n_imp][4 nkb][n_fw]
     float* grid = nullptr;      // [n_rows][n_ticks]
     float2* shat = nullptr;     // time-axis spectra, blocked [n_imp][nkb][n_wires][4]
     float2* mt = nullptr;       // wire-summed spectra, blocked [nkb][n_wires][4]

@@ -102,10 +102,11 @@ k_wire_pass(ConvDims d, FftPlan p, const float2* __restrict__ shat, const float2
         const bool landed = mbar_wait(&sm.bar[s], (i >> 1) & 1);
         if (!__syncthreads_and(landed)) break;
         const float2* z = run_plan<false, LOGB>(p, StagedTileLd{sm.st_s(s), d.n_w}, sm.X, sm.Y);
-        const float2* h = sm.st_h(s, d.n_w);
+        const float2* h = sm.st_h(s, d.n_w);     // [4][N]
         for (int e = tid; e < N * kBlockCols; e += blockDim.x) {
-            const int idx = (pad16(e >> LOGB) << LOGB) + (e & (kBlockCols - 1));
-            const float2 hv = h[e], v = z[idx];
+            const int c = e & (kBlockCols - 1), kw = e >> LOGB;
+            const int idx = (pad16(kw) << LOGB) + c;
+            const float2 hv = h[c * N + kw], v = z[idx];
             float2 a = sm.acc[idx];
             a.x += hv.x * v.x - hv.y * v.y;
             a.y += hv.x * v.y + hv.y * v.x;
@@ -161,11 +162,11 @@ k_wire_direct(ConvDims d, FftPlan p, const float2* __restrict__ shat, const floa
     for (int j = 0; j < d.n_imp; ++j) {
         const float2* sj = shat + (int64_t)j * d.nkb * d.n_w * kBlockCols;
         const float2* z = run_plan<false, LG>(p, BlockedColLd<LG>{sj, d.n_w, kt0}, X, Y);
-        const float2* hj = H + (int64_t)j * d.nkb * N * kBlockCols;
+        const float2* hj = H + (int64_t)j * d.nkb * N * kBlockCols;   // [4 nkb][N]
         for (int e = threadIdx.x; e < (N << LG); e += blockDim.x) {
             const int c = e & (B - 1), kw = e >> LG;
             const int idx = (pad16(kw) << LG) + c;
-            const float2 hv = __ldg(hj + blk_index(kt0 + c, kw, N)), v = z[idx];
+            const float2 hv = __ldg(hj + (int64_t)(kt0 + c) * N + kw), v = z[idx];
             float2 a = acc[idx];
             a.x += hv.x * v.x - hv.y * v.y;
             a.y += hv.x * v.y + hv.y * v.x;
@@ -180,29 +181,35 @@ k_wire_direct(ConvDims d, FftPlan p, const float2* __restrict__ shat, const floa
     }
 }
 
+// H[j][kt][kw] = scale (R_j[kw][kt] + conj R_j[-kw][-kt]) / 2 for kt < nh, zero for the
+// padding rows nh <= kt < 4 nkb.  A 32 x 32 tile of (kw, kt) per CTA, transposed through
+// shared memory so that both the reads of R (along kt) and the writes of H (along kw) are
+// coalesced.  grid (ceil(4 nkb / 32), ceil(n_fw / 32), n_imp), block (32, 8).
 __global__ void k_make_hermitian(ConvDims d, const float2* __restrict__ R, float2* __restrict__ H,
                                  float scale)
 {
-    // blocked output element e = ((j * nkb + kb) * n_fw + kw) * 4 + c, kt = 4 kb + c
-    const int64_t total = (int64_t)d.n_imp * d.nkb * d.n_fw * kBlockCols;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(e & (kBlockCols - 1));
-        int64_t rest = e >> 2;
-        const int kw = (int)(rest % d.n_fw);
-        rest /= d.n_fw;
-        const int kb = (int)(rest % d.nkb);
-        const int j = (int)(rest / d.nkb);
-        const int kt = kb * kBlockCols + c;
+    __shared__ float2 tile[32][33];
+    const int j = blockIdx.z, kt0 = blockIdx.x * 32, kw0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int n_kt = d.nkb * kBlockCols;
+    const float f = 0.5f * scale;
+    const float2* Rj = R + (int64_t)j * d.n_fw * d.n_ft;
+    for (int i = ty; i < 32; i += blockDim.y) {
+        const int kw = kw0 + i, kt = kt0 + tx;
         float2 h = make_float2(0.f, 0.f);
-        if (kt < d.nh) {
-            const float2 a = R[((int64_t)j * d.n_fw + kw) * d.n_ft + kt];
+        if (kw < d.n_fw && kt < d.nh) {
+            const float2 a = Rj[(int64_t)kw * d.n_ft + kt];
             const int kwm = (d.n_fw - kw) % d.n_fw, ktm = (d.n_ft - kt) % d.n_ft;
-            const float2 b = R[((int64_t)j * d.n_fw + kwm) * d.n_ft + ktm];
-            const float f = 0.5f * scale;
+            const float2 b = Rj[(int64_t)kwm * d.n_ft + ktm];
             h = make_float2(f * (a.x + b.x), f * (a.y - b.y));
         }
-        H[e] = h;
+        tile[i][tx] = h;
+    }
+    __syncthreads();
+    float2* Hj = H + (int64_t)j * n_kt * d.n_fw;
+    for (int i = ty; i < 32; i += blockDim.y) {
+        const int kt = kt0 + i, kw = kw0 + tx;
+        if (kt < n_kt && kw < d.n_fw) Hj[(int64_t)kt * d.n_fw + kw] = tile[tx][i];
     }
 }
 
@@ -225,10 +232,9 @@ int sm_count()
 cudaError_t launch_make_hermitian(const ConvDims& d, const float2* resp, float2* H, float scale,
                                   cudaStream_t s)
 {
-    const int64_t total = (int64_t)d.n_imp * d.nkb * d.n_fw * kBlockCols;
-    int64_t blocks = (total + 255) / 256;
-    if (blocks > 65535 * 16) blocks = 65535 * 16;
-    k_make_hermitian<<<(unsigned)blocks, 256, 0, s>>>(d, resp, H, scale);
+    const dim3 grid((unsigned)((d.nkb * kBlockCols + 31) / 32), (unsigned)((d.n_fw + 31) / 32),
+                    (unsigned)d.n_imp);
+    k_make_hermitian<<<grid, dim3(32, 8), 0, s>>>(d, resp, H, scale);
     return cudaGetLastError();
 }
 

@@ -43,8 +43,8 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
     constexpr uint32_t kTileBytes = N * kBlockCols * sizeof(float2);
     __shared__ float2 s_twf[N];          // W^(l k2) at k2 * 32 + l
     __shared__ float2 s_tr[kWarps][TR];
-    // dynamic: H_j's tile [kw][4]; after the j loop the inverse twiddles, then the output
-    // columns [4][n]; an mbarrier behind it
+    // dynamic: H_j's tile [4][n] (one column per warp, read without bank conflicts); after
+    // the j loop the inverse twiddles, then the output columns [4][n]; an mbarrier behind it
     extern __shared__ __align__(128) unsigned char smraw[];
     float2* s_h = reinterpret_cast<float2*>(smraw);
     uint64_t* bar = reinterpret_cast<uint64_t*>(s_h + N * kBlockCols);
@@ -79,7 +79,7 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
         if (landed && lane < M) {
 #pragma unroll
             for (int k1 = 0; k1 < 32; ++k1) {
-                const float2 h = s_h[(lane + M * k1) * kBlockCols + c];
+                const float2 h = s_h[c * N + lane + M * k1];
                 acc[k1].x += h.x * u[k1].x - h.y * u[k1].y;
                 acc[k1].y += h.x * u[k1].y + h.y * u[k1].x;
             }

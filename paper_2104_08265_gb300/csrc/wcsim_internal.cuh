@@ -128,7 +128,10 @@ __host__ __device__ inline int64_t blk_index(int kt, int w, int n)
     return ((int64_t)(kt >> 2) * n + w) * kBlockCols + (kt & 3);
 }
 
-// H_j(kt, kw) = s * (R_j[kw][kt] + conj(R_j[-kw][-kt])) / 2, blocked [n_imp][nkb][n_fw][4].
+// H_j(kt, kw) = s * (R_j[kw][kt] + conj(R_j[-kw][-kt])) / 2, stored time-frequency major,
+// [n_imp][4 nkb][n_fw] (zero for kt >= nh): the 4 columns of a block are 4 contiguous rows
+// of n_fw, so one block's tile is contiguous and a warp reads a column with consecutive
+// lanes on consecutive wires.
 cudaError_t launch_make_hermitian(const ConvDims& d, const float2* resp, float2* H, float scale,
                                   cudaStream_t s);
 // Time-axis real-to-complex FFT of every grid row; writes Shat_j blocked
