@@ -24,9 +24,9 @@ constexpr int kWarps = 4;     // = kBlockCols: warp c takes column c of a block
 
 // Adjoint part A, one warp per time frequency kt: G^ = wire FFT of G's time-axis spectrum
 // (kept for part B in g2d, blocked [nkb][n_fw][4]); for every j, the wire FFT of S_j and
-// dL/dR_j(kw, kt) = conj(S^_j) G^ / n with its Hermitian mirror (-kw, -kt).  Each warp
-// leaves its output column in its own transpose buffer (column c at c * 33 M), from which the
-// rows of dL/dR_j are written 4 adjacent values at a time.
+// dL/dR_j(kw, kt) = conj(S^_j) G^ / n with its Hermitian mirror (-kw, -kt).  G^ stays in
+// shared memory; each warp leaves its output column in its own transpose buffer (column c at
+// c * 33 M), from which the rows of dL/dR_j are written 4 adjacent values at a time.
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ gt,
@@ -36,41 +36,47 @@ k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __res
     constexpr int N = 32 * M, TR = 33 * M;
     __shared__ float2 s_twf[N];
     __shared__ __align__(16) float2 s_tr[kWarps * TR];
+    // dynamic: G^'s columns [4][n] (warp c's at c * n), kept for every j
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float2* s_g = reinterpret_cast<float2*>(smraw);
     load_wire_twiddles<M>(tw2, s_twf, nullptr);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb = blockIdx.x, c = warp, kt0 = kb * kBlockCols;
     float2* tr = s_tr + warp * TR;
+    float2* gcol = s_g + c * N;
 
-    float2 g[32];
     {
-        float2 v[M];
+        float2 v[M], g[32];
         load_col<M>(gt + (int64_t)kb * d.n_w * kBlockCols, c, d.n_w, lane, v);
         warp_fft_fwd<M>(v, s_twf, tr, lane, g);
-    }
-    if (lane < M) {
-#pragma unroll
-        for (int k1 = 0; k1 < 32; ++k1) tr[lane + M * k1] = g[k1];
-    }
-    __syncthreads();
-    store_tile_cols(s_tr, N, TR, g2d + (int64_t)kb * N * kBlockCols);
-    if (dR == nullptr || kt0 >= d.nh) return;            // uniform per CTA
-    const bool vec = (d.n_ft % 2) == 0 && (reinterpret_cast<uintptr_t>(dR) & 15) == 0;
-    for (int j = 0; j < d.n_imp; ++j) {
-        const int64_t blk = (int64_t)j * d.nkb + kb;
-        float2 u[32];
-        {
-            float2 v[M];
-            load_col<M>(shat + blk * d.n_w * kBlockCols, c, d.n_w, lane, v);
-            __syncthreads();                              // s_tr is read out
-            warp_fft_fwd<M>(v, s_twf, tr, lane, u);
-        }
         if (lane < M) {
 #pragma unroll
-            for (int k1 = 0; k1 < 32; ++k1)
-                tr[lane + M * k1] = make_float2(inv_n * (u[k1].x * g[k1].x + u[k1].y * g[k1].y),
-                                                inv_n * (u[k1].x * g[k1].y - u[k1].y * g[k1].x));
+            for (int k1 = 0; k1 < 32; ++k1) gcol[lane + M * k1] = g[k1];
+        }
+    }
+    __syncthreads();
+    store_tile_cols(s_g, N, N, g2d + (int64_t)kb * N * kBlockCols);
+    if (dR == nullptr || kt0 >= d.nh) return;            // uniform per CTA
+    const bool vec = (d.n_ft % 2) == 0 && (reinterpret_cast<uintptr_t>(dR) & 15) == 0;
+    // S_j's column is loaded one impact ahead: the loads of S_{j+1} are in flight while the
+    // rows of dL/dR_j are written
+    float2 v[M];
+    load_col<M>(shat + (int64_t)kb * d.n_w * kBlockCols, c, d.n_w, lane, v);
+    for (int j = 0; j < d.n_imp; ++j) {
+        float2 u[32];
+        __syncthreads();                                  // s_tr is read out
+        warp_fft_fwd<M>(v, s_twf, tr, lane, u);
+        if (lane < M) {
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1) {
+                const float2 g = gcol[lane + M * k1];
+                tr[lane + M * k1] = make_float2(inv_n * (u[k1].x * g.x + u[k1].y * g.y),
+                                                inv_n * (u[k1].x * g.y - u[k1].y * g.x));
+            }
         }
         __syncthreads();
+        if (j + 1 < d.n_imp)
+            load_col<M>(shat + ((int64_t)(j + 1) * d.nkb + kb) * d.n_w * kBlockCols, c, d.n_w, lane, v);
         float2* dRj = dR + (int64_t)j * N * d.n_ft;
         // direct values (kw, kt0 + cc), kt < nh: pairs of columns as 16-byte stores
         for (int e = threadIdx.x; e < N * 2; e += blockDim.x) {
@@ -185,7 +191,16 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
     switch (d.n_fw / 32) {
 #define WCSIM_CASE(MM)                                                                           \
     case MM: {                                                                                   \
-        k_wire_adjoint_a<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, gt, shat, g2d, dR, inv_n);    \
+        const size_t smem_a = (size_t)32 * MM * kBlockCols * sizeof(float2);                   \
+        static bool attr_set = false;                                                           \
+        if (!attr_set) {                                                                        \
+            cudaError_t e = cudaFuncSetAttribute(k_wire_adjoint_a<MM>,                          \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                                 (int)smem_a);                                  \
+            if (e) return e;                                                                    \
+            attr_set = true;                                                                    \
+        }                                                                                       \
+        k_wire_adjoint_a<MM><<<d.nkb, kWarps * 32, smem_a, s>>>(d, tw2, gt, shat, g2d, dR, inv_n); \
         k_wire_adjoint_b<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, g2d, shat, H);               \
         break;                                                                                   \
     }
