@@ -153,7 +153,7 @@ k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __res
 }
 
 template <int FIX>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, FIX == kPlanRuntime ? 2 : 3)
 k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* __restrict__ grid)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -168,7 +168,7 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
     const int64_t slab = (int64_t)d.nkb * d.n_w * kBlockCols;
     stage_herm_pair(shat + j * slab, shat + j * slab, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
     __syncthreads();
-    const float2* z = run_row_plan<true, FIX>(p, FlatLd<0>{X}, Y, X);
+    const float2* z = run_row_plan<true, FIX, 256>(p, X, Y);
     float* o0 = grid + ((int64_t)w0 * d.n_imp + j) * d.n_t;
     float* o1 = grid + ((int64_t)w1 * d.n_imp + j) * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
@@ -223,8 +223,9 @@ cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const flo
         g_attr = true;
     }
     const int64_t n_ctas = (int64_t)d.n_imp * ((d.n_w + 1) / 2);
-    auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_c2r_grid<kPlan6000> : k_rows_c2r_grid<kPlanRuntime>;
-    k<<<(unsigned)n_ctas, 256, 2 * (size_t)padded_len(pt.n) * sizeof(float2), s>>>(d, pt, shat, grid);
+    const int fix = fixed_plan_of(pt);
+    auto k = fix == kPlan6000 ? k_rows_c2r_grid<kPlan6000> : k_rows_c2r_grid<kPlanRuntime>;
+    k<<<(unsigned)n_ctas, 256, row_plan_smem(fix, pt.n), s>>>(d, pt, shat, grid);
     return cudaGetLastError();
 }
 

@@ -448,6 +448,75 @@ __device__ __forceinline__ float2* run_plan_fixed(const FftPlan& p, const FirstL
     return X;
 }
 
+// In-place variant of pass_fixed for a block of exactly T threads: every thread first loads
+// the inputs of all its butterflies (at most ceil(N / R / T)) into registers, the block
+// synchronises, and the outputs are written over the same buffer.  One buffer per sequence
+// instead of two, for more CTAs per SM.  Ends with a block barrier.
+template <int R, bool INV, int N, int NS, int T, class Ld>
+__device__ __forceinline__ void pass_fixed_inplace(const Ld& ld, float2* buf,
+                                                   const float2* __restrict__ tw)
+{
+    constexpr int NB = N / R;
+    constexpr int NI = (NB + T - 1) / T;
+    float2 v[NI][R];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int j = threadIdx.x + i * T;
+        if (j < NB) {
+            if constexpr (IsShared<Ld>::value && NB % 16 == 0) {
+                const int p0 = pad16(j);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[i][r] = ld.at(0, p0 + r * (NB + NB / 16));
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[i][r] = ld(0, j + r * NB);
+            }
+        }
+    }
+    __syncthreads();
+    const SmemSt<0> st{buf};
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int j = threadIdx.x + i * T;
+        if (j < NB) {
+            const int q = j / NS, k = j - q * NS;
+            if constexpr (NS > 1) {
+                if (k > 0) {
+                    const float2* t = tw + k;
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[i][r] = twiddle<INV>(v[i][r], __ldg(t + (r - 1) * NS));
+                }
+            }
+            dft<R, INV>(v[i]);
+            const int o = q * NS * R + k;
+            if constexpr (NS % 16 == 0 || (R == 16 && NS == 1)) {
+                constexpr int PS = (NS == 1) ? 1 : NS + NS / 16;
+                const int p0 = pad16(o);
+#pragma unroll
+                for (int r = 0; r < R; ++r) st.at(0, p0 + r * PS, v[i][r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) st(0, o + r * NS, v[i][r]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// The three passes of plan (R0, R1, R2) in place in X (padded layout on return), the first
+// reading through `first` (which may alias X, e.g. FlatLd over the staged input).  A block of
+// exactly T threads.  Returns X.
+template <bool INV, int R0, int R1, int R2, int T, class FirstLd>
+__device__ __forceinline__ float2* run_plan_fixed_inplace(const FftPlan& p, const FirstLd& first,
+                                                          float2* X)
+{
+    constexpr int N = R0 * R1 * R2;
+    pass_fixed_inplace<R0, INV, N, 1, T>(first, X, p.tw + p.tw_off[0]);
+    pass_fixed_inplace<R1, INV, N, R0, T>(SmemLd<0>{X}, X, p.tw + p.tw_off[1]);
+    pass_fixed_inplace<R2, INV, N, R0 * R1, T>(SmemLd<0>{X}, X, p.tw + p.tw_off[2]);
+    return X;
+}
+
 // Plans with a compile-time variant: the 6000-point transform as radices 16, 25, 15.
 enum FixedPlan : int { kPlanRuntime = 0, kPlan6000 = 1 };
 
@@ -458,14 +527,22 @@ __host__ inline int fixed_plan_of(const FftPlan& p)
     return kPlanRuntime;
 }
 
-// All passes of a single-sequence plan, through the compile-time variant FIX when it
-// applies (FIX must equal fixed_plan_of(p)).  Same buffer convention as run_plan.
-template <bool INV, int FIX, class FirstLd>
-__device__ __forceinline__ float2* run_row_plan(const FftPlan& p, const FirstLd& first, float2* X,
-                                                float2* Y)
+// All passes of a single-sequence plan for a block of T threads whose first pass reads the
+// staged input in Z (through FlatLd) and whose result may land in Z or W.  The compile-time
+// variant FIX (which must equal fixed_plan_of(p)) runs in place in Z alone; the runtime plan
+// ping-pongs between W and Z.  Returns the buffer holding the transform (padded layout).
+template <bool INV, int FIX, int T>
+__device__ __forceinline__ float2* run_row_plan(const FftPlan& p, float2* Z, float2* W)
 {
-    if constexpr (FIX == kPlan6000) return run_plan_fixed<INV, 16, 25, 15>(p, first, X, Y);
-    else return run_plan<INV, 0>(p, first, X, Y);
+    if constexpr (FIX == kPlan6000) return run_plan_fixed_inplace<INV, 16, 25, 15, T>(p, FlatLd<0>{Z}, Z);
+    else return run_plan<INV, 0>(p, FlatLd<0>{Z}, W, Z);
+}
+
+// Shared bytes of a row kernel for transform length n: one padded buffer for the in-place
+// compile-time plans, two for the runtime plans.
+__host__ inline size_t row_plan_smem(int fix, int n)
+{
+    return (fix == kPlanRuntime ? 2 : 1) * (size_t)padded_len(n) * sizeof(float2);
 }
 
 }  // namespace wcsim

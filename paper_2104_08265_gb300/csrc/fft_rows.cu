@@ -179,7 +179,7 @@ k_rows_r2c_staged(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
 // most likely take over its slot once it retires), so that pair's first pass reads L2.
 // FIX: compile-time plan variant (fixed_plan_of(p)).
 template <int FIX>
-__global__ void __launch_bounds__(kDirectThreads, 2)
+__global__ void __launch_bounds__(kDirectThreads, FIX == kPlanRuntime ? 2 : 3)
 k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __restrict__ shat,
                   int pf_ahead)
 {
@@ -203,12 +203,12 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __res
     float* g0 = grid + r0 * d.n_t;
     stage_real_pair(g0, has1 ? g0 + d.n_t : nullptr, d.n_t, N, vec, d.clear_input != 0, X);
     __syncthreads();
-    const float2* z = run_row_plan<false, FIX>(p, FlatLd<0>{X}, Y, X);
+    const float2* z = run_row_plan<false, FIX, kDirectThreads>(p, X, Y);
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
 
 template <int FIX>
-__global__ void __launch_bounds__(kDirectThreads, 2)
+__global__ void __launch_bounds__(kDirectThreads, FIX == kPlanRuntime ? 2 : 3)
 k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -221,7 +221,7 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     const bool has1 = w1 < d.n_w;
     stage_herm_pair(mt, mt, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
     __syncthreads();
-    const float2* z = run_row_plan<true, FIX>(p, FlatLd<0>{X}, Y, X);
+    const float2* z = run_row_plan<true, FIX, kDirectThreads>(p, X, Y);
     float* o0 = wave + (int64_t)w0 * d.n_t;
     float* o1 = wave + (int64_t)w1 * d.n_t;
     for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
@@ -231,17 +231,15 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     }
 }
 
-size_t direct_smem(int n) { return 2 * (size_t)padded_len(n) * sizeof(float2); }
-
-// CTAs of k_rows_r2c_direct resident on the whole GPU for transform length n, when its rows
-// may be prefetched with bulk copies (16-byte aligned rows); 0 otherwise.
-int r2c_prefetch_ahead(const ConvDims& d, const float* grid, int n)
+// CTAs of the direct R2C kernel k resident on the whole GPU with smem bytes each, when its
+// rows may be prefetched with bulk copies (16-byte aligned rows); 0 otherwise.
+template <class K>
+int r2c_prefetch_ahead(const ConvDims& d, const float* grid, K k, size_t smem)
 {
     if ((d.n_t % 4) != 0 || (reinterpret_cast<uintptr_t>(grid) & 15) != 0) return 0;
     if (d.ev_grid % 4 != 0) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rows_r2c_direct<kPlanRuntime>, kDirectThreads,
-                                                      direct_smem(n)) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDirectThreads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -278,10 +276,11 @@ cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* g
         k_rows_r2c_staged<<<grid_n, kStagedThreads, smem, s>>>(d, pt, grid, shat, flags);
     } else {
         // the kernel writes the grid only with d.clear_input (consume and clear)
-        auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_r2c_direct<kPlan6000>
-                                                : k_rows_r2c_direct<kPlanRuntime>;
-        k<<<(unsigned)n_pairs, kDirectThreads, direct_smem(pt.n), s>>>(
-            d, pt, const_cast<float*>(grid), shat, r2c_prefetch_ahead(d, grid, pt.n));
+        const int fix = fixed_plan_of(pt);
+        auto k = fix == kPlan6000 ? k_rows_r2c_direct<kPlan6000> : k_rows_r2c_direct<kPlanRuntime>;
+        const size_t sm = row_plan_smem(fix, pt.n);
+        k<<<(unsigned)n_pairs, kDirectThreads, sm, s>>>(d, pt, const_cast<float*>(grid), shat,
+                                                        r2c_prefetch_ahead(d, grid, k, sm));
     }
     return cudaGetLastError();
 }
@@ -300,8 +299,9 @@ cudaError_t launch_rows_c2r_batch(const ConvDims& d, const FftPlan& pt, const fl
     cudaError_t e = attrs();
     if (e) return e;
     const dim3 grid((unsigned)((d.n_w + 1) / 2), (unsigned)n_ev);
-    auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_c2r<kPlan6000> : k_rows_c2r<kPlanRuntime>;
-    k<<<grid, kDirectThreads, direct_smem(pt.n), s>>>(d, pt, mt, waves);
+    const int fix = fixed_plan_of(pt);
+    auto k = fix == kPlan6000 ? k_rows_c2r<kPlan6000> : k_rows_c2r<kPlanRuntime>;
+    k<<<grid, kDirectThreads, row_plan_smem(fix, pt.n), s>>>(d, pt, mt, waves);
     return cudaGetLastError();
 }
 
@@ -312,10 +312,11 @@ cudaError_t launch_rows_r2c_batch(const ConvDims& d, const FftPlan& pt, const fl
     if (e) return e;
     const int64_t n_pairs = ((int64_t)d.n_w * d.n_imp + 1) / 2;
     const dim3 g((unsigned)n_pairs, (unsigned)n_ev);
-    auto k = fixed_plan_of(pt) == kPlan6000 ? k_rows_r2c_direct<kPlan6000>
-                                            : k_rows_r2c_direct<kPlanRuntime>;
-    k<<<g, kDirectThreads, direct_smem(pt.n), s>>>(
-        d, pt, const_cast<float*>(grid), shat, r2c_prefetch_ahead(d, grid, pt.n));
+    const int fix = fixed_plan_of(pt);
+    auto k = fix == kPlan6000 ? k_rows_r2c_direct<kPlan6000> : k_rows_r2c_direct<kPlanRuntime>;
+    const size_t sm = row_plan_smem(fix, pt.n);
+    k<<<g, kDirectThreads, sm, s>>>(d, pt, const_cast<float*>(grid), shat,
+                                    r2c_prefetch_ahead(d, grid, k, sm));
     return cudaGetLastError();
 }
 
