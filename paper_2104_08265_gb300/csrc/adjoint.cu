@@ -26,24 +26,28 @@ constexpr int kWarps = 4;     // = kBlockCols: warp c takes column c of a block
 // (kept for part B in g2d, blocked [nkb][n_fw][4]); for every j, the wire FFT of S_j and
 // dL/dR_j(kw, kt) = conj(S^_j) G^ / n with its Hermitian mirror (-kw, -kt).  G^ stays in
 // shared memory; each warp leaves its output column in its own transpose buffer (column c at
-// c * 33 M), from which the rows of dL/dR_j are written 4 adjacent values at a time.
+// c * TR), from which the rows of dL/dR_j are written 4 adjacent values at a time.
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ gt,
                  const float2* __restrict__ shat, float2* __restrict__ g2d, float2* __restrict__ dR,
                  float inv_n)
 {
-    constexpr int N = 32 * M, TR = 33 * M;
+    // per-warp region >= 33 M (the transpose tile) with TR = 4 mod 16: the four output
+    // columns then start 32 bytes apart modulo 128 and the row-wise reads below are free of
+    // bank conflicts
+    constexpr int N = 32 * M, TR = 33 * M + ((4 - 33 * M) % 16 + 16) % 16;
+    static_assert(TR % 16 == 4 && TR >= 33 * M, "transpose region stride");
     __shared__ float2 s_twf[N];
     __shared__ __align__(16) float2 s_tr[kWarps * TR];
-    // dynamic: G^'s columns [4][n] (warp c's at c * n), kept for every j
+    // dynamic: G^'s columns [4][ld] (warp c's at c * ld), kept for every j
     extern __shared__ __align__(128) unsigned char smraw[];
     float2* s_g = reinterpret_cast<float2*>(smraw);
     load_wire_twiddles<M>(tw2, s_twf, nullptr);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb = blockIdx.x, c = warp, kt0 = kb * kBlockCols;
     float2* tr = s_tr + warp * TR;
-    float2* gcol = s_g + c * N;
+    float2* gcol = s_g + c * tile_ld(N);
 
     {
         float2 v[M], g[32];
@@ -55,7 +59,7 @@ k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __res
         }
     }
     __syncthreads();
-    store_tile_cols(s_g, N, N, g2d + (int64_t)kb * N * kBlockCols);
+    store_tile_cols(s_g, N, tile_ld(N), g2d + (int64_t)kb * N * kBlockCols);
     if (dR == nullptr || kt0 >= d.nh) return;            // uniform per CTA
     const bool vec = (d.n_ft % 2) == 0 && (reinterpret_cast<uintptr_t>(dR) & 15) == 0;
     // S_j's column is loaded one impact ahead: the loads of S_{j+1} are in flight while the
@@ -191,7 +195,7 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
     switch (d.n_fw / 32) {
 #define WCSIM_CASE(MM)                                                                           \
     case MM: {                                                                                   \
-        const size_t smem_a = (size_t)32 * MM * kBlockCols * sizeof(float2);                   \
+        const size_t smem_a = (size_t)kBlockCols * tile_ld(32 * MM) * sizeof(float2);         \
         static bool attr_set = false;                                                           \
         if (!attr_set) {                                                                        \
             cudaError_t e = cudaFuncSetAttribute(k_wire_adjoint_a<MM>,                          \
