@@ -47,6 +47,9 @@ def parse():
                     help="skip the 64-event batched run (wcsim_batch_run vs 64 wcsim_run calls)")
     ap.add_argument("--soak-s", type=float, default=0.5,
                     help="untimed load before the timed loop, so the clock sampler sees the GPU busy")
+    ap.add_argument("--write-traffic", nargs="+", metavar="NCU_REP",
+                    help="no run: read DRAM bytes per launch from these ncu reports (ncu -i, raw "
+                         "page) and write profiles/dram_traffic.json for the current sources")
     return ap.parse_args()
 
 
@@ -75,15 +78,38 @@ def config(name, g, d, prm, extra=None):
 
 # ---------------------------------------------------------------- byte / flop models
 def stage_bytes(g, n_depos, mean_bins):
-    """Algorithmic (compulsory) bytes per launch of each stage."""
+    """Algorithmic (compulsory) bytes per launch of each forward stage.  The grid is cleared
+    inside rows_r2c as it is read (consume and clear), so after the first run the zero stage
+    moves nothing; the clearing writes are not counted in rows_r2c either."""
     rows = g.n_rows
     nh = g.n_ticks // 2 + 1
     return {
-        "zero": rows * g.n_ticks * 4,
+        "zero": 0,
         "rasterize": n_depos * (32 + 4 * mean_bins),
         "rows_r2c": rows * g.n_ticks * 4 + rows * nh * 8,
         "wire_pass": rows * nh * 8 + g.n_imp * g.n_wires * nh * 8 + g.n_wires * nh * 8,
         "rows_c2r": g.n_wires * nh * 8 + g.n_wires * g.n_ticks * 4,
+    }
+
+
+def backward_stage_bytes(g, n_depos, mean_bins):
+    """Algorithmic bytes per launch of each backward stage (wcsim_run_backward with dL/dR,
+    n_fw = n_wires, n_ft = n_ticks): S recomputed, S and G transformed, the wire adjoint
+    (reads S^, G^ and H; writes dL/dR in full [n_imp][n_fw][n_ft] and dL/dS^), the inverse
+    time FFT of dL/dS and the per-depo gather."""
+    rows = g.n_rows
+    nh = g.n_ticks // 2 + 1
+    spec = rows * nh * 8                    # S^ or dL/dS^, all impact positions
+    wspec = g.n_wires * nh * 8              # one plane-wide half spectrum (G^, M~)
+    return {
+        "bwd_zero": 0,                          # the preceding wcsim_run left the grid clear
+        "bwd_rasterize": n_depos * (32 + 4 * mean_bins),
+        "bwd_r2c_S": rows * g.n_ticks * 4 + spec,
+        "bwd_r2c_G": g.n_wires * g.n_ticks * 4 + wspec,
+        "bwd_wire_adjoint": (spec + wspec + g.n_imp * g.n_wires * g.n_ticks * 8   # part A
+                             + spec + g.n_imp * g.n_wires * nh * 8 + spec),          # part B
+        "bwd_c2r_dS": spec + rows * g.n_ticks * 4,
+        "bwd_depo_adjoint": n_depos * (32 + 20 + 4 * mean_bins),
     }
 
 
@@ -109,20 +135,60 @@ STAGE_KERNEL = {"rows_r2c": "k_rows_r2c_direct", "wire_pass": "k_wire_warp",
                 "rasterize": "k_rasterize", "rows_c2r": "k_rows_c2r"}
 
 
-def ncu_traffic(stage):
-    """DRAM bytes per launch of the stage's kernel from the committed ncu record, or None
-    when the CUDA sources changed since the counters were taken."""
+def source_hash():
     import glob
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if not os.path.exists(path) or stage not in STAGE_KERNEL:
-        return None
-    rec = json.load(open(path))
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2104_08265_gb300", "csrc")
     for f in sorted(glob.glob(os.path.join(src, "*.cu")) + glob.glob(os.path.join(src, "*.cuh"))):
         h.update(open(f, "rb").read())
-    if h.hexdigest() != rec.get("source_sha256"):
+    return h.hexdigest()
+
+
+def kernel_base(name):
+    """'void wcsim::<unnamed>::k_rows_r2c_direct<1>(wcsim::ConvDims, ...)' (ncu may shorten
+    the namespace part) -> 'k_rows_r2c_direct'."""
+    name = name.split("(")[0].split("::")[-1]
+    return name.split("<")[0].split()[-1]
+
+
+def write_traffic(reps):
+    """DRAM bytes (read + write) per launch of every kernel captured in the ncu reports,
+    averaged over launches, into profiles/dram_traffic.json with the hash of the sources."""
+    import csv
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    acc = {}
+    for rep in reps:
+        out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True,
+                             text=True, check=True).stdout
+        rows = list(csv.reader(out.splitlines()))
+        hdr, units = rows[0], rows[1]
+        ki = hdr.index("Kernel Name")
+        cols = [hdr.index("dram__bytes_read.sum"), hdr.index("dram__bytes_write.sum")]
+        for r in rows[2:]:
+            b = sum(float(r[c].replace(",", "")) * scale[units[c]] for c in cols)
+            acc.setdefault(kernel_base(r[ki]), []).append(b)
+    rec = {"_about": "DRAM bytes (read + write) per launch, mean over the captured launches, "
+                     "from ncu --set full captures of the 960-wire x 6000-tick plane with 100k "
+                     "depos; valid only while the CUDA sources hash to source_sha256.",
+           "reports": [os.path.basename(r) for r in reps],
+           "source_sha256": source_hash(),
+           "bytes_per_launch": {k: float(np.mean(v)) for k, v in sorted(acc.items())}}
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(json.dumps(rec["bytes_per_launch"]))
+
+
+def ncu_traffic(stage):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu record, or None
+    when the CUDA sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path) or stage not in STAGE_KERNEL:
+        return None
+    rec = json.load(open(path))
+    if source_hash() != rec.get("source_sha256"):
         return None
     return rec["bytes_per_launch"].get(STAGE_KERNEL[stage])
 
@@ -342,10 +408,8 @@ def run_gpu(args):
         for _ in range(20):
             plane.run(dd, out=wave)
         torch.cuda.synchronize()
-    plane.set_timing(True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage_ms = {k: [] for k in wcsim.STAGES}
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -355,16 +419,23 @@ def run_gpu(args):
         starts[i].record(stream)
         plane.run(dd, out=wave)
         ends[i].record(stream)
-        torch.cuda.synchronize()
-        for k, v in plane.stage_times().items():
-            stage_ms[k].append(v)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    plane.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # per-stage breakdown, in a separate loop (the library's stage events stay out of the
+    # timed steps above)
+    plane.set_timing(True)
+    stage_ms = {k: [] for k in wcsim.STAGES}
+    for i in range(args.steps):
+        flush.zero_()
+        plane.run(dd, out=wave)
+        torch.cuda.synchronize()
+        for k, v in plane.stage_times().items():
+            stage_ms[k].append(v)
+    plane.set_timing(False)
     tot_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([tot_ms], device="cuda")
@@ -458,9 +529,11 @@ def run_gpu(args):
         return
     hbm, peak_kind = peaks()
     sb = stage_bytes(g, len(d), mean_bins)
+    bsb = backward_stage_bytes(g, len(d), mean_bins)
     avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     stages = {k: {"ms": avg[k], "GB/s": sb[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None,
                   "alg_bytes": sb[k]} for k in avg}
+    stages["zero"]["note"] = "no-op: the grid is cleared inside rows_r2c (consume and clear)"
     dom = max(avg, key=avg.get)
     ach = sb[dom] / (avg[dom] * 1e-3) / 1e9
     per_step = tot_ms / args.steps
@@ -474,6 +547,9 @@ def run_gpu(args):
                                "fwd_bwd": (ws * 1e3 / fb_ms) if fb_ms else None},
         "fwd_bwd_ms_per_step": fb_ms,
         "backward_stages_ms": bwd_stages,
+        "backward_stages": ({k: {"ms": v, "alg_bytes": bsb[k],
+                                 "GB/s": bsb[k] / (v * 1e-3) / 1e9 if v > 0 else None}
+                             for k, v in bwd_stages.items()} if bwd_stages else None),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm,
                      "unit": "GB/s", "frac": ach / hbm, "traffic": ncu_traffic(dom),
                      "alg_bytes": sb[dom],
@@ -501,7 +577,9 @@ def run_gpu(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.write_traffic:
+        write_traffic(args.write_traffic)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
