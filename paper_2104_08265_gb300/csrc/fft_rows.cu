@@ -94,24 +94,32 @@ __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, i
 // Separate the two real rows' half spectra and store them in the blocked layout (zeros in
 // the padding columns nh .. 4 nkb - 1).  Consecutive lanes take consecutive frequencies, so
 // the shared reads are free of conflicts and every 4 lanes fill one 32-byte sector per row.
+// The block size is a multiple of 16, so the output addresses and the padded shared indices
+// of k and N - k advance by constants from one iteration to the next.
 __device__ __forceinline__ void store_pair_spectra(const ConvDims& d, const float2* z, int N,
                                                    int64_t r0, bool has1, float2* shat)
 {
     const int w0 = (int)(r0 / d.n_imp), j0 = (int)(r0 % d.n_imp);
     const int64_t r1 = r0 + 1;
     const int w1 = (int)(r1 / d.n_imp), j1 = (int)(r1 % d.n_imp);
-    float2* o0 = shat + (int64_t)j0 * d.nkb * d.n_w * kBlockCols;
-    float2* o1 = shat + (int64_t)j1 * d.nkb * d.n_w * kBlockCols;
-    for (int k = threadIdx.x; k < d.nkb * kBlockCols; k += blockDim.x) {
+    const int nk = d.nkb * kBlockCols, nh = d.nh;
+    const int k0 = threadIdx.x;
+    const int64_t row = (int64_t)d.n_w * kBlockCols;                  // one block of columns
+    const int64_t step = (int64_t)(blockDim.x / kBlockCols) * row;
+    float2* q0 = shat + (int64_t)j0 * d.nkb * row + (k0 >> 2) * row + w0 * kBlockCols + (k0 & 3);
+    float2* q1 = shat + (int64_t)j1 * d.nkb * row + (k0 >> 2) * row + w1 * kBlockCols + (k0 & 3);
+    const int dp = blockDim.x + (blockDim.x >> 4);                      // pad16 step
+    int pa = pad16(k0), pb = pad16(N - k0);
+    for (int k = k0; k < nk; k += blockDim.x, q0 += step, q1 += step, pa += dp, pb -= dp) {
         float2 x0 = make_float2(0.f, 0.f), x1 = x0;
-        if (k < d.nh) {
-            const float2 a = z[pad16(k)];
-            const float2 b = z[pad16(k == 0 ? 0 : N - k)];
+        if (k < nh) {
+            const float2 a = z[pa];
+            const float2 b = z[k == 0 ? 0 : pb];
             x0 = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
             x1 = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
         }
-        o0[blk_index(k, w0, d.n_w)] = x0;
-        if (has1) o1[blk_index(k, w1, d.n_w)] = x1;
+        *q0 = x0;
+        if (has1) *q1 = x1;
     }
 }
 
