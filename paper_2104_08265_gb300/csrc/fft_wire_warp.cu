@@ -28,36 +28,43 @@
 namespace wcsim {
 namespace {
 
-constexpr int kWarps = 4;            // = kBlockCols: warp c takes column c of a block
+// A CTA takes CW of the 4 columns of a block, one warp per column (CW = 2: the 751 blocks of
+// a 6000-tick plane become 1502 CTAs, which fill whole waves of the 5 CTAs that fit an SM).
+constexpr int kCols = 2;
 
-template <int M>
-constexpr size_t warp_smem() { return (size_t)32 * M * kBlockCols * sizeof(float2) + 16; }
+template <int M, int CW>
+constexpr size_t warp_smem() { return (size_t)32 * M * CW * sizeof(float2) + 16; }
 
-template <int M>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+template <int M, int CW>
+__global__ void __launch_bounds__(CW * 32, CW == 4 ? 3 : 5)
 k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ shat,
             const float2* __restrict__ H, float2* __restrict__ mt, int* flags)
 {
+    static_assert(CW == 2 || CW == 4, "columns per CTA");
     constexpr int N = 32 * M;
     constexpr int TR = (33 * M > 32 * (M + 1)) ? 33 * M : 32 * (M + 1);
-    constexpr uint32_t kTileBytes = N * kBlockCols * sizeof(float2);
+    constexpr uint32_t kTileBytes = N * CW * sizeof(float2);
     __shared__ float2 s_twf[N];          // W^(l k2) at k2 * 32 + l
-    __shared__ float2 s_tr[kWarps][TR];
-    // dynamic: H_j's tile [4][n] (one column per warp, read without bank conflicts); after
-    // the j loop the inverse twiddles, then the output columns [4][n]; an mbarrier behind it
+    __shared__ float2 s_tr[CW][TR];
+    // dynamic: H_j's tile [CW][n] (one column per warp, read without bank conflicts); after
+    // the j loop the inverse twiddles, then the output columns [CW][n]; an mbarrier behind it
     extern __shared__ __align__(128) unsigned char smraw[];
     float2* s_h = reinterpret_cast<float2*>(smraw);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(s_h + N * kBlockCols);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(s_h + N * CW);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // grid (events, blocks): the events of one block run side by side and share H's tiles
-    const int kb = blockIdx.y, c = warp;
+    // grid (events, blocks x parts): the events of one block run side by side and share H's
+    // tiles; columns c0 .. c0 + CW - 1 of block kb
+    constexpr int kParts = kBlockCols / CW;
+    const int kb = blockIdx.y / kParts, c0 = (blockIdx.y % kParts) * CW, c = c0 + warp;
     shat += blockIdx.x * d.ev_shat;
     mt += blockIdx.x * d.ev_mt;
+    // rows 4 kb + c0 .. of H_j (time-frequency major): one contiguous tile
+    auto h_tile = [&](int64_t blk) { return H + (blk * kBlockCols + c0) * N; };
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
         mbar_arrive_expect_tx(bar, kTileBytes);
-        bulk_g2s(s_h, H + (int64_t)kb * N * kBlockCols, kTileBytes, bar);
+        bulk_g2s(s_h, h_tile(kb), kTileBytes, bar);
     }
     for (int e = threadIdx.x; e < N; e += blockDim.x) s_twf[e] = tw2[e];
     __syncthreads();
@@ -79,7 +86,7 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
         if (landed && lane < M) {
 #pragma unroll
             for (int k1 = 0; k1 < 32; ++k1) {
-                const float2 h = s_h[c * N + lane + M * k1];
+                const float2 h = s_h[warp * N + lane + M * k1];
                 acc[k1].x += h.x * u[k1].x - h.y * u[k1].y;
                 acc[k1].y += h.x * u[k1].y + h.y * u[k1].x;
             }
@@ -95,7 +102,7 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
         if (threadIdx.x == 0 && j + 1 < d.n_imp) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, kTileBytes);
-            bulk_g2s(s_h, H + (blk + d.nkb) * N * kBlockCols, kTileBytes, bar);
+            bulk_g2s(s_h, h_tile(blk + d.nkb), kTileBytes, bar);
         }
     }
 
@@ -109,10 +116,18 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
 #pragma unroll
     for (int n1 = 0; n1 < M; ++n1) {
         const int w = lane + 32 * n1;
-        if (w < d.n_w) s_h[c * N + w] = v[n1];
+        if (w < d.n_w) s_h[warp * N + w] = v[n1];
     }
     __syncthreads();
-    store_tile_cols(s_h, d.n_w, N, mt + (int64_t)kb * d.n_w * kBlockCols);
+    float2* out = mt + (int64_t)kb * d.n_w * kBlockCols;
+    if constexpr (CW == 4) {
+        store_tile_cols(s_h, d.n_w, N, out);
+    } else {
+        for (int w = threadIdx.x; w < d.n_w; w += blockDim.x) {
+            const float2 a = s_h[w], b = s_h[N + w];
+            *reinterpret_cast<float4*>(out + (int64_t)w * kBlockCols + c0) = make_float4(a.x, a.y, b.x, b.y);
+        }
+    }
 }
 
 #define WCSIM_WARP_M(X) X(4) X(8) X(15) X(16) X(20) X(24) X(25) X(30)
@@ -152,20 +167,21 @@ cudaError_t wire_warp_twiddles(int n_fw, float2** dev)
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
                              const float2* H, float2* mt, int* flags, cudaStream_t s, int n_ev)
 {
-    const dim3 grid((unsigned)n_ev, (unsigned)d.nkb);
+    const dim3 grid((unsigned)n_ev, (unsigned)(d.nkb * (kBlockCols / kCols)));
     switch (d.n_fw / 32) {
-#define WCSIM_CASE(MM)                                                                      \
-    case MM: {                                                                              \
-        static bool attr_set = false;                                                       \
-        if (!attr_set) {                                                                    \
-            cudaError_t e = cudaFuncSetAttribute(k_wire_warp<MM>,                           \
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                 (int)warp_smem<MM>());                     \
-            if (e) return e;                                                                \
-            attr_set = true;                                                                \
-        }                                                                                   \
-        k_wire_warp<MM><<<grid, kWarps * 32, warp_smem<MM>(), s>>>(d, tw2, shat, H, mt, flags); \
-        break;                                                                              \
+#define WCSIM_CASE(MM)                                                                         \
+    case MM: {                                                                                 \
+        static bool attr_set = false;                                                          \
+        if (!attr_set) {                                                                       \
+            cudaError_t e = cudaFuncSetAttribute(k_wire_warp<MM, kCols>,                       \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                                 (int)warp_smem<MM, kCols>());                 \
+            if (e) return e;                                                                   \
+            attr_set = true;                                                                   \
+        }                                                                                      \
+        k_wire_warp<MM, kCols><<<grid, kCols * 32, warp_smem<MM, kCols>(), s>>>(d, tw2, shat, H, \
+                                                                                mt, flags);    \
+        break;                                                                                 \
     }
         WCSIM_WARP_M(WCSIM_CASE)
 #undef WCSIM_CASE
