@@ -5,10 +5,11 @@
 // Work split.  A block of 8 warps owns KD consecutive depos (32 by default; 64 or 128 when
 // the autotuner finds them faster; the adjoint uses 64).  Threads 0..KD-1 take the FP64 bin
 // decision of one depo each (one thread per depo: FP64 is scarce on this part, so it is
-// never evaluated redundantly by a whole warp) and park it in shared memory.  Each warp then
-// walks KD / 8 of the block's depos: lanes compute one erfc per bin edge of the patch (rows
-// and ticks together), difference them into the per-bin 1D weights in shared memory and
-// stride over (row, 4-tick group) items.
+// never evaluated redundantly by a whole warp) and park it in shared memory.  Each half warp
+// then walks KD / 16 of the block's depos (the two halves of a warp work on two depos side
+// by side): its lanes compute one erfc per bin edge of the patch (rows and ticks together),
+// difference them into the per-bin 1D weights in shared memory and stride over (row,
+// 4-tick group) items.
 // An item draws one Philox block for its four ticks when fluctuating (four Box-Muller
 // normals), forms Q' w_p w_t per bin and adds the four values into the grid with one
 // vector reduction.
@@ -144,19 +145,27 @@ __device__ __forceinline__ float bin_mass(int64_t koff, float frac, float s, flo
     return 1.0f - 0.5f * (ea + eb);
 }
 
+// Lanes per depo group: a half warp takes one depo, so that the two halves of a warp work
+// on two depos side by side (a patch of ~17 rows x 3 four-tick groups fills three rounds
+// of 16 lanes better than two rounds of 32).
+constexpr int kGroup = 16;
+
 // The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps.
 template <int KD>
 __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const DepoArrays& d,
                                                 float* __restrict__ grid, int* flags, int64_t blk)
 {
     static_assert(KD <= kWarps * 32, "one deciding thread per depo");
+    constexpr int G = kGroup, NG = kWarps * 32 / G;
     __shared__ Decision s_dec[KD];
-    __shared__ float s_wp[kWarps][kWmax];
+    __shared__ float s_wp[NG][kWmax];
     // tick weights of a tile laid out on 4-tick groups: slot p is tick 4 q_lo + p (zero
     // outside the window), so that an item reads its four weights with one 16-byte load
-    __shared__ __align__(16) float s_wt[kWarps][kWmax + 8];
-    __shared__ float s_edge[kWarps][2 * (kWmax + 1)];    // row edges, then tick edges
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ __align__(16) float s_wt[NG][kWmax + 8];
+    __shared__ float s_edge[NG][2 * (kWmax + 1)];        // row edges, then tick edges
+    const int gl = threadIdx.x % G, grp = threadIdx.x / G;
+    // the lanes of this group within its warp
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
     const int64_t base = blk * KD;
     if (threadIdx.x < KD) {
         Decision r;
@@ -171,11 +180,11 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     __syncthreads();
     // 16-byte reductions need 4-tick groups to start on 16-byte boundaries
     const bool vec4 = ((c.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
-    float* wp = s_wp[warp];
-    float* wt = s_wt[warp];
-    float* ed = s_edge[warp];
+    float* wp = s_wp[grp];
+    float* wt = s_wt[grp];
+    float* ed = s_edge[grp];
 
-    for (int i = warp; i < KD; i += kWarps) {
+    for (int i = grp; i < KD; i += NG) {
         const Decision dd = s_dec[i];
         if (!dd.ok || !(dd.qatt > 0.0f)) continue;    // nothing, or Q' underflowed
         // u = offset_in_bins * bin / (sqrt(2) sigma); sigma == 0 puts all weight in the
@@ -189,7 +198,7 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
             for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kWmax) {
                 const int nt = min(kWmax, dd.k_hi - k0 + 1);
                 // one erfc per bin edge: nr + 1 row edges and nt + 1 tick edges
-                for (int e = lane; e < nr + nt + 2; e += 32) {
+                for (int e = gl; e < nr + nt + 2; e += G) {
                     float v;
                     if (e <= nr) v = edge_erfc((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p);
                     else v = edge_erfc((int64_t)(k0 + e - nr - 1) - dd.i0t, dd.frac_t, s_t);
@@ -198,8 +207,8 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                 const int q_lo = k0 >> 2, q_hi = (k0 + nt - 1) >> 2;
                 const int nq = q_hi - q_lo + 1;
                 const int koff = k0 - 4 * q_lo;            // slot of tick k0
-                __syncwarp();
-                for (int e = lane; e < nr + 4 * nq; e += 32) {
+                __syncwarp(gmask);
+                for (int e = gl; e < nr + 4 * nq; e += G) {
                     if (e < nr) {
                         wp[e] = dd.qatt * ((dd.sp > 0.0f)
                                     ? bin_mass((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p, ed[e], ed[e + 1])
@@ -214,9 +223,9 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                         wt[e - nr] = w;
                     }
                 }
-                __syncwarp();
+                __syncwarp(gmask);
                 const float inv_nq = 1.0f / (float)nq;
-                for (int item = lane; item < nr * nq; item += 32) {
+                for (int item = gl; item < nr * nq; item += G) {
                     const int ir = (int)(((float)item + 0.5f) * inv_nq);
                     const int iq = item - ir * nq;
                     const int64_t r = r0 + ir;
@@ -247,7 +256,7 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                         }
                     }
                 }
-                __syncwarp();
+                __syncwarp(gmask);
             }
         }
     }
