@@ -281,31 +281,38 @@ k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
     rasterize_block<KD>(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
 }
 
-__device__ __forceinline__ float warp_sum(float v)
+// Sum over the G lanes of a lane group (mask: the group's lanes), in every lane of it.
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned mask)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
 }
 
-// Per depo: recompute the patch weights and their mu / sigma derivatives, gather dL/dS over
-// the patch and apply the chain rule through Q' = Q exp(-t_d / tau), t_a = t + t_d and
-// sigma = sqrt(2 D t_d).  The global sums are reduced per block in FP64.
+// Per depo (a half warp each): recompute the patch weights and their mu / sigma derivatives,
+// gather dL/dS over the patch and apply the chain rule through Q' = Q exp(-t_d / tau),
+// t_a = t + t_d and sigma = sqrt(2 D t_d).  The global sums are reduced per block in FP64.
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, DepoGrads g,
                int* flags)
 {
+    // a half warp per depo (as in the forward); patch tiles of at most kTile rows x kTile
+    // ticks
+    constexpr int G = kGroup, NG = kWarps * 32 / G, kTile = 32;
     __shared__ Decision s_dec[kDepos];
     // wp, dwp/dmu, dwp/dsig per row; wt, dwt/dmu, dwt/dsig per tick laid out on 4-tick
     // groups (slot p is tick 4 q_lo + p, zero outside the window)
-    __shared__ float s_w[kWarps][3][kWmax];
-    __shared__ __align__(16) float s_t[kWarps][3][kWmax + 8];
+    __shared__ float s_w[NG][3][kTile];
+    __shared__ __align__(16) float s_t[NG][3][kTile + 8];
     // per bin edge u: erfc|u|, phi(u) = exp(-u^2) / sqrt(2 pi) and u phi(u); rows then ticks
-    __shared__ float s_e[kWarps][3][2 * (kWmax + 1)];
+    __shared__ float s_e[NG][3][2 * (kTile + 1)];
     // per depo, the FP32 factors of its terms in the three global sums (dL/dsigma_L,
     // sigma_L; dL/dsigma_T, sigma_T; dL/dQ', Q'), zero for depos that add nothing
     __shared__ float s_gt[kDepos][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = threadIdx.x % G, grp = threadIdx.x / G;
+    const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
     const int64_t base = (int64_t)blockIdx.x * kDepos;
     if (threadIdx.x < kDepos) {
         Decision r;
@@ -320,18 +327,18 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
         for (int k = 0; k < 6; ++k) s_gt[threadIdx.x][k] = 0.0f;
     }
     __syncthreads();
-    float* wp = s_w[warp][0];
-    float* wpm = s_w[warp][1];
-    float* wps = s_w[warp][2];
-    float* wt = s_t[warp][0];
-    float* wtm = s_t[warp][1];
-    float* wts = s_t[warp][2];
-    float* eE = s_e[warp][0];
-    float* eP = s_e[warp][1];
-    float* eU = s_e[warp][2];
+    float* wp = s_w[grp][0];
+    float* wpm = s_w[grp][1];
+    float* wps = s_w[grp][2];
+    float* wt = s_t[grp][0];
+    float* wtm = s_t[grp][1];
+    float* wts = s_t[grp][2];
+    float* eE = s_e[grp][0];
+    float* eP = s_e[grp][1];
+    float* eU = s_e[grp][2];
     const bool vec4 = ((c.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(dgrid) & 15) == 0);
 
-    for (int i = warp; i < kDepos; i += kWarps) {
+    for (int i = grp; i < kDepos; i += NG) {
         const int64_t gi = base + i;
         if (gi >= d.n) break;
         const Decision dd = s_dec[i];
@@ -341,14 +348,14 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
             const float s_t = (dd.st > 0.0f) ? c.dt_f / (1.41421356237309505f * dd.st) : 0.0f;
             const float isp = (dd.sp > 0.0f) ? 1.0f / dd.sp : 0.0f;
             const float ist = (dd.st > 0.0f) ? 1.0f / dd.st : 0.0f;
-            for (int32_t r0 = dd.r_lo; r0 <= dd.r_hi; r0 += kWmax) {
-                const int nr = min(kWmax, dd.r_hi - r0 + 1);
-                for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kWmax) {
-                    const int nt = min(kWmax, dd.k_hi - k0 + 1);
+            for (int32_t r0 = dd.r_lo; r0 <= dd.r_hi; r0 += kTile) {
+                const int nr = min(kTile, dd.r_hi - r0 + 1);
+                for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kTile) {
+                    const int nt = min(kTile, dd.k_hi - k0 + 1);
                     const int q_lo = k0 >> 2, q_hi = (k0 + nt - 1) >> 2, nq = q_hi - q_lo + 1;
                     const int koff = k0 - 4 * q_lo;        // slot of tick k0
                     // edge terms: nr + 1 row edges, nt + 1 tick edges
-                    for (int e = lane; e < nr + nt + 2; e += 32) {
+                    for (int e = gl; e < nr + nt + 2; e += G) {
                         const float u = (e <= nr) ? ((float)((int64_t)(r0 + e) - dd.i0p) - dd.frac_p) * s_p
                                                   : ((float)((int64_t)(k0 + e - nr - 1) - dd.i0t) - dd.frac_t) * s_t;
                         const float ph = 0.398942280401432678f * expf(-u * u);
@@ -356,10 +363,10 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                         eP[e] = ph;
                         eU[e] = u * ph;
                     }
-                    __syncwarp();
+                    __syncwarp(gmask);
                     // w = Phi(b') - Phi(a'); dw/dmu = -(phi(b') - phi(a')) / sigma;
                     // dw/dsigma = -(b' phi(b') - a' phi(a')) / sigma, with b' = sqrt(2) ub
-                    for (int e = lane; e < nr + 4 * nq; e += 32) {
+                    for (int e = gl; e < nr + 4 * nq; e += G) {
                         if (e < nr) {
                             float w = 1.0f, m = 0.0f, sg = 0.0f;
                             if (dd.sp > 0.0f) {
@@ -387,11 +394,11 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                             wts[e - nr] = sg * ist;
                         }
                     }
-                    __syncwarp();
+                    __syncwarp(gmask);
                     if (vec4) {
                         // (row, 4-tick group) items: one 16-byte load of dL/dS per item
                         const float inv_nq = 1.0f / (float)nq;
-                        for (int item = lane; item < nr * nq; item += 32) {
+                        for (int item = gl; item < nr * nq; item += G) {
                             const int ir = (int)(((float)item + 0.5f) * inv_nq);
                             const int iq = item - ir * nq;
                             const int kq = (q_lo + iq) * 4;
@@ -412,7 +419,7 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                         }
                     } else {
                         const float inv_nt = 1.0f / (float)nt;
-                        for (int b = lane; b < nr * nt; b += 32) {
+                        for (int b = gl; b < nr * nt; b += G) {
                             const int ir = (int)(((float)b + 0.5f) * inv_nt);
                             const int ik = b - ir * nt;
                             const float sv = __ldg(dgrid + (int64_t)(r0 + ir) * c.n_ticks + (k0 + ik));
@@ -424,16 +431,16 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                             a_ts += sv * pw * wts[ik + koff];
                         }
                     }
-                    __syncwarp();
+                    __syncwarp(gmask);
                 }
             }
-            a_q = warp_sum(a_q);
-            a_pm = warp_sum(a_pm);
-            a_ps = warp_sum(a_ps);
-            a_tm = warp_sum(a_tm);
-            a_ts = warp_sum(a_ts);
+            a_q = group_sum<G>(a_q, gmask);
+            a_pm = group_sum<G>(a_pm, gmask);
+            a_ps = group_sum<G>(a_ps, gmask);
+            a_tm = group_sum<G>(a_tm, gmask);
+            a_ts = group_sum<G>(a_ts, gmask);
         }
-        if (lane == 0) {
+        if (gl == 0) {
             const float qa = dd.ok ? dd.qatt : 0.0f;
             const float att = (dd.ok && qa > 0.0f) ? qa / d.q[gi] : 0.0f;
             const float dst = qa * a_ps, dsl = qa * a_ts * c.inv_v;
