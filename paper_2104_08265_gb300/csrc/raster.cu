@@ -5,11 +5,11 @@
 // Work split.  A block of 8 warps owns KD consecutive depos (32 by default; 64 or 128 when
 // the autotuner finds them faster; the adjoint uses 64).  Threads 0..KD-1 take the FP64 bin
 // decision of one depo each (one thread per depo: FP64 is scarce on this part, so it is
-// never evaluated redundantly by a whole warp) and park it in shared memory.  Each half warp
-// then walks KD / 16 of the block's depos (the two halves of a warp work on two depos side
-// by side): its lanes compute one erfc per bin edge of the patch (rows and ticks together),
-// difference them into the per-bin 1D weights in shared memory and stride over (row,
-// 4-tick group) items.
+// never evaluated redundantly by a whole warp) and park it in shared memory.  Each group of
+// 8 lanes then walks KD / 32 of the block's depos (the four groups of a warp work on four
+// depos side by side): its lanes compute one erfc per bin edge of the patch (rows and ticks
+// together), difference them into the per-bin 1D weights in shared memory and stride over
+// (row, 4-tick group) items.
 // An item draws one Philox block for its four ticks when fluctuating (four Box-Muller
 // normals), forms Q' w_p w_t per bin and adds the four values into the grid with one
 // vector reduction.
@@ -145,10 +145,10 @@ __device__ __forceinline__ float bin_mass(int64_t koff, float frac, float s, flo
     return 1.0f - 0.5f * (ea + eb);
 }
 
-// Lanes per depo group: a half warp takes one depo, so that the two halves of a warp work
-// on two depos side by side (a patch of ~17 rows x 3 four-tick groups fills three rounds
-// of 16 lanes better than two rounds of 32).
-constexpr int kGroup = 16;
+// Lanes per depo group: 8 lanes take one depo, so that the four groups of a warp work on
+// four depos side by side (a patch of ~17 rows x 3 four-tick groups, ~47 items, fills six
+// rounds of 8 lanes better than two rounds of 32).
+constexpr int kGroup = 8;
 
 // The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps.
 template <int KD>
@@ -290,16 +290,17 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask)
     return v;
 }
 
-// Per depo (a half warp each): recompute the patch weights and their mu / sigma derivatives,
-// gather dL/dS over the patch and apply the chain rule through Q' = Q exp(-t_d / tau),
-// t_a = t + t_d and sigma = sqrt(2 D t_d).  The global sums are reduced per block in FP64.
+// Per depo (a half warp each, so that the per-group tiles fit static shared memory):
+// recompute the patch weights and their mu / sigma derivatives, gather dL/dS over the patch
+// and apply the chain rule through Q' = Q exp(-t_d / tau), t_a = t + t_d and
+// sigma = sqrt(2 D t_d).  The global sums are reduced per block in FP64.
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, DepoGrads g,
                int* flags)
 {
     // a half warp per depo (as in the forward); patch tiles of at most kTile rows x kTile
     // ticks
-    constexpr int G = kGroup, NG = kWarps * 32 / G, kTile = 32;
+    constexpr int G = 16, NG = kWarps * 32 / G, kTile = 32;
     __shared__ Decision s_dec[kDepos];
     // wp, dwp/dmu, dwp/dsig per row; wt, dwt/dmu, dwt/dsig per tick laid out on 4-tick
     // groups (slot p is tick 4 q_lo + p, zero outside the window)
