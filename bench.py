@@ -171,6 +171,13 @@ def write_traffic(reps):
     rec = {"_about": "DRAM bytes (read + write) per launch, mean over the captured launches, "
                      "from ncu --set full captures of the 960-wire x 6000-tick plane with 100k "
                      "depos; valid only while the CUDA sources hash to source_sha256.",
+           "capture": ("CMD='python bench.py --steps 2 --warmup 1 --no-autotune --no-batch "
+                       "--no-cpu-baseline --no-cufft --no-e2e --soak-s 0'; ncu --set full "
+                       "--import-source no --clock-control none -k 'regex:k_rasterize|"
+                       "k_rows_r2c_direct|k_wire_warp|k_rows_c2r' -s 4 -c 4 -o fwd $CMD; ncu --set "
+                       "full --import-source no --clock-control none -k 'regex:k_wire_adjoint|"
+                       "k_rows_c2r_grid|k_depo_adjoint' -c 4 -o bwd $CMD; then "
+                       "python bench.py --write-traffic fwd.ncu-rep bwd.ncu-rep"),
            "reports": [os.path.basename(r) for r in reps],
            "source_sha256": source_hash(),
            "bytes_per_launch": {k: float(np.mean(v)) for k, v in sorted(acc.items())}}
