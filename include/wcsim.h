@@ -210,6 +210,15 @@ wcsim_status wcsim_plane_reserve_batch(wcsim_plane* plane, int32_t n_events);
  * WCSIM_OK. */
 wcsim_status wcsim_plane_check(wcsim_plane* plane, void* stream, int32_t* flags);
 
+/* Limit, in ns of the device's global timer, of each device-side wait of this plane's
+ * kernels for a bulk asynchronous copy (default 2e9: far above any legitimate wait).  A wait
+ * that runs out sets flag bit 1 (reported by wcsim_plane_check as WCSIM_ETIMEOUT), lets the
+ * copy it was waiting for land (bounded by the default limit) and ends its CTA, leaving that
+ * CTA's output incomplete; the context stays usable.  0 makes every wait that is not
+ * satisfied at once run out, which exercises that path (a diagnostic; no counterpart in the
+ * paper).  Applies to the calls issued after it. */
+wcsim_status wcsim_plane_set_wait_limit(wcsim_plane* plane, uint64_t ns);
+
 /* Per-stage device time of the last compute calls on this plane (CUDA events), when
  * enabled with wcsim_plane_set_timing(plane, 1).  ms[0..n) receives, in order, the forward
  * stages of the last wcsim_run / rasterize / convolve: zero grid, rasterize+scatter,

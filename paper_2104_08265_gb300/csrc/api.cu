@@ -750,6 +750,13 @@ wcsim_status wcsim_plane_check(wcsim_plane* pl, void* stream, int32_t* flags)
     return WCSIM_OK;
 }
 
+wcsim_status wcsim_plane_set_wait_limit(wcsim_plane* pl, uint64_t ns)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    pl->dims.wait_ns = ns;
+    return WCSIM_OK;
+}
+
 wcsim_status wcsim_plane_set_timing(wcsim_plane* pl, int32_t enable)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");

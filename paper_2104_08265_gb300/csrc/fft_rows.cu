@@ -167,7 +167,7 @@ k_rows_r2c_staged(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
         const int s = i & 1;
         const int64_t r0 = 2 * ((int64_t)blockIdx.x + (int64_t)i * gridDim.x);
         const bool has1 = r0 + 1 < n_rows;
-        const bool landed = mbar_wait(&bar[s], (i >> 1) & 1);
+        const bool landed = mbar_wait(&bar[s], (i >> 1) & 1, d.wait_ns);
         if (!__syncthreads_and(landed)) break;
         const float2* z = run_plan<false, 0>(p, StagedPairLd{st + s * 2 * d.n_t, d.n_t, has1}, X, Y);
         if (tid == 0 && i + 2 < n_items) {     // stage s was read by the first pass only

@@ -99,7 +99,7 @@ k_wire_pass(ConvDims d, FftPlan p, const float2* __restrict__ shat, const float2
     for (; i < n_items; ++i) {
         const int s = i & 1, j = i % d.n_imp;
         const int kb = blockIdx.x + (i / d.n_imp) * gridDim.x;
-        const bool landed = mbar_wait(&sm.bar[s], (i >> 1) & 1);
+        const bool landed = mbar_wait(&sm.bar[s], (i >> 1) & 1, d.wait_ns);
         if (!__syncthreads_and(landed)) break;
         const float2* z = run_plan<false, LOGB>(p, StagedTileLd{sm.st_s(s), d.n_w}, sm.X, sm.Y);
         const float2* h = sm.st_h(s, d.n_w);     // [4][N]

@@ -80,7 +80,7 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
         {
             float2 v[M];
             load_col<M>(shat + blk * d.n_w * kBlockCols, c, d.n_w, lane, v);
-            landed = mbar_wait(bar, j & 1);      // H_j's tile, copied while S_j loads
+            landed = mbar_wait(bar, j & 1, d.wait_ns);   // H_j's tile, copied while S_j loads
             warp_fft_fwd<M>(v, s_twf, tr, lane, u);
         }
         if (landed && lane < M) {

@@ -120,6 +120,9 @@ struct ConvDims {
     // Batched runs: event e's grid, time-axis spectra and wire-summed spectra start
     // e * ev_grid, e * ev_shat and e * ev_mt elements after the first event's.
     int64_t ev_grid, ev_shat, ev_mt;
+    // limit of each device-side wait for a bulk asynchronous copy (ns of %globaltimer);
+    // a wait that runs out raises the timeout flag and its CTA leaves
+    uint64_t wait_ns = 2000000000ull;
 };
 
 

@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_batch_run": [i32, P(vp), P(CDepos), P(vp), vp],
         "wcsim_plane_autotune": [vp, P(CDepos), vp, P(CTuneReport)],
         "wcsim_plane_reserve_batch": [vp, i32],
+        "wcsim_plane_set_wait_limit": [vp, ctypes.c_uint64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -315,6 +316,10 @@ class Plane:
         if st not in (OK, EDEVICE_CHECK):
             check(st)
         return int(f.value)
+
+    def set_wait_limit(self, ns: int):
+        """Limit (ns) of the device-side waits for bulk copies; see wcsim_plane_set_wait_limit."""
+        check(lib().wcsim_plane_set_wait_limit(self._h, ctypes.c_uint64(int(ns))))
 
     def set_timing(self, enable: bool = True):
         check(lib().wcsim_plane_set_timing(self._h, 1 if enable else 0))

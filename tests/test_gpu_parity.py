@@ -302,6 +302,30 @@ def test_repeated_runs_leave_a_clean_grid(W):
         assert_close(o, ref, what="repeat")
 
 
+def test_copy_wait_timeout_is_reported_and_the_plane_recovers(W, monkeypatch):
+    """Failure detection without a fault: with a wait limit of 0 the wire pass's waits for
+    its bulk-copied response tiles run out (a copy issued just before is not complete yet),
+    wcsim_plane_check reports WCSIM_ETIMEOUT, and with the normal limit restored the same
+    plane gives the oracle's frame again (the context stays usable)."""
+    monkeypatch.delenv("WCSIM_WIRE_KERNEL", raising=False)
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    dd = to_dev(W, d)
+    ref = O.run(g, prm, R, d)
+    assert pl.check_flags() == 0
+    pl.set_wait_limit(0)
+    pl.run(dd)
+    with pytest.raises(W.WcsimError) as e:
+        pl.check_flags()
+    assert e.value.status == W.ETIMEOUT
+    pl.set_wait_limit(2_000_000_000)
+    got = pl.run(dd).cpu().numpy()
+    assert pl.check_flags() == 0
+    assert_close(got, ref, what="after a timed-out run")
+
+
 def test_autotune_picks_variants_without_changing_results(W):
     wl = S.make_workload("plane960-100k", n_depos=20000)
     g, prm, kind, d = wl.planes[0]
