@@ -60,6 +60,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_params(prm, rank):
+    """Ranks are replicas: each simulates its own event of the same shape, its fluctuation
+    seed offset by the rank."""
+    return synth.DriftParams(**{**prm.__dict__, "seed": prm.seed + rank})
+
+
+def max_over_ranks(x, ws, device):
+    """The largest x over the ranks of the default process group (x itself when alone)."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ws, steps, units_per_rank_step, max_total_ms):
+    """Whole-job units per second: the units every rank processed over the slowest rank's
+    time (weak scaling: fixed work per rank)."""
+    return ws * steps * units_per_rank_step / (max_total_ms / 1e3)
+
+
 def workload(name):
     wl = synth.make_workload(name)
     g, prm, kind, d = wl.planes[0]
@@ -271,23 +294,45 @@ def cpu_baseline(g, prm, R, d):
                       "%.1f s wall" % (len(d), g.n_wires, g.n_ticks, dt)}
 
 
+REFERENCE_BUDGET_STEPS = 60     # full-workload oracle steps (about 2 s each) per run, at most
+
+
+def reference_sample(d, steps, warmup):
+    """The depos of one reference step: the whole workload while the W + K steps stay within
+    REFERENCE_BUDGET_STEPS full steps, else the first depos (whole tracks first) of a
+    proportionally smaller sample (the frame and its convolution stay full size)."""
+    n = len(d)
+    total = max(1, steps + warmup)
+    if total <= REFERENCE_BUDGET_STEPS:
+        return d
+    k = max(1000, n * REFERENCE_BUDGET_STEPS // total)
+    return synth.Depos(p=d.p[:k], t=d.t[:k], td=d.td[:k], q=d.q[:k], id=d.id[:k])
+
+
 def run_reference(args):
+    """The oracle on the host cores (rank 0 only; the other ranks exit without work): W
+    untimed and exactly K timed steps, each one forward of a bounded sample of the workload."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     wl, g, prm, kind, d = workload(args.workload)
     R = synth.make_response(g, kind)
-    steps = max(1, min(args.steps, 3))
-    warm = min(args.warmup, 0)
-    times = [oracle_step(g, prm, R, d) for _ in range(steps)]
+    ds = reference_sample(d, args.steps, args.warmup)
+    for _ in range(args.warmup):
+        oracle_step(g, prm, R, ds)
+    times = [oracle_step(g, prm, R, ds) for _ in range(args.steps)]
     tot = sum(times)
-    v = steps * len(d) / tot
+    v = args.steps * len(ds) / tot
+    sample = ("%d of the workload's %d depos per step (full %dx%d frame and convolution), "
+              "single thread" % (len(ds), len(d), g.n_wires, g.n_ticks))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "depos/s",
-            "n_gpus": args.gpus, "steps": steps, "warmup": warm, "ms_per_step": 1e3 * tot / steps,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args.workload, g, d, prm),
             "cpu_baseline": {"value": v, "unit": "depos/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d full forward(s) of the workload" % steps},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "depos/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -387,7 +432,7 @@ def run_gpu(args):
 
     wl, g, prm, kind, d = workload(args.workload)
     # every rank simulates its own event: per-rank seed offset, same shapes
-    prm = synth.DriftParams(**{**prm.__dict__, "seed": prm.seed + rank})
+    prm = rank_params(prm, rank)
     R = synth.make_response(g, kind)
 
     cpu = None
@@ -443,11 +488,7 @@ def run_gpu(args):
         for k, v in plane.stage_times().items():
             stage_ms[k].append(v)
     plane.set_timing(False)
-    tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), ws, "cuda")
     assert plane.check_flags() == 0
 
     # ---- forward + backward (loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10,
@@ -516,12 +557,8 @@ def run_gpu(args):
             e2e_step()
             ee[i].record(stream)
         torch.cuda.synchronize()
-        e2e_ms = sum(s.elapsed_time(e) for s, e in zip(es, ee))
-        if ws > 1:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": ws * args.steps * len(d) / (e2e_ms / 1e3), "unit": "depos/s",
+        e2e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(es, ee)), ws, "cuda")
+        e2e = {"value": job_throughput(ws, args.steps, len(d), e2e_ms), "unit": "depos/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_ms / args.steps}
 
@@ -545,7 +582,7 @@ def run_gpu(args):
     ach = sb[dom] / (avg[dom] * 1e-3) / 1e9
     per_step = tot_ms / args.steps
     line = {
-        "metric": METRIC, "value": ws * args.steps * len(d) / (tot_ms / 1e3), "unit": "depos/s",
+        "metric": METRIC, "value": job_throughput(ws, args.steps, len(d), tot_ms), "unit": "depos/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config(args.workload, g, d, prm,
