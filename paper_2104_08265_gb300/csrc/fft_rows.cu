@@ -42,10 +42,12 @@ struct StagedPairLd {
 // 16-byte aligned, n_t a multiple of 4) each thread issues its 16-byte loads in batches of
 // kU per row before storing them.  With clear the
 // rows are left zero (consume and clear): only the groups that hold a nonzero value are
-// written, so the untouched part of a sparse grid costs no writes.  Ends without a barrier.
-__device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, int n, bool vec,
+// written, so the untouched part of a sparse grid costs no writes.  Returns whether this
+// thread saw a nonzero value.  Ends without a barrier.
+__device__ __forceinline__ bool stage_real_pair(float* g0, float* g1, int n_t, int n, bool vec,
                                                 bool clear, float2* z)
 {
+    bool any = false;
     for (int i = n_t + threadIdx.x; i < n; i += blockDim.x) z[i] = make_float2(0.f, 0.f);
     float4* z4 = reinterpret_cast<float4*>(z);
     if (vec) {
@@ -72,9 +74,11 @@ __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, i
                 if (q < nq) {
                     z4[2 * q] = make_float4(a[u].x, b[u].x, a[u].y, b[u].y);
                     z4[2 * q + 1] = make_float4(a[u].z, b[u].z, a[u].w, b[u].w);
+                    const bool na = nz(a[u]), nb = nz(b[u]);
+                    any |= na | nb;
                     if (clear) {
-                        if (nz(a[u])) q0[q] = zero;
-                        if (g1 && nz(b[u])) q1[q] = zero;
+                        if (na) q0[q] = zero;
+                        if (g1 && nb) q1[q] = zero;
                     }
                 }
             }
@@ -83,12 +87,14 @@ __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, i
         for (int i = threadIdx.x; i < n_t; i += blockDim.x) {
             const float x0 = g0[i], x1 = g1 ? g1[i] : 0.f;
             z[i] = make_float2(x0, x1);
+            any |= (x0 != 0.f) | (x1 != 0.f);
             if (clear) {
                 if (x0 != 0.f) g0[i] = 0.f;
                 if (x1 != 0.f) g1[i] = 0.f;
             }
         }
     }
+    return any;
 }
 
 // Separate the two real rows' half spectra and store them in the blocked layout (zeros in
@@ -97,7 +103,8 @@ __device__ __forceinline__ void stage_real_pair(float* g0, float* g1, int n_t, i
 // The block size is a multiple of 16, so the output addresses and the padded shared indices
 // of k and N - k advance by constants from one iteration to the next.
 __device__ __forceinline__ void store_pair_spectra(const ConvDims& d, const float2* z, int N,
-                                                   int64_t r0, bool has1, float2* shat)
+                                                   int64_t r0, bool has1, float2* shat,
+                                                   bool zero = false)
 {
     const int w0 = (int)(r0 / d.n_imp), j0 = (int)(r0 % d.n_imp);
     const int64_t r1 = r0 + 1;
@@ -112,7 +119,7 @@ __device__ __forceinline__ void store_pair_spectra(const ConvDims& d, const floa
     int pa = pad16(k0), pb = pad16(N - k0);
     for (int k = k0; k < nk; k += blockDim.x, q0 += step, q1 += step, pa += dp, pb -= dp) {
         float2 x0 = make_float2(0.f, 0.f), x1 = x0;
-        if (k < nh) {
+        if (k < nh && !zero) {
             const float2 a = z[pa];
             const float2 b = z[k == 0 ? 0 : pb];
             x0 = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
@@ -209,8 +216,13 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __res
     }
     const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
     float* g0 = grid + r0 * d.n_t;
-    stage_real_pair(g0, has1 ? g0 + d.n_t : nullptr, d.n_t, N, vec, d.clear_input != 0, X);
-    __syncthreads();
+    const bool any = stage_real_pair(g0, has1 ? g0 + d.n_t : nullptr, d.n_t, N, vec,
+                                     d.clear_input != 0, X);
+    // the transform of two all-zero rows is zero: store zero spectra and skip the passes
+    if (!__syncthreads_or(any)) {
+        store_pair_spectra(d, X, N, r0, has1, shat, true);
+        return;
+    }
     const float2* z = run_row_plan<false, FIX, kDirectThreads>(p, X, Y);
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
