@@ -175,16 +175,13 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
     const float2* z = run_row_plan<true, FIX, 256>(p, X, Y);
     float* o0 = grid + ((int64_t)w0 * d.n_imp + j) * d.n_t;
     float* o1 = grid + ((int64_t)w1 * d.n_imp + j) * d.n_t;
-    for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
-        const float2 v = z[pad16(t)];
-        o0[t] = v.x;
-        if (has1) o1[t] = v.y;
-    }
+    const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
+    store_real_pair(z, o0, o1, d.n_t, has1, vec);
 }
 
 #define WCSIM_ADJ_M(X) X(4) X(8) X(15) X(16) X(20) X(24) X(25) X(30)
 
-bool g_attr = false;
+DeviceOnce g_attr;
 
 }  // namespace
 
@@ -196,13 +193,13 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
 #define WCSIM_CASE(MM)                                                                           \
     case MM: {                                                                                   \
         const size_t smem_a = (size_t)kBlockCols * tile_ld(32 * MM) * sizeof(float2);         \
-        static bool attr_set = false;                                                           \
-        if (!attr_set) {                                                                        \
+        static DeviceOnce attr_set;                                                             \
+        if (attr_set.pending()) {                                                               \
             cudaError_t e = cudaFuncSetAttribute(k_wire_adjoint_a<MM>,                          \
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                                  (int)smem_a);                                  \
             if (e) return e;                                                                    \
-            attr_set = true;                                                                    \
+            attr_set.mark();                                                                    \
         }                                                                                       \
         k_wire_adjoint_a<MM><<<d.nkb, kWarps * 32, smem_a, s>>>(d, tw2, gt, shat, g2d, dR, inv_n); \
         k_wire_adjoint_b<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, g2d, shat, H);               \
@@ -218,13 +215,13 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
 cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const float2* shat,
                                  float* grid, cudaStream_t s)
 {
-    if (!g_attr) {
+    if (g_attr.pending()) {
         cudaError_t e = cudaFuncSetAttribute(k_rows_c2r_grid<kPlanRuntime>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (!e) e = cudaFuncSetAttribute(k_rows_c2r_grid<kPlan6000>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e) return e;
-        g_attr = true;
+        g_attr.mark();
     }
     const int64_t n_ctas = (int64_t)d.n_imp * ((d.n_w + 1) / 2);
     const int fix = fixed_plan_of(pt);

@@ -371,6 +371,31 @@ __device__ __forceinline__ void stage_herm_pair(const float2* __restrict__ s0,
     }
 }
 
+// Write the two real rows of an inverse real-pair transform held in the padded buffer z
+// (row 0 in .x, row 1 in .y; o1 ignored when !has1), ticks t < n_t.  With vec (rows 16-byte
+// aligned, n_t a multiple of 4) a thread writes 4 ticks of each row with one 16-byte store.
+__device__ __forceinline__ void store_real_pair(const float2* z, float* __restrict__ o0,
+                                                float* __restrict__ o1, int n_t, bool has1,
+                                                bool vec)
+{
+    if (vec) {
+        float4* p0 = reinterpret_cast<float4*>(o0);
+        float4* p1 = reinterpret_cast<float4*>(o1);
+        for (int q = threadIdx.x; q < (n_t >> 2); q += blockDim.x) {
+            const int i = pad16(4 * q);            // 4q .. 4q + 3 share one 16-slot group
+            const float2 a = z[i], b = z[i + 1], c = z[i + 2], e = z[i + 3];
+            p0[q] = make_float4(a.x, b.x, c.x, e.x);
+            if (has1) p1[q] = make_float4(a.y, b.y, c.y, e.y);
+        }
+    } else {
+        for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
+            const float2 v = z[pad16(t)];
+            o0[t] = v.x;
+            if (has1) o1[t] = v.y;
+        }
+    }
+}
+
 // All passes of plan p.  The first pass reads through `first` (global memory or a shared
 // buffer outside X/Y), later passes ping-pong between X and Y.  Returns the buffer holding
 // the transform; ends with a block barrier.

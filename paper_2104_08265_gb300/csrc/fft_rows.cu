@@ -243,12 +243,8 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     __syncthreads();
     const float2* z = run_row_plan<true, FIX, kDirectThreads>(p, X, Y);
     float* o0 = wave + (int64_t)w0 * d.n_t;
-    float* o1 = wave + (int64_t)w1 * d.n_t;
-    for (int t = threadIdx.x; t < d.n_t; t += blockDim.x) {
-        const float2 v = z[pad16(t)];
-        o0[t] = v.x;
-        if (has1) o1[t] = v.y;
-    }
+    const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(wave) & 15) == 0);
+    store_real_pair(z, o0, o0 + d.n_t, d.n_t, has1, vec);
 }
 
 // CTAs of the direct R2C kernel k resident on the whole GPU with smem bytes each, when its
@@ -266,17 +262,17 @@ int r2c_prefetch_ahead(const ConvDims& d, const float* grid, K k, size_t smem)
     return per_sm * sm_count();
 }
 
-bool g_attr = false;
+DeviceOnce g_attr;
 cudaError_t attrs()
 {
-    if (g_attr) return cudaSuccess;
+    if (!g_attr.pending()) return cudaSuccess;
     const int mx = (int)kMaxSmem;
     cudaError_t e = cudaFuncSetAttribute(k_rows_r2c_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (!e) e = cudaFuncSetAttribute(k_rows_r2c_direct<kPlanRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (!e) e = cudaFuncSetAttribute(k_rows_r2c_direct<kPlan6000>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (!e) e = cudaFuncSetAttribute(k_rows_c2r<kPlanRuntime>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (!e) e = cudaFuncSetAttribute(k_rows_c2r<kPlan6000>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) g_attr = true;
+    if (!e) g_attr.mark();
     return e;
 }
 

@@ -213,20 +213,22 @@ __global__ void k_make_hermitian(ConvDims d, const float2* __restrict__ R, float
     }
 }
 
-bool g_attr = false;
+DeviceOnce g_attr;
 
 }  // namespace
 
 int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-            n = 1;
+    static int n[64] = {};                 // per device ordinal
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (n[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 1;
+        n[dev] = v;
     }
-    return n;
+    return n[dev];
 }
 
 cudaError_t launch_make_hermitian(const ConvDims& d, const float2* resp, float2* H, float scale,
@@ -243,12 +245,12 @@ constexpr size_t kMaxSmem = 227 * 1024;
 cudaError_t launch_wire_pass(const ConvDims& d, const FftPlan& pw, const float2* shat,
                              const float2* H, float2* mt, int* flags, cudaStream_t s)
 {
-    if (!g_attr) {
+    if (g_attr.pending()) {
         cudaError_t e = cudaFuncSetAttribute(k_wire_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         if (!e) e = cudaFuncSetAttribute(k_wire_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         if (!e) e = cudaFuncSetAttribute(k_wire_direct<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         if (e) return e;
-        g_attr = true;
+        g_attr.mark();
     }
     const size_t staged = wire_smem_bytes(d.n_w, pw.n);
     if (staged <= kMaxSmem) {

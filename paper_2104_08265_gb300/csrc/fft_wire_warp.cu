@@ -171,13 +171,13 @@ cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2*
     switch (d.n_fw / 32) {
 #define WCSIM_CASE(MM)                                                                         \
     case MM: {                                                                                 \
-        static bool attr_set = false;                                                          \
-        if (!attr_set) {                                                                       \
+        static DeviceOnce attr_set;                                                            \
+        if (attr_set.pending()) {                                                              \
             cudaError_t e = cudaFuncSetAttribute(k_wire_warp<MM, kCols>,                       \
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                                  (int)warp_smem<MM, kCols>());                 \
             if (e) return e;                                                                   \
-            attr_set = true;                                                                   \
+            attr_set.mark();                                                                   \
         }                                                                                      \
         k_wire_warp<MM, kCols><<<grid, kCols * 32, warp_smem<MM, kCols>(), s>>>(d, tw2, shat, H, \
                                                                                 mt, flags);    \

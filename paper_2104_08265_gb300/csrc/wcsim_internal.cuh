@@ -176,4 +176,18 @@ cudaError_t launch_rows_c2r_batch(const ConvDims& d, const FftPlan& pt, const fl
 // Streaming multiprocessors of the current device (cached).
 int sm_count();
 
+// A once-per-device flag: kernel attributes (cudaFuncSetAttribute) are set per device, so a
+// process that drives several GPUs sets them once on each.
+class DeviceOnce {
+public:
+    // true if the current device has not been marked yet
+    bool pending() const { const int d = dev(); return d < 0 || d >= kMax || !done_[d]; }
+    void mark() { const int d = dev(); if (d >= 0 && d < kMax) done_[d] = true; }
+
+private:
+    static constexpr int kMax = 64;
+    static int dev() { int d = -1; return cudaGetDevice(&d) == cudaSuccess ? d : -1; }
+    bool done_[kMax] = {};
+};
+
 }  // namespace wcsim
