@@ -8,6 +8,11 @@
 // order.  B = 2^LOGB independent sequences are transformed together; element (c, i) of the
 // batch lives at buf[pad(i) * B + c], where pad() inserts one slot every 16 elements so
 // that the stride-R writes of early passes do not pile onto one shared-memory bank.
+//
+// Plans come in two forms: a runtime plan (FftPlan: any length that factors into radices
+// <= 25, passes ping-ponging between two buffers) and compile-time plans (pass_fixed /
+// pass_fixed_inplace, all strides and divisors constants; the in-place form holds each
+// thread's butterfly inputs in registers across a barrier and needs one buffer).
 #pragma once
 
 #include <cuda_runtime.h>

@@ -4,12 +4,15 @@
 // X1 = (Z[k] - conj Z[-k]) / 2i.
 //
 // rows_r2c (direct, the default) takes one pair of rows per CTA: both rows are loaded into
-// shared memory with batched 16-byte loads (scalar loads when rows are not 16-byte aligned)
-// and every pass of the plan runs in shared memory; the CTA also asks L2 for the rows of the
-// CTA expected to follow it on the SM.  rows_r2c (staged, chosen by the autotuner or
+// shared memory with batched 16-byte loads (scalar loads when rows are not 16-byte aligned),
+// a pair with no nonzero value stores zero spectra at once, and otherwise every pass of the
+// plan runs in shared memory (in place, in one buffer, for the compile-time 6000-point plan;
+// between two buffers for runtime plans); the CTA also asks L2 for the rows of the CTA
+// expected to follow it on the SM.  rows_r2c (staged, chosen by the autotuner or
 // WCSIM_ROWS_KERNEL) is persistent: one CTA per SM walks pairs of rows, and one bulk copy
 // brings both rows of the next pair into a two-stage shared buffer while the previous pair
-// is transformed.  The inverse kernels stage their Hermitian inputs the same way.
+// is transformed.  The inverse kernel stages its Hermitian input (each element read once,
+// its mirror written from the same load) and writes 4 ticks per 16-byte store.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
