@@ -1,4 +1,6 @@
-// Wire-axis part of Eq. 2 and the response preparation.
+// Wire-axis part of Eq. 2 for wire FFT sizes that are not 32 M (the one-warp-per-column
+// kernel of fft_wire_warp.cu covers those), and the response preparation (make_hermitian:
+// the Hermitian half of R, scaled, transposed into the time-frequency-major H).
 //
 // wire_pass is persistent: one CTA per SM walks work items (block kb of 4 time
 // frequencies, impact position j).  For each item it bulk-copies the contiguous tiles
