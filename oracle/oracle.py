@@ -17,6 +17,9 @@ Stages (paper Sec. 2.1.1, Eq. 1 and Eq. 2):
   dS_j = Re IFFT2(conj(R_j) . FFT2(G)) and dR_j = conj(FFT2(S_j)) . FFT2(G) / (n_fw n_ft)
   (the gradient convention of complex tensors in PyTorch: dL/dRe + i dL/dIm).
 * ``depo_grads`` -- per-depo chain rule through rasterization and drift (C code).
+* ``noise``      -- Eq. 1's additive term N(t, x): per wire, the normalised inverse DFT of an
+  amplitude spectrum times unit complex Gaussians drawn from Philox4x32-10 (C code for the
+  draws, numpy's irfft for the transform).
 
 Pins (tests, not this file): erf telescoping and quadrature for the weights, brute-force
 bin enumeration for the windows, direct circular-sum convolution on tiny grids, a point
@@ -78,6 +81,9 @@ def _load():
             lib.og_normal.restype = d
             lib.og_bin_normal.argtypes = [i64, i64, u32, u32, P(u32)]
             lib.og_bin_normal.restype = d
+            lib.og_noise_spectrum.argtypes = [ctypes.c_int32, ctypes.c_int32, u32, P(u32),
+                                              P(d), P(d)]
+            lib.og_noise_spectrum.restype = None
             lib.og_windows.argtypes = [P(_Geom), P(_Params), i64, P(d), P(d), P(d), P(f),
                                        P(i64)]
             lib.og_depo_weights.argtypes = [P(_Geom), P(_Params), d, d, d, f, P(d), P(d),
@@ -217,6 +223,29 @@ def convolve(geom, response, grid) -> np.ndarray:
 def run(geom, params, response, depos) -> np.ndarray:
     """Depos to per-wire waveforms: rasterize, then convolve."""
     return convolve(geom, response, rasterize(geom, params, depos))
+
+
+# --------------------------------------------------------------------------- noise
+def noise_spectrum(n_w: int, n_ft: int, plane_id: int, seed: int) -> np.ndarray:
+    """xi [n_w][n_ft/2 + 1] complex128: the unit-mean-square complex Gaussians of the noise
+    (Philox4x32-10 + Box-Muller; real at k = 0 and at the Nyquist frequency)."""
+    nh = n_ft // 2 + 1
+    re = np.zeros((n_w, nh), np.float64)
+    im = np.zeros((n_w, nh), np.float64)
+    key = (ctypes.c_uint32 * 2)(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    _load().og_noise_spectrum(int(n_w), int(n_ft), int(plane_id) & 0xFFFFFFFF, key,
+                              _ptr(re, ctypes.c_double), _ptr(im, ctypes.c_double))
+    return re + 1j * im
+
+
+def noise(geom, amp, n_ft: int, plane_id: int, seed: int) -> np.ndarray:
+    """Eq. 1's N(t, x), [n_wires][n_ticks] float64: per wire the normalised inverse DFT over
+    n_ft points of A(k) xi(k) (A: n_ft/2 + 1 amplitudes, Hermitian extension), cropped to the
+    frame."""
+    amp = np.asarray(amp, np.float64)
+    assert amp.shape == (n_ft // 2 + 1,)
+    xi = noise_spectrum(geom.n_wires, n_ft, plane_id, seed)
+    return np.fft.irfft(amp[None, :] * xi, n=n_ft, axis=1)[:, : geom.n_ticks].copy()
 
 
 def convolve_adjoint(geom, response, grid, G):

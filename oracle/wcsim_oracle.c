@@ -98,6 +98,37 @@ double og_bin_normal(int64_t r, int64_t k, uint32_t id, uint32_t plane_id, const
     return (m < 2) ? og_normal(x[0], x[1], m) : og_normal(x[2], x[3], m - 2);
 }
 
+/* ---- noise (Eq. 1's additive term N(t, x); the paper gives no model, the readings are):
+ *   per wire w, the noise is the normalised inverse DFT over n_ft points of A(k) xi_w(k),
+ *   with A the plane's amplitude spectrum (k < n_ft/2 + 1, extended as A(n_ft - k) = A(k))
+ *   and xi_w(n_ft - k) = conj(xi_w(k)) complex Gaussians of unit mean square:
+ *     xi = (z_re + i z_im) / sqrt 2 for 0 < k < n_ft / 2,  xi = z_re at k = 0 and, for even
+ *     n_ft, at k = n_ft / 2;
+ *   z from Philox4x32-10 with counter (k div 2, w, OG_NOISE_TAG, plane id) and key = the
+ *   noise seed: the block's first Box-Muller pair gives (z_re, z_im) of k = 2 (k div 2), the
+ *   second those of k + 1. */
+#define OG_NOISE_TAG 0x4E4F4953u
+
+/* xi_w(k) for w < n_w, k < nh (nh = n_ft / 2 + 1), row-major [n_w][nh]. */
+void og_noise_spectrum(int32_t n_w, int32_t n_ft, uint32_t plane_id, const uint32_t key[2],
+                       double* re, double* im)
+{
+    const int32_t nh = n_ft / 2 + 1;
+    for (int32_t w = 0; w < n_w; ++w) {
+        for (int32_t k = 0; k < nh; ++k) {
+            uint32_t ctr[4] = {(uint32_t)(k >> 1), (uint32_t)w, OG_NOISE_TAG, plane_id};
+            uint32_t x[4];
+            og_philox4x32_10(ctr, key, x);
+            const int m = k & 1;
+            const double zr = og_normal(x[2 * m], x[2 * m + 1], 0);
+            const double zi = og_normal(x[2 * m], x[2 * m + 1], 1);
+            const int real_only = (k == 0) || (2 * k == n_ft);
+            re[(size_t)w * nh + k] = real_only ? zr : zr / OG_SQRT2;
+            im[(size_t)w * nh + k] = real_only ? 0.0 : zi / OG_SQRT2;
+        }
+    }
+}
+
 /* Per-call constants of the bin decision, formed the same way for every depo. */
 typedef struct {
     double inv_dp, inv_dt;          /* 1/(pitch/n_imp), 1/tick, FP64 */
