@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-noise", action="store_true",
+                    help="skip the forward timed with Eq. 1's noise on")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-event batched run (wcsim_batch_run vs 64 wcsim_run calls)")
     ap.add_argument("--soak-s", type=float, default=0.5,
@@ -491,6 +493,28 @@ def run_gpu(args):
     tot_ms = max_over_ranks(sum(step_ms), ws, "cuda")
     assert plane.check_flags() == 0
 
+    # ---- the same forward with Eq. 1's noise on (a low-pass amplitude spectrum): the noise
+    # is added while the inverse time FFT stages its input
+    noise = None
+    if not args.no_noise:
+        k = np.arange(g.n_ticks // 2 + 1)
+        amp = (np.sqrt(g.n_ticks) / (1.0 + (k / (0.1 * g.n_ticks)) ** 2)).astype(np.float32)
+        plane.set_noise(amp, seed=0x0015E)
+        for _ in range(args.warmup):
+            plane.run(dd, out=wave)
+        ns_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ne_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ns_[i].record(stream)
+            plane.run(dd, out=wave)
+            ne_[i].record(stream)
+        torch.cuda.synchronize()
+        nms = sum(a.elapsed_time(b) for a, b in zip(ns_, ne_)) / args.steps
+        plane.set_noise(None)
+        noise = {"ms_per_step": nms, "depos_per_s": len(d) / (nms * 1e-3),
+                 "model": "spectral noise per wire, A(k) = sqrt(n_t) / (1 + (k / 0.1 n_t)^2)"}
+
     # ---- forward + backward (loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10,
     # lifetime 8 ms; the backward runs on the mean path and includes dL/dR)
     fb_ms = None
@@ -642,6 +666,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "cufft_comparison": cufft,
         "batch64": batch,
+        "with_noise": noise,
         "autotune": tune,
         "clocks": clk,
     }

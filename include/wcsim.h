@@ -210,6 +210,22 @@ wcsim_status wcsim_plane_reserve_batch(wcsim_plane* plane, int32_t n_events);
  * WCSIM_OK. */
 wcsim_status wcsim_plane_check(wcsim_plane* plane, void* stream, int32_t* flags);
 
+/* Electronics noise N(t, x), the additive term of Eq. 1, for the waveforms of wcsim_run and
+ * wcsim_batch_run (wcsim_convolve stays Eq. 2 alone).  The paper gives no noise model; this
+ * is spectral noise per wire: the normalised inverse DFT over n_ft points of A(k) xi_w(k),
+ * cropped to the frame, where amp (HOST, n_amp = n_ft / 2 + 1 values >= 0, extended as
+ * A(n_ft - k) = A(k)) is the amplitude spectrum and xi_w(k) = (z_re + i z_im) / sqrt 2 are
+ * complex Gaussians of unit mean square (z_re alone at k = 0 and, for even n_ft, at
+ * n_ft / 2), z from Philox4x32-10 (counter = (k / 2, wire, 0x4E4F4953, plane id), key =
+ * seed, plus the event index in a batch) and Box-Muller.  The noise is added to the wire
+ * spectra as the inverse time FFT reads them (no extra memory pass).  amp == NULL or
+ * n_amp == 0 turns it off.  Copies the spectrum once on `stream` and waits for the copy;
+ * WCSIM_ESHAPE if n_amp is not n_ft / 2 + 1, WCSIM_EINVAL for a negative or non-finite
+ * amplitude (the previous setting is kept).  No counterpart in the paper beyond Eq. 1's
+ * term. */
+wcsim_status wcsim_plane_set_noise(wcsim_plane* plane, const float* amp, int32_t n_amp,
+                                   uint64_t seed, void* stream);
+
 /* Limit, in ns of the device's global timer, of each device-side wait of this plane's
  * kernels for a bulk asynchronous copy (default 2e9: far above any legitimate wait).  A wait
  * that runs out sets flag bit 1 (reported by wcsim_plane_check as WCSIM_ETIMEOUT), lets the

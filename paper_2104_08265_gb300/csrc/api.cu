@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "async_copy.cuh"
 #include "wcsim_internal.cuh"
@@ -72,6 +73,8 @@ struct wcsim_plane {
     float2* shat = nullptr;     // time-axis spectra, blocked [n_imp][nkb][n_wires][4]
     float2* mt = nullptr;       // wire-summed spectra, blocked [nkb][n_wires][4]
     float2* g2d = nullptr;      // adjoint: 2D spectrum of G, blocked [nkb][n_fw][4]
+    float* noise_amp = nullptr; // Eq. 1's noise: A(k) / n_ft, k < nh (null: no noise)
+    uint64_t noise_seed = 0;
     int* flags = nullptr;       // device flag word
     // scratch of batched runs: bcap events' grids, time-axis and wire-summed spectra
     float* bgrid = nullptr;
@@ -189,6 +192,7 @@ void plane_free(wcsim_plane* pl)
     cudaFree(pl->shat);
     cudaFree(pl->mt);
     cudaFree(pl->g2d);
+    cudaFree(pl->noise_amp);
     cudaFree(pl->flags);
     cudaFree(pl->bgrid);
     cudaFree(pl->bshat);
@@ -259,6 +263,14 @@ wcsim_status reserve_batch(wcsim_plane* pl, int32_t n)
 }
 
 // Events ev[0..k) of one plane (global batch indices idx[] for the seeds), k <= kMaxBatch.
+// The inverse time FFT of a run adds the plane's noise, when it has one (Eq. 1).
+void with_noise(const wcsim_plane* pl, ConvDims& d)
+{
+    d.noise_amp = pl->noise_amp;
+    d.noise_seed = pl->noise_seed;
+    d.plane_id = pl->prm.plane_id;
+}
+
 wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_depos* depos,
                        float* const* waves, cudaStream_t s)
 {
@@ -297,7 +309,11 @@ wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_d
                 return cuda_fail(e, "batch wire launch");
     }
     WavePtrs w;
-    for (int i = 0; i < k; ++i) w.p[i] = waves[idx[i]];
+    for (int i = 0; i < k; ++i) {
+        w.p[i] = waves[idx[i]];
+        w.ev[i] = idx[i];
+    }
+    with_noise(pl, d);
     if ((e = launch_rows_c2r_batch(d, pl->pt, pl->bmt, w, k, s))) return cuda_fail(e, "batch rows_c2r launch");
     return WCSIM_OK;
 }
@@ -468,8 +484,10 @@ wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, v
     // the time-axis transform reads the plane's own grid once: it clears it as it goes
     // (the direct kernel; the staged one reads through bulk copies and leaves it as is)
     pl->dims.clear_input = (pl->dims.rows_variant == 0);
+    with_noise(pl, pl->dims);
     st = do_convolve(pl, pl->grid, wave, s, 3);
     pl->dims.clear_input = 0;
+    pl->dims.noise_amp = nullptr;
     if (st == WCSIM_OK && pl->dims.rows_variant == 0) pl->grid_clean = true;
     return st;
 }
@@ -747,6 +765,37 @@ wcsim_status wcsim_plane_check(wcsim_plane* pl, void* stream, int32_t* flags)
     if (h & kErrTimeout)
         return fail(WCSIM_ETIMEOUT, "a device-side wait for an asynchronous copy gave up (flags 0x%x)", h);
     if (h) return fail(WCSIM_EDEVICE_CHECK, "device flagged invalid depo values (flags 0x%x)", h);
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_set_noise(wcsim_plane* pl, const float* amp, int32_t n_amp,
+                                   uint64_t seed, void* stream)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (!amp || n_amp == 0) {
+        cudaFree(pl->noise_amp);
+        pl->noise_amp = nullptr;
+        return WCSIM_OK;
+    }
+    if (n_amp != pl->dims.nh)
+        return fail(WCSIM_ESHAPE, "the noise amplitude spectrum needs n_ft / 2 + 1 = %d values (got %d)",
+                    pl->dims.nh, n_amp);
+    DeviceGuard dg(pl->device);
+    if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+    std::vector<float> a((size_t)n_amp);
+    for (int k = 0; k < n_amp; ++k) {
+        if (!(amp[k] >= 0.0f) || !isfinite(amp[k]))
+            return fail(WCSIM_EINVAL, "noise amplitude %d is negative or not finite", k);
+        a[(size_t)k] = (float)((double)amp[k] / (double)pl->dims.n_ft);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!pl->noise_amp) e = cudaMalloc(&pl->noise_amp, (size_t)n_amp * sizeof(float));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!e) e = cudaMemcpyAsync(pl->noise_amp, a.data(), (size_t)n_amp * sizeof(float),
+                                cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(e, "noise spectrum upload");
+    pl->noise_seed = seed;
     return WCSIM_OK;
 }
 

@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include "dft_roots.cuh"
+#include "rng.cuh"
 #include "wcsim_internal.cuh"
 
 namespace wcsim {
@@ -346,12 +347,16 @@ __device__ __forceinline__ void pass_any(int R, const Ld& ld, const St& st, cons
 
 // Stage the input of an inverse real-pair transform: z[k] = X0[k] + i X1[k], k < n, for two
 // Hermitian spectra given by their halves k < nh at columns w0, w1 of blocked slabs s0, s1
-// (X1 = 0 when !has1), into the unpadded shared buffer z (read back through FlatLd).  Each stored element is read once
-// and also gives the mirror z[n - k] (conj X0 + i conj X1); loads are issued in batches of
-// kU per thread before their stores.  Ends without a barrier.
+// (X1 = 0 when !has1), into the unpadded shared buffer z (read back through FlatLd).  Each
+// stored element is read once and also gives the mirror z[n - k] (conj X0 + i conj X1);
+// loads are issued in batches of kU per thread before their stores.  With amp (k < nh) the
+// noise A(k) xi_w(k) of Eq. 1 is added to each half spectrum on the way (xi from noise_xi,
+// key seed, wires w0 and w1).  Ends without a barrier.
 __device__ __forceinline__ void stage_herm_pair(const float2* __restrict__ s0,
                                                 const float2* __restrict__ s1, int w0, int w1,
-                                                bool has1, int n_w, int nh, int n, float2* z)
+                                                bool has1, int n_w, int nh, int n, float2* z,
+                                                const float* __restrict__ amp = nullptr,
+                                                uint64_t seed = 0, uint32_t plane_id = 0)
 {
     constexpr int kU = 6;
     for (int base = threadIdx.x; base < nh; base += kU * blockDim.x) {
@@ -363,6 +368,23 @@ __device__ __forceinline__ void stage_herm_pair(const float2* __restrict__ s0,
             if (kk < nh) {
                 a[u] = __ldg(s0 + blk_index(kk, w0, n_w));
                 if (has1) b[u] = __ldg(s1 + blk_index(kk, w1, n_w));
+            }
+        }
+        if (amp) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int kk = base + u * blockDim.x;
+                if (kk < nh) {
+                    const float A = __ldg(amp + kk);
+                    const float2 x0 = noise_xi((uint32_t)w0, kk, n, plane_id, seed);
+                    a[u].x = fmaf(A, x0.x, a[u].x);
+                    a[u].y = fmaf(A, x0.y, a[u].y);
+                    if (has1) {
+                        const float2 x1 = noise_xi((uint32_t)w1, kk, n, plane_id, seed);
+                        b[u].x = fmaf(A, x1.x, b[u].x);
+                        b[u].y = fmaf(A, x1.y, b[u].y);
+                    }
+                }
             }
         }
 #pragma unroll

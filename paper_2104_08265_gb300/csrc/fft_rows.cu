@@ -242,7 +242,8 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     float2* Y = X + padded_len(N);
     const int w0 = 2 * blockIdx.x, w1 = w0 + 1;
     const bool has1 = w1 < d.n_w;
-    stage_herm_pair(mt, mt, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X);
+    stage_herm_pair(mt, mt, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X, d.noise_amp,
+                    d.noise_seed + (uint64_t)waves.ev[blockIdx.y], d.plane_id);
     __syncthreads();
     const float2* z = run_row_plan<true, FIX, kDirectThreads>(p, X, Y);
     float* o0 = wave + (int64_t)w0 * d.n_t;
@@ -309,6 +310,7 @@ cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* 
 {
     WavePtrs w;
     w.p[0] = wave;
+    w.ev[0] = 0;
     return launch_rows_c2r_batch(d, pt, mt, w, 1, s);
 }
 

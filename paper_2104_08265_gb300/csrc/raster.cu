@@ -17,6 +17,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "rng.cuh"
 #include "wcsim_internal.cuh"
 
 namespace wcsim {
@@ -85,45 +86,6 @@ __device__ __forceinline__ Decision decide(const RasterConsts& c, const DepoArra
     r.qatt = q * expf(-td_f * c.inv_tau);
     r.ok = 1;
     return r;
-}
-
-// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of the multiply-xor bijection with a
-// Weyl-sequence key schedule.
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp, 0 at 0).
-__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
-
-// Four standard normals from one Philox block: two Box-Muller pairs (Box & Muller 1958),
-// u = (x + 1/2) 2^-32; z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1), z2, z3 likewise.
-// Hardware log2 / sin / cos (absolute error ~1e-6 in z); the angle is taken as
-// 2 pi (u - 1/2) in [-pi, pi], where the hardware sine and cosine are accurate, and the
-// half turn is undone by negating both.
-__device__ __forceinline__ void box_muller4(uint4 x, float z[4])
-{
-    const float sc = 2.3283064365386963e-10f, off = 1.1641532182693481e-10f;
-    const float two_pi = 6.28318530717958648f, ln2x2 = -1.38629436111989061f;   // -2 ln 2
-    const float u0 = fmaf((float)x.x, sc, off), u1 = fmaf((float)x.y, sc, off);
-    const float u2 = fmaf((float)x.z, sc, off), u3 = fmaf((float)x.w, sc, off);
-    const float ra = sqrt_fast(ln2x2 * __log2f(u0)), rb = sqrt_fast(ln2x2 * __log2f(u2));
-    float sa, ca, sb, cb;
-    __sincosf(two_pi * (u1 - 0.5f), &sa, &ca);
-    __sincosf(two_pi * (u3 - 0.5f), &sb, &cb);
-    z[0] = -ra * ca;
-    z[1] = -ra * sa;
-    z[2] = -rb * cb;
-    z[3] = -rb * sb;
 }
 
 // erfc(|u|) at bin edge u = (koff - frac) s: the edge term of the bin masses below.

@@ -53,6 +53,7 @@ struct BatchEvents {
 
 struct WavePtrs {
     float* p[kMaxBatch];
+    int32_t ev[kMaxBatch];     // event index within the caller's batch (noise key offset)
 };
 
 cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* grid,
@@ -123,6 +124,12 @@ struct ConvDims {
     // limit of each device-side wait for a bulk asynchronous copy (ns of %globaltimer);
     // a wait that runs out raises the timeout flag and its CTA leaves
     uint64_t wait_ns = 2000000000ull;
+    // Eq. 1's noise, added to the wire-summed time spectra as the inverse time FFT stages
+    // them (null: none): A(k) / n_ft for k < nh (device), Philox key = noise_seed + event
+    // index, counter word 3 = plane_id
+    const float* noise_amp = nullptr;
+    uint64_t noise_seed = 0;
+    uint32_t plane_id = 0;
 };
 
 

@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_autotune": [vp, P(CDepos), vp, P(CTuneReport)],
         "wcsim_plane_reserve_batch": [vp, i32],
         "wcsim_plane_set_wait_limit": [vp, ctypes.c_uint64],
+        "wcsim_plane_set_noise": [vp, vp, i32, ctypes.c_uint64, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -316,6 +317,18 @@ class Plane:
         if st not in (OK, EDEVICE_CHECK):
             check(st)
         return int(f.value)
+
+    def set_noise(self, amp=None, seed: int = 0, stream=None):
+        """Eq. 1's noise for run / batch runs: amplitude spectrum amp (n_ft / 2 + 1 values,
+        host) and Philox seed; None turns it off.  See wcsim_plane_set_noise."""
+        import numpy as np
+        if amp is None:
+            check(lib().wcsim_plane_set_noise(self._h, None, 0, ctypes.c_uint64(0),
+                                              _stream_handle(stream)))
+            return
+        a = np.ascontiguousarray(amp, np.float32)
+        check(lib().wcsim_plane_set_noise(self._h, a.ctypes.data, a.size,
+                                          ctypes.c_uint64(int(seed)), _stream_handle(stream)))
 
     def set_wait_limit(self, ns: int):
         """Limit (ns) of the device-side waits for bulk copies; see wcsim_plane_set_wait_limit."""
