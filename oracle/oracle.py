@@ -20,6 +20,7 @@ Stages (paper Sec. 2.1.1, Eq. 1 and Eq. 2):
 * ``noise``      -- Eq. 1's additive term N(t, x): per wire, the normalised inverse DFT of an
   amplitude spectrum times unit complex Gaussians drawn from Philox4x32-10 (C code for the
   draws, numpy's irfft for the transform).
+* ``digitize``   -- M as ADC codes: clamp(floor(g M + p + 1/2), 0, 2^bits - 1) in FP32.
 
 Pins (tests, not this file): erf telescoping and quadrature for the weights, brute-force
 bin enumeration for the windows, direct circular-sum convolution on tiny grids, a point
@@ -246,6 +247,22 @@ def noise(geom, amp, n_ft: int, plane_id: int, seed: int) -> np.ndarray:
     assert amp.shape == (n_ft // 2 + 1,)
     xi = noise_spectrum(geom.n_wires, n_ft, plane_id, seed)
     return np.fft.irfft(amp[None, :] * xi, n=n_ft, axis=1)[:, : geom.n_ticks].copy()
+
+
+# --------------------------------------------------------------------------- digitization
+def digitize(wave, gain: float, pedestal: float, bits: int) -> np.ndarray:
+    """M as ADC codes (Eq. 1 reads M as "an ADC value"; the paper gives no digitizer):
+    code = clamp(floor(g M + p + 1/2), 0, 2^bits - 1), uint16.  The rounding is an integer
+    decision, so it is taken in FP32, one rounded operation at a time: x = fl(fl(g M) + p),
+    code = floor(fl(x + 1/2))."""
+    m = np.asarray(wave, np.float32)
+    g = np.float32(gain)
+    p = np.float32(pedestal)
+    x = (g * m).astype(np.float32) + p
+    x = np.asarray(x, np.float32) + np.float32(0.5)
+    code = np.floor(np.asarray(x, np.float32))
+    top = float((1 << int(bits)) - 1)
+    return np.clip(code, 0.0, top).astype(np.uint16)
 
 
 def convolve_adjoint(geom, response, grid, G):
