@@ -116,9 +116,23 @@ wcsim_status wcsim_rasterize(wcsim_plane* plane, const wcsim_depos* depos, float
 wcsim_status wcsim_convolve(wcsim_plane* plane, const float* grid, float* wave, void* stream);
 
 /* Whole signal simulation: zero the plane's grid, rasterize `depos` into it, convolve into
- * `wave` (DEVICE float32 [n_wires][n_ticks]).  Same concurrency rule as wcsim_convolve. */
+ * `wave` (DEVICE float32 [n_wires][n_ticks]), plus the plane's noise (Eq. 1) if it has
+ * one.  Same concurrency rule as wcsim_convolve. */
 wcsim_status wcsim_run(wcsim_plane* plane, const wcsim_depos* depos, float* wave,
                        void* stream);
+
+/* wcsim_run with the frame read out as ADC codes (Eq. 1 reads M as "an ADC value"; the paper
+ * gives no digitizer): `adc` (DEVICE uint16 [n_wires][n_ticks]) receives
+ * clamp(floor(fl(fl(gain M) + pedestal) + 1/2), 0, 2^bits - 1) with the plane's digitizer
+ * settings, each step one correctly rounded FP32 operation on the float frame wcsim_run
+ * would write.  WCSIM_EINVAL if no digitizer was set. */
+wcsim_status wcsim_run_adc(wcsim_plane* plane, const wcsim_depos* depos, uint16_t* adc,
+                           void* stream);
+
+/* Digitizer of wcsim_run_adc: gain (ADC counts per unit of M), pedestal (counts), bits in
+ * 1..16.  WCSIM_EINVAL for bits out of range or a non-finite gain or pedestal. */
+wcsim_status wcsim_plane_set_digitizer(wcsim_plane* plane, float gain, float pedestal,
+                                       int32_t bits);
 
 /* Bins each depo covers, as decided by wcsim_rasterize: `out` DEVICE int32 [n][4] =
  * (r_lo, r_hi, k_lo, k_hi) inclusive, or (-1, -1, -1, -1) when the depo covers nothing. */

@@ -75,6 +75,8 @@ struct wcsim_plane {
     float2* g2d = nullptr;      // adjoint: 2D spectrum of G, blocked [nkb][n_fw][4]
     float* noise_amp = nullptr; // Eq. 1's noise: A(k) / n_ft, k < nh (null: no noise)
     uint64_t noise_seed = 0;
+    float adc_gain = 0.0f, adc_pedestal = 0.0f;   // digitizer (adc_max 0: none set)
+    int32_t adc_max = 0;
     int* flags = nullptr;       // device flag word
     // scratch of batched runs: bcap events' grids, time-axis and wire-summed spectra
     float* bgrid = nullptr;
@@ -460,12 +462,16 @@ wcsim_status wcsim_convolve(wcsim_plane* pl, const float* grid, float* wave, voi
     return do_convolve(pl, grid, wave, s, 3);
 }
 
-wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, void* stream)
+// wcsim_run and wcsim_run_adc: rasterize into the plane's grid, then convolve (with the
+// plane's noise); adc: the inverse time FFT writes the plane's ADC codes to out.
+static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* out, bool adc,
+                              void* stream)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
     wcsim_status st = check_depos(depos);
     if (st) return st;
-    if (!wave) return fail(WCSIM_EINVAL, "wave is NULL");
+    if (!out) return fail(WCSIM_EINVAL, "output is NULL");
+    if (adc && pl->adc_max <= 0) return fail(WCSIM_EINVAL, "no digitizer set (wcsim_plane_set_digitizer)");
     DeviceGuard dg(pl->device);
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
@@ -485,11 +491,39 @@ wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, v
     // (the direct kernel; the staged one reads through bulk copies and leaves it as is)
     pl->dims.clear_input = (pl->dims.rows_variant == 0);
     with_noise(pl, pl->dims);
-    st = do_convolve(pl, pl->grid, wave, s, 3);
+    if (adc) {
+        pl->dims.adc_gain = pl->adc_gain;
+        pl->dims.adc_pedestal = pl->adc_pedestal;
+        pl->dims.adc_max = pl->adc_max;
+    }
+    st = do_convolve(pl, pl->grid, static_cast<float*>(out), s, 3);
     pl->dims.clear_input = 0;
     pl->dims.noise_amp = nullptr;
+    pl->dims.adc_max = 0;
     if (st == WCSIM_OK && pl->dims.rows_variant == 0) pl->grid_clean = true;
     return st;
+}
+
+wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, void* stream)
+{
+    return run_frame(pl, depos, wave, false, stream);
+}
+
+wcsim_status wcsim_run_adc(wcsim_plane* pl, const wcsim_depos* depos, uint16_t* adc, void* stream)
+{
+    return run_frame(pl, depos, adc, true, stream);
+}
+
+wcsim_status wcsim_plane_set_digitizer(wcsim_plane* pl, float gain, float pedestal, int32_t bits)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (bits < 1 || bits > 16) return fail(WCSIM_EINVAL, "ADC bits must be in 1..16 (got %d)", bits);
+    if (!isfinite(gain) || !isfinite(pedestal))
+        return fail(WCSIM_EINVAL, "ADC gain and pedestal must be finite");
+    pl->adc_gain = gain;
+    pl->adc_pedestal = pedestal;
+    pl->adc_max = (1 << bits) - 1;
+    return WCSIM_OK;
 }
 
 wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, const float* grid,

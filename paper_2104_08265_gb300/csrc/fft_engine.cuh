@@ -423,6 +423,42 @@ __device__ __forceinline__ void store_real_pair(const float2* z, float* __restri
     }
 }
 
+// ADC code of waveform value m: clamp(floor(fl(fl(g m) + p) + 1/2), 0, top), each step one
+// correctly rounded FP32 operation.
+__device__ __forceinline__ uint16_t adc_code(float m, float g, float p, float top)
+{
+    const float x = __fadd_rn(__fmul_rn(g, m), p);
+    const float c = floorf(__fadd_rn(x, 0.5f));
+    return (uint16_t)fminf(fmaxf(c, 0.0f), top);
+}
+
+// store_real_pair for ADC codes: row 0 (.x) to o0, row 1 (.y) to o1, uint16.  With vec (rows
+// 8-byte aligned, n_t a multiple of 4) a thread writes 4 codes per row with one 8-byte store.
+__device__ __forceinline__ void store_real_pair_adc(const float2* z, uint16_t* __restrict__ o0,
+                                                    uint16_t* __restrict__ o1, int n_t, bool has1,
+                                                    bool vec, float g, float p, float top)
+{
+    if (vec) {
+        uint2* p0 = reinterpret_cast<uint2*>(o0);
+        uint2* p1 = reinterpret_cast<uint2*>(o1);
+        for (int q = threadIdx.x; q < (n_t >> 2); q += blockDim.x) {
+            const int i = pad16(4 * q);
+            const float2 a = z[i], b = z[i + 1], c = z[i + 2], e = z[i + 3];
+            auto pack = [&](float u, float v) {
+                return (uint32_t)adc_code(u, g, p, top) | ((uint32_t)adc_code(v, g, p, top) << 16);
+            };
+            p0[q] = make_uint2(pack(a.x, b.x), pack(c.x, e.x));
+            if (has1) p1[q] = make_uint2(pack(a.y, b.y), pack(c.y, e.y));
+        }
+    } else {
+        for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
+            const float2 v = z[pad16(t)];
+            o0[t] = adc_code(v.x, g, p, top);
+            if (has1) o1[t] = adc_code(v.y, g, p, top);
+        }
+    }
+}
+
 // All passes of plan p.  The first pass reads through `first` (global memory or a shared
 // buffer outside X/Y), later passes ping-pong between X and Y.  Returns the buffer holding
 // the transform; ends with a block barrier.

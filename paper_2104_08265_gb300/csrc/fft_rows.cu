@@ -246,6 +246,14 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
                     d.noise_seed + (uint64_t)waves.ev[blockIdx.y], d.plane_id);
     __syncthreads();
     const float2* z = run_row_plan<true, FIX, kDirectThreads>(p, X, Y);
+    if (d.adc_max > 0) {                       // digitized: uint16 codes at the same rows
+        uint16_t* adc = reinterpret_cast<uint16_t*>(wave);
+        uint16_t* a0 = adc + (int64_t)w0 * d.n_t;
+        const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(adc) & 7) == 0);
+        store_real_pair_adc(z, a0, a0 + d.n_t, d.n_t, has1, vec, d.adc_gain, d.adc_pedestal,
+                            (float)d.adc_max);
+        return;
+    }
     float* o0 = wave + (int64_t)w0 * d.n_t;
     const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(wave) & 15) == 0);
     store_real_pair(z, o0, o0 + d.n_t, d.n_t, has1, vec);

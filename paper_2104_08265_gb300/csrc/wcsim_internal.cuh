@@ -130,6 +130,10 @@ struct ConvDims {
     const float* noise_amp = nullptr;
     uint64_t noise_seed = 0;
     uint32_t plane_id = 0;
+    // adc_max > 0: the inverse time FFT writes ADC codes (uint16) instead of floats:
+    // clamp(floor(fl(fl(adc_gain M) + adc_pedestal) + 1/2), 0, adc_max)
+    float adc_gain = 0.0f, adc_pedestal = 0.0f;
+    int32_t adc_max = 0;
 };
 
 

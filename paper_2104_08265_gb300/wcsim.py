@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_reserve_batch": [vp, i32],
         "wcsim_plane_set_wait_limit": [vp, ctypes.c_uint64],
         "wcsim_plane_set_noise": [vp, vp, i32, ctypes.c_uint64, vp],
+        "wcsim_run_adc": [vp, P(CDepos), vp, vp],
+        "wcsim_plane_set_digitizer": [vp, ctypes.c_float, ctypes.c_float, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -238,6 +240,23 @@ class Plane:
         out = self._wave(out)
         check(lib().wcsim_run(self._h, ctypes.byref(depos.c), out.data_ptr(),
                               _stream_handle(stream)))
+        return out
+
+    def set_digitizer(self, gain: float, pedestal: float, bits: int):
+        """ADC settings of run_adc; see wcsim_plane_set_digitizer."""
+        check(lib().wcsim_plane_set_digitizer(self._h, float(gain), float(pedestal), int(bits)))
+
+    def run_adc(self, depos: DeviceDepos, out=None, stream=None):
+        """The frame of run() as ADC codes: a [n_wires, n_ticks] int16 tensor holding the
+        uint16 codes' bits (view the host copy as uint16)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.geom.n_wires, self.geom.n_ticks), dtype=torch.int16,
+                              device="cuda")
+        assert out.dtype == torch.int16 and out.is_contiguous()
+        assert tuple(out.shape) == (self.geom.n_wires, self.geom.n_ticks)
+        check(lib().wcsim_run_adc(self._h, ctypes.byref(depos.c), out.data_ptr(),
+                                  _stream_handle(stream)))
         return out
 
     # ------------------------------------------------------------ adjoint
