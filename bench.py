@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-noise", action="store_true",
-                    help="skip the forward timed with Eq. 1's noise on")
+                    help="skip the forwards timed with Eq. 1's noise on and with ADC readout")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-event batched run (wcsim_batch_run vs 64 wcsim_run calls)")
     ap.add_argument("--soak-s", type=float, default=0.5,
@@ -515,6 +515,25 @@ def run_gpu(args):
         noise = {"ms_per_step": nms, "depos_per_s": len(d) / (nms * 1e-3),
                  "model": "spectral noise per wire, A(k) = sqrt(n_t) / (1 + (k / 0.1 n_t)^2)"}
 
+    # ---- the same forward read out as 12-bit ADC codes (wcsim_run_adc)
+    adc = None
+    if not args.no_noise:
+        plane.set_digitizer(2.0, 2048.0, 12)
+        codes = torch.empty((g.n_wires, g.n_ticks), dtype=torch.int16, device="cuda")
+        for _ in range(args.warmup):
+            plane.run_adc(dd, out=codes)
+        as_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ae_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            as_[i].record(stream)
+            plane.run_adc(dd, out=codes)
+            ae_[i].record(stream)
+        torch.cuda.synchronize()
+        ams = sum(a.elapsed_time(b) for a, b in zip(as_, ae_)) / args.steps
+        adc = {"ms_per_step": ams, "depos_per_s": len(d) / (ams * 1e-3),
+               "digitizer": "gain 2, pedestal 2048, 12 bits"}
+
     # ---- forward + backward (loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10,
     # lifetime 8 ms; the backward runs on the mean path and includes dL/dR)
     fb_ms = None
@@ -667,6 +686,7 @@ def run_gpu(args):
         "cufft_comparison": cufft,
         "batch64": batch,
         "with_noise": noise,
+        "adc_readout": adc,
         "autotune": tune,
         "clocks": clk,
     }
