@@ -67,7 +67,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("v_mm_per_us", ctypes.c_double), ("DL_cm2_s", ctypes.c_double),
                 ("DT_cm2_s", ctypes.c_double), ("lifetime_us", ctypes.c_double),
                 ("nsigma", ctypes.c_double), ("fluctuate", ctypes.c_int32),
-                ("plane_id", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+                ("plane_id", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("renormalize", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _load():
@@ -108,7 +109,8 @@ def _geom(g) -> _Geom:
 def _params(p) -> _Params:
     return _Params(float(p.v_mm_per_us), float(p.DL_cm2_s), float(p.DT_cm2_s),
                    float(p.lifetime_us), float(p.nsigma), int(p.fluctuate),
-                   int(p.plane_id) & 0xFFFFFFFF, int(p.seed) & 0xFFFFFFFFFFFFFFFF)
+                   int(p.plane_id) & 0xFFFFFFFF, int(p.seed) & 0xFFFFFFFFFFFFFFFF,
+                   int(getattr(p, "renormalize", 0)), 0)
 
 
 def _ptr(a, ct):

@@ -24,7 +24,8 @@
  *     CUDA kernel uses (position in FP64 bin units, half-width n*sigma/bin in FP32), so that
  *     both sides pick the same bins; everything else here is FP64;
  *   - sigma == 0 (in that FP32 decision) puts all of an axis' weight into the single bin;
- *   - no renormalisation after truncation;
+ *   - no renormalisation after truncation, unless renormalize is set: then each axis'
+ *     weights are divided by their sum over the window (the truncated patch carries Q');
  *   - one Philox block per aligned group of four ticks of a row: counter = (k div 4, row r,
  *     depo id, plane id), key = (seed lo, seed hi).  Its four words form two Box-Muller
  *     pairs, u = (x + 0.5) 2^-32, giving four normals
@@ -52,6 +53,8 @@ typedef struct {
     int32_t fluctuate;
     uint32_t plane_id;
     uint64_t seed;
+    int32_t renormalize;   /* 1: each axis' weights divided by their sum over the window */
+    int32_t reserved;
 } og_params;
 
 /* ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random numbers: as
@@ -260,6 +263,23 @@ static void axis_weight_derivs(double mu, double sig, int delta, double origin, 
     }
 }
 
+/* Post-truncation renormalisation of one axis: w / T with T = sum of w over the window;
+ * with dmu, dsig (may be NULL) the quotient rule, d(w/T) = (dw - (w/T) sum dw) / T. */
+static void renormalize_axis(int64_t n, double* w, double* dmu, double* dsig)
+{
+    double T = 0.0, sm = 0.0, ss = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        T += w[i];
+        if (dmu) sm += dmu[i];
+        if (dsig) ss += dsig[i];
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        w[i] /= T;
+        if (dmu) dmu[i] = (dmu[i] - w[i] * sm) / T;
+        if (dsig) dsig[i] = (dsig[i] - w[i] * ss) / T;
+    }
+}
+
 #define OG_MAXB 4096
 
 /* Bins each depo covers: out[4*i + (0..3)] = r_lo, r_hi, k_lo, k_hi, or -1s if none. */
@@ -289,6 +309,10 @@ int og_depo_weights(const og_geom* g, const og_params* pr, double p, double t, d
     double dp = g->pitch_mm / (double)g->n_imp;
     axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
     axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
+    if (pr->renormalize) {
+        renormalize_axis(d.r_hi - d.r_lo + 1, wp, NULL, NULL);
+        renormalize_axis(d.k_hi - d.k_lo + 1, wt, NULL, NULL);
+    }
     *qatt = d.qatt;
     return 1;
 }
@@ -309,6 +333,10 @@ int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double*
         if (d.r_hi - d.r_lo + 1 > OG_MAXB || d.k_hi - d.k_lo + 1 > OG_MAXB) return -1;
         axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
         axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
+        if (pr->renormalize) {
+            renormalize_axis(d.r_hi - d.r_lo + 1, wp, NULL, NULL);
+            renormalize_axis(d.k_hi - d.k_lo + 1, wt, NULL, NULL);
+        }
         for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
             double* row = grid + r * nt;
             for (int64_t k = d.k_lo; k <= d.k_hi; ++k) {
@@ -355,6 +383,10 @@ int og_depo_grads(const og_geom* g, const og_params* pr, int64_t n, const double
                            dwp_mu, dwp_s);
         axis_weight_derivs(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo,
                            d.k_hi, dwt_mu, dwt_s);
+        if (pr->renormalize) {
+            renormalize_axis(d.r_hi - d.r_lo + 1, wp, dwp_mu, dwp_s);
+            renormalize_axis(d.k_hi - d.k_lo + 1, wt, dwt_mu, dwt_s);
+        }
         double a_q = 0.0, a_pm = 0.0, a_ps = 0.0, a_tm = 0.0, a_ts = 0.0;
         for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
             const double* row = dS + r * nt;

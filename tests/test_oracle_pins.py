@@ -431,3 +431,66 @@ def test_depo_sigma_grads_individually():
     sL = math.sqrt(2 * 6.0e-4 * 33.0)
     assert gr["DT"] == pytest.approx(gr["sigma_T"][0] * sT / (2 * 10.0), rel=1e-12)
     assert gr["DL"] == pytest.approx(gr["sigma_L"][0] * sL / (2 * 6.0), rel=1e-12)
+
+
+# ------------------------------------------------------------------ renormalized patches
+def test_renormalized_patch_carries_exactly_the_attenuated_charge():
+    """With renormalize the truncated patch sums to Q' = Q exp(-t_d / tau); without it the
+    truncation loses the tails; the two patches are proportional."""
+    import dataclasses
+    g = S.Geometry(n_wires=16, n_imp=10, n_ticks=1024, pitch_mm=3.0)
+    prm = S.DriftParams(nsigma=2.0)
+    rn = dataclasses.replace(prm, renormalize=1)
+    rng = np.random.default_rng(31)
+    for _ in range(8):
+        p = rng.uniform(10, 38); t = rng.uniform(5, 40); td = rng.uniform(50, 300)
+        d = one(p, t, td, 7000.0)
+        qatt = 7000.0 * np.exp(-td / prm.lifetime_us)
+        plain, norm = O.rasterize(g, prm, d), O.rasterize(g, rn, d)
+        assert norm.sum() == pytest.approx(qatt, rel=1e-12)
+        assert plain.sum() < qatt * (1 - 1e-3)              # 2-sigma windows lose ~9%
+        nz = plain > 0
+        ratio = norm[nz] / plain[nz]
+        assert np.ptp(ratio) <= 1e-12 * ratio.max()
+
+
+def test_renormalized_grads_match_central_finite_differences():
+    """The quotient-rule gradients of renormalized patches against FP64 finite differences
+    (window frozen), in Q, p, t, D_L, D_T and tau."""
+    import dataclasses
+    g = S.Geometry(n_wires=12, n_imp=10, n_ticks=128, pitch_mm=3.0)
+    rng = np.random.default_rng(41)
+    R = S.make_response(g, "induction").astype(np.complex128)
+    G = rng.normal(size=(g.n_wires, g.n_ticks))
+    prm = S.DriftParams(DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0, renormalize=1)
+    checked = 0
+    for trial in range(6):
+        p = rng.uniform(8, 28); t = rng.uniform(5, 20); td = rng.uniform(20, 40); q = 5000.0
+        d = one(p, t, td, q)
+        w0 = O.windows(g, prm, d)[0]
+        dS, _ = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G)
+        gr = O.depo_grads(g, prm, d, dS)
+
+        def fd(make, x, rel):
+            h = rel * abs(x)
+            dp_, dm_ = make(x + h), make(x - h)
+            for (dd, pp) in (dp_, dm_):
+                if not np.array_equal(O.windows(g, pp, dd)[0], w0):
+                    return None
+            return (_loss(g, dp_[1], R, dp_[0], G) - _loss(g, dm_[1], R, dm_[0], G)) / (2 * h)
+        cases = [
+            ("q", lambda x: (one(p, t, td, x), prm), q, gr["q"][0]),
+            ("p", lambda x: (one(x, t, td, q), prm), p, gr["p"][0]),
+            ("t", lambda x: (one(p, x, td, q), prm), t, gr["t"][0]),
+            ("DL", lambda x: (d, dataclasses.replace(prm, DL_cm2_s=x)), prm.DL_cm2_s, gr["DL"]),
+            ("DT", lambda x: (d, dataclasses.replace(prm, DT_cm2_s=x)), prm.DT_cm2_s, gr["DT"]),
+            ("tau", lambda x: (d, dataclasses.replace(prm, lifetime_us=x)), prm.lifetime_us, gr["lifetime"]),
+        ]
+        for name, make, x, ana in cases:
+            num = fd(make, x, 1e-6 if name in ("p", "t") else 1e-4)
+            if num is None:
+                continue
+            scale = max(abs(num), abs(ana), 1e-30)
+            assert abs(num - ana) <= 2e-5 * scale + 1e-9, (name, num, ana)
+            checked += 1
+    assert checked >= 30
