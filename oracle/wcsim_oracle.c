@@ -25,7 +25,10 @@
  *     both sides pick the same bins; everything else here is FP64;
  *   - sigma == 0 (in that FP32 decision) puts all of an axis' weight into the single bin;
  *   - no renormalisation after truncation, unless renormalize is set: then each axis'
- *     weights are divided by their sum over the window (the truncated patch carries Q');
+ *     weights are divided by their sum T over the whole n-sigma window before it is clipped
+ *     to the grid, so that the patch carries Q' less only what falls outside the grid (the
+ *     truncation is compensated, the grid border is not).  That window holds the mean, so
+ *     T >= erf(n / sqrt 2) never underflows;
  *   - one Philox block per aligned group of four ticks of a row: counter = (k div 4, row r,
  *     depo id, plane id), key = (seed lo, seed hi).  Its four words form two Box-Muller
  *     pairs, u = (x + 0.5) 2^-32, giving four normals
@@ -53,7 +56,8 @@ typedef struct {
     int32_t fluctuate;
     uint32_t plane_id;
     uint64_t seed;
-    int32_t renormalize;   /* 1: each axis' weights divided by their sum over the window */
+    int32_t renormalize;   /* 1: each axis' weights divided by their sum over the n-sigma
+                              window before clipping to the grid */
     int32_t reserved;
 } og_params;
 
@@ -154,8 +158,10 @@ static og_consts make_consts(const og_geom* g, const og_params* pr)
 }
 
 /* One axis of the bin decision.  x: depo position in bin units (FP64), hw: half-width
- * n*sigma/bin (FP32).  Returns 0 if no bin of [0, n) is covered. */
-static int axis_window(double x, float hw, int64_t n, int64_t* lo, int64_t* hi)
+ * n*sigma/bin (FP32).  lo_u, hi_u receive the window before clipping to [0, n), lo, hi the
+ * clipped one.  Returns 0 if no bin of [0, n) is covered. */
+static int axis_window(double x, float hw, int64_t n, int64_t* lo, int64_t* hi,
+                       int64_t* lo_u, int64_t* hi_u)
 {
     if (!(x > -1e12 && x < 1e12)) return 0;       /* also rejects NaN */
     double i0 = floor(x);
@@ -164,6 +170,8 @@ static int axis_window(double x, float hw, int64_t n, int64_t* lo, int64_t* hi)
     float b = frac + hw;
     double l = i0 + floor((double)a);
     double h = i0 + floor((double)b);
+    *lo_u = (int64_t)l;
+    *hi_u = (int64_t)h;
     if (l < 0.0) l = 0.0;
     if (h > (double)(n - 1)) h = (double)(n - 1);
     if (l > h) return 0;
@@ -176,6 +184,7 @@ static int axis_window(double x, float hw, int64_t n, int64_t* lo, int64_t* hi)
 typedef struct {
     int ok;                        /* 0: contributes nothing */
     int64_t r_lo, r_hi, k_lo, k_hi;
+    int64_t r_lo_u, r_hi_u, k_lo_u, k_hi_u;   /* the same windows before clipping */
     double mu_p, mu_t;             /* pitch position [mm] and arrival time [us] */
     double sig_p, sig_t;           /* FP64 sigma_T [mm], sigma_t [us] */
     int delta_p, delta_t;          /* sigma == 0 in the FP32 decision */
@@ -210,8 +219,8 @@ static og_depo drift_and_window(const og_geom* g, const og_params* pr, const og_
     double xp = (p - g->p0_mm) * c->inv_dp;
     double xt = (d.mu_t - g->t0_us) * c->inv_dt;
     int64_t nrows = (int64_t)g->n_wires * g->n_imp;
-    if (!axis_window(xp, hw_p, nrows, &d.r_lo, &d.r_hi)) return d;
-    if (!axis_window(xt, hw_t, g->n_ticks, &d.k_lo, &d.k_hi)) return d;
+    if (!axis_window(xp, hw_p, nrows, &d.r_lo, &d.r_hi, &d.r_lo_u, &d.r_hi_u)) return d;
+    if (!axis_window(xt, hw_t, g->n_ticks, &d.k_lo, &d.k_hi, &d.k_lo_u, &d.k_hi_u)) return d;
     d.ok = 1;
     return d;
 }
@@ -263,16 +272,37 @@ static void axis_weight_derivs(double mu, double sig, int delta, double origin, 
     }
 }
 
-/* Post-truncation renormalisation of one axis: w / T with T = sum of w over the window;
- * with dmu, dsig (may be NULL) the quotient rule, d(w/T) = (dw - (w/T) sum dw) / T. */
-static void renormalize_axis(int64_t n, double* w, double* dmu, double* dsig)
+#define OG_MAXB 4096
+
+/* Sums over the bins lo..hi of one axis of the weights (T) and, when wanted, of their mu
+ * and sigma derivatives (sm, ss), bin by bin with the definitions above, OG_MAXB bins at a
+ * time.  Returns 0, or -1 for a window of more than 2^26 bins. */
+static int axis_sums(double mu, double sig, int delta, double origin, double bin, int64_t lo,
+                     int64_t hi, double* T, double* sm, double* ss)
 {
-    double T = 0.0, sm = 0.0, ss = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        T += w[i];
-        if (dmu) sm += dmu[i];
-        if (dsig) ss += dsig[i];
+    static double w[OG_MAXB], dm[OG_MAXB], ds[OG_MAXB];
+    *T = 0.0;
+    if (sm) *sm = 0.0;
+    if (ss) *ss = 0.0;
+    if (hi - lo + 1 > ((int64_t)1 << 26)) return -1;
+    for (int64_t c0 = lo; c0 <= hi; c0 += OG_MAXB) {
+        int64_t c1 = (c0 + OG_MAXB - 1 < hi) ? c0 + OG_MAXB - 1 : hi;
+        axis_weights(mu, sig, delta, origin, bin, c0, c1, w);
+        if (sm) axis_weight_derivs(mu, sig, delta, origin, bin, c0, c1, dm, ds);
+        for (int64_t i = 0; i <= c1 - c0; ++i) {
+            *T += w[i];
+            if (sm) { *sm += dm[i]; *ss += ds[i]; }
+        }
     }
+    return 0;
+}
+
+/* Post-truncation renormalisation of one axis: the n window weights w (and, if not NULL,
+ * their derivatives dmu, dsig) divided by the totals T, sm, ss of the unclipped window, by
+ * the quotient rule d(w/T) = (dw - (w/T) dT) / T. */
+static void renormalize_axis(int64_t n, double* w, double* dmu, double* dsig, double T,
+                             double sm, double ss)
+{
     for (int64_t i = 0; i < n; ++i) {
         w[i] /= T;
         if (dmu) dmu[i] = (dmu[i] - w[i] * sm) / T;
@@ -280,7 +310,25 @@ static void renormalize_axis(int64_t n, double* w, double* dmu, double* dsig)
     }
 }
 
-#define OG_MAXB 4096
+/* Renormalisation of both axes of depo d (weights, and derivatives when dwp_mu != NULL). */
+static int renormalize_depo(const og_geom* g, const og_depo* d, double* wp, double* wt,
+                            double* dwp_mu, double* dwp_s, double* dwt_mu, double* dwt_s)
+{
+    const double dp = g->pitch_mm / (double)g->n_imp;
+    double T, sm, ss;
+    if (axis_sums(d->mu_p, d->sig_p, d->delta_p, g->p0_mm, dp, d->r_lo_u, d->r_hi_u, &T,
+                  dwp_mu ? &sm : NULL, dwp_mu ? &ss : NULL))
+        return -1;
+    renormalize_axis(d->r_hi - d->r_lo + 1, wp, dwp_mu, dwp_s, T, dwp_mu ? sm : 0.0,
+                     dwp_mu ? ss : 0.0);
+    if (axis_sums(d->mu_t, d->sig_t, d->delta_t, g->t0_us, g->tick_us, d->k_lo_u, d->k_hi_u,
+                  &T, dwt_mu ? &sm : NULL, dwt_mu ? &ss : NULL))
+        return -1;
+    renormalize_axis(d->k_hi - d->k_lo + 1, wt, dwt_mu, dwt_s, T, dwt_mu ? sm : 0.0,
+                     dwt_mu ? ss : 0.0);
+    return 0;
+}
+
 
 /* Bins each depo covers: out[4*i + (0..3)] = r_lo, r_hi, k_lo, k_hi, or -1s if none. */
 void og_windows(const og_geom* g, const og_params* pr, int64_t n, const double* p,
@@ -309,10 +357,7 @@ int og_depo_weights(const og_geom* g, const og_params* pr, double p, double t, d
     double dp = g->pitch_mm / (double)g->n_imp;
     axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
     axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
-    if (pr->renormalize) {
-        renormalize_axis(d.r_hi - d.r_lo + 1, wp, NULL, NULL);
-        renormalize_axis(d.k_hi - d.k_lo + 1, wt, NULL, NULL);
-    }
+    if (pr->renormalize && renormalize_depo(g, &d, wp, wt, NULL, NULL, NULL, NULL)) return 0;
     *qatt = d.qatt;
     return 1;
 }
@@ -333,10 +378,8 @@ int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double*
         if (d.r_hi - d.r_lo + 1 > OG_MAXB || d.k_hi - d.k_lo + 1 > OG_MAXB) return -1;
         axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
         axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
-        if (pr->renormalize) {
-            renormalize_axis(d.r_hi - d.r_lo + 1, wp, NULL, NULL);
-            renormalize_axis(d.k_hi - d.k_lo + 1, wt, NULL, NULL);
-        }
+        if (pr->renormalize && renormalize_depo(g, &d, wp, wt, NULL, NULL, NULL, NULL))
+            return -1;
         for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
             double* row = grid + r * nt;
             for (int64_t k = d.k_lo; k <= d.k_hi; ++k) {
@@ -383,10 +426,9 @@ int og_depo_grads(const og_geom* g, const og_params* pr, int64_t n, const double
                            dwp_mu, dwp_s);
         axis_weight_derivs(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo,
                            d.k_hi, dwt_mu, dwt_s);
-        if (pr->renormalize) {
-            renormalize_axis(d.r_hi - d.r_lo + 1, wp, dwp_mu, dwp_s);
-            renormalize_axis(d.k_hi - d.k_lo + 1, wt, dwt_mu, dwt_s);
-        }
+        if (pr->renormalize &&
+            renormalize_depo(g, &d, wp, wt, dwp_mu, dwp_s, dwt_mu, dwt_s))
+            return -1;
         double a_q = 0.0, a_pm = 0.0, a_ps = 0.0, a_tm = 0.0, a_ts = 0.0;
         for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
             const double* row = dS + r * nt;

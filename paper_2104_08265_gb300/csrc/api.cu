@@ -122,6 +122,9 @@ wcsim_status check_params(const wcsim_drift_params* p)
     if (!(p->lifetime_us > 0.0)) return fail(WCSIM_EINVAL, "lifetime_us must be > 0");
     if (!finite_pos(p->nsigma)) return fail(WCSIM_EINVAL, "nsigma must be finite and > 0");
     if (p->fluctuate != 0 && p->fluctuate != 1) return fail(WCSIM_EINVAL, "fluctuate must be 0 or 1");
+    if (p->renormalize != 0 && p->renormalize != 1)
+        return fail(WCSIM_EINVAL, "renormalize must be 0 or 1");
+    if (p->reserved != 0) return fail(WCSIM_EINVAL, "reserved must be 0");
     return WCSIM_OK;
 }
 
@@ -160,6 +163,7 @@ RasterConsts make_consts(const wcsim_plane* pl)
     c.n_rows = (int64_t)g.n_wires * g.n_imp;
     c.n_ticks = g.n_ticks;
     c.fluctuate = p.fluctuate;
+    c.renorm = p.renormalize;
     c.key0 = (uint32_t)p.seed;
     c.key1 = (uint32_t)(p.seed >> 32);
     c.plane_id = p.plane_id;

@@ -27,15 +27,49 @@ constexpr int kWarps = 8;       // warps per block
 constexpr int kDepos = 64;      // depos per block
 constexpr int kWmax = 64;       // weights per axis held per patch tile
 
-struct Decision {
+struct Decision {                // 64 bytes, no padding
+    int64_t i0p, i0t;           // floor of the depo position in bin units
     int32_t ok;                 // covers >= 1 bin and carries charge
     int32_t r_lo, r_hi, k_lo, k_hi;
-    int64_t i0p, i0t;           // floor of the depo position in bin units
     float frac_p, frac_t;       // position - floor, FP32
     float sp, st;               // sigma_T [mm], sigma_t [us] (FP32)
     float qatt;                 // Q' = Q exp(-t_d / lifetime)
+    float qw;                   // scale of the weight products: Q', or Q' / (T_p T_t) when
+                                // each axis is renormalised over its window
     uint32_t id;                // depo id (fluctuation key)
 };
+static_assert(sizeof(Decision) == 64, "Decision packs into 64 bytes");
+
+// Normal mass between two edges at u = offset / (sqrt(2) sigma) from their edge terms
+// ea = erfc|ua|, eb = erfc|ub|: 0.5 (erfc ua - erfc ub) on the upper side of the mean,
+// 0.5 (erfc -ub - erfc -ua) on the lower side (both keep relative precision in the tails),
+// 1 - 0.5 (ea + eb) for a span holding the mean.
+__device__ __forceinline__ float span_mass(float ua, float ub, float ea, float eb)
+{
+    if (ua >= 0.0f) return 0.5f * (ea - eb);
+    if (ub <= 0.0f) return 0.5f * (eb - ea);
+    return 1.0f - 0.5f * (ea + eb);
+}
+
+// Edge u of one axis' n-sigma window before it is clipped to the grid: the lower edge
+// floor(frac - hw) or the upper edge floor(frac + hw) + 1 (offsets from the floor of the
+// position, in bins; the same FP32 operations as the bin decision).
+__device__ __forceinline__ float outer_edge_u(float frac, float hw, float s, bool upper)
+{
+    const float e = upper ? floorf(__fadd_rn(frac, hw)) + 1.0f : floorf(__fsub_rn(frac, hw));
+    return (e - frac) * s;
+}
+
+// Total weight T of one axis' unclipped window: the bin masses telescope to the mass
+// between its outer edges, which lie on either side of the mean, so T >= erf(n / sqrt 2).
+// sigma == 0 (s == 0) puts the whole weight in the window's one bin.
+__device__ __forceinline__ float window_mass(float frac, float hw, float s)
+{
+    if (!(s > 0.0f)) return 1.0f;
+    const float ua = outer_edge_u(frac, hw, s, false);
+    const float ub = outer_edge_u(frac, hw, s, true);
+    return span_mass(ua, ub, erfcf(fabsf(ua)), erfcf(fabsf(ub)));
+}
 
 // One axis of the bin decision.  Every operation is an explicitly rounded IEEE operation
 // (no contraction), so that the result is a function of the inputs alone.
@@ -59,9 +93,10 @@ __device__ __forceinline__ bool axis_window(double x, float hw, int64_t n, int32
 }
 
 // Drift (t_a = t + t_d, Q' = Q e^{-t_d/tau}, sigma = sqrt(2 D t_d)) and the window of bins
-// whose span meets [mu - n sigma, mu + n sigma], clipped to the grid.
+// whose span meets [mu - n sigma, mu + n sigma], clipped to the grid.  The weight scale qw
+// is formed only when `weights` is set (the forward); elsewhere it is left at Q'.
 __device__ __forceinline__ Decision decide(const RasterConsts& c, const DepoArrays& d,
-                                           int64_t i, int* flags)
+                                           int64_t i, int* flags, bool weights = false)
 {
     Decision r;
     r.ok = 0;
@@ -84,6 +119,15 @@ __device__ __forceinline__ Decision decide(const RasterConsts& c, const DepoArra
     if (!axis_window(xp, hw_p, c.n_rows, r.r_lo, r.r_hi, r.i0p, r.frac_p)) return r;
     if (!axis_window(xt, hw_t, c.n_ticks, r.k_lo, r.k_hi, r.i0t, r.frac_t)) return r;
     r.qatt = q * expf(-td_f * c.inv_tau);
+    r.qw = r.qatt;
+    if (weights && c.renorm) {
+        // each axis' weights divided by their sum T over the n-sigma window before it is
+        // clipped to the grid: the truncation is compensated, charge beyond the grid's
+        // border stays lost
+        const float s_p = (r.sp > 0.0f) ? c.dp_f / (1.41421356237309505f * r.sp) : 0.0f;
+        const float s_t = (r.st > 0.0f) ? c.dt_f / (1.41421356237309505f * r.st) : 0.0f;
+        r.qw = r.qatt / (window_mass(r.frac_p, hw_p, s_p) * window_mass(r.frac_t, hw_t, s_t));
+    }
     r.ok = 1;
     return r;
 }
@@ -94,17 +138,13 @@ __device__ __forceinline__ float edge_erfc(int64_t koff, float frac, float s)
     return erfcf(fabsf(((float)koff - frac) * s));
 }
 
-// Mass of the bin between edges a < b from their edge terms ea = erfc|ua|, eb = erfc|ub|:
-// 0.5 (erfc ua - erfc ub) on the upper side of the mean, 0.5 (erfc -ub - erfc -ua) on the
-// lower side (both keep relative precision in the tails), 1 - 0.5 (ea + eb) for the bin
-// holding the mean.  u = offset / (sqrt(2) sigma), so that erfc gives the normal tail mass.
+// Mass of the bin [koff, koff + 1) (offset from the floor of the position, in bins) from
+// its edge terms ea = erfc|ua|, eb = erfc|ub|.
 __device__ __forceinline__ float bin_mass(int64_t koff, float frac, float s, float ea, float eb)
 {
     const float ua = ((float)koff - frac) * s;
     const float ub = ((float)(koff + 1) - frac) * s;
-    if (ua >= 0.0f) return 0.5f * (ea - eb);
-    if (ub <= 0.0f) return 0.5f * (eb - ea);
-    return 1.0f - 0.5f * (ea + eb);
+    return span_mass(ua, ub, ea, eb);
 }
 
 // Lanes per depo group: 8 lanes take one depo, so that the four groups of a warp work on
@@ -134,7 +174,7 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
         r.ok = 0;
         const int64_t i = base + threadIdx.x;
         if (i < d.n) {
-            r = decide(c, d, i, flags);
+            r = decide(c, d, i, flags, true);
             r.id = d.id[i];
         }
         s_dec[threadIdx.x] = r;
@@ -172,7 +212,7 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                 __syncwarp(gmask);
                 for (int e = gl; e < nr + 4 * nq; e += G) {
                     if (e < nr) {
-                        wp[e] = dd.qatt * ((dd.sp > 0.0f)
+                        wp[e] = dd.qw * ((dd.sp > 0.0f)
                                     ? bin_mass((int64_t)(r0 + e) - dd.i0p, dd.frac_p, s_p, ed[e], ed[e + 1])
                                     : 1.0f);
                     } else {
@@ -252,10 +292,38 @@ __device__ __forceinline__ float group_sum(float v, unsigned mask)
     return v;
 }
 
+// Renormalisation factors of one depo for the adjoint: 1 / T and the telescoped dT/dmu,
+// dT/dsigma per axis (rows, then ticks), T the unclipped window's mass between its outer
+// edges: dT/dmu = -(phi(B') - phi(A')) / sigma, dT/dsigma = -(B' phi(B') - A' phi(A')) /
+// sigma.  The identity (1, 0, 0) when renormalisation is off or sigma == 0.
+__device__ __forceinline__ void renorm_factors(const RasterConsts& c, const Decision& r, float* f)
+{
+    f[0] = 1.0f; f[1] = 0.0f; f[2] = 0.0f;
+    f[3] = 1.0f; f[4] = 0.0f; f[5] = 0.0f;
+    if (!c.renorm || !r.ok) return;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        const float sg = ax ? r.st : r.sp;
+        if (!(sg > 0.0f)) continue;
+        const float bin = ax ? c.dt_f : c.dp_f;
+        const float s = bin / (1.41421356237309505f * sg);
+        const float hw = __fmul_rn(__fmul_rn(c.nsig, sg), ax ? c.inv_dt_f : c.inv_dp_f);
+        const float frac = ax ? r.frac_t : r.frac_p;
+        const float ua = outer_edge_u(frac, hw, s, false), ub = outer_edge_u(frac, hw, s, true);
+        const float pa = 0.398942280401432678f * expf(-ua * ua);
+        const float pb = 0.398942280401432678f * expf(-ub * ub);
+        const float isg = 1.0f / sg;
+        f[3 * ax + 0] = 1.0f / span_mass(ua, ub, erfcf(fabsf(ua)), erfcf(fabsf(ub)));
+        f[3 * ax + 1] = -(pb - pa) * isg;
+        f[3 * ax + 2] = -1.41421356237309505f * (ub * pb - ua * pa) * isg;
+    }
+}
+
 // Per depo (a half warp each, so that the per-group tiles fit static shared memory):
 // recompute the patch weights and their mu / sigma derivatives, gather dL/dS over the patch
 // and apply the chain rule through Q' = Q exp(-t_d / tau), t_a = t + t_d and
 // sigma = sqrt(2 D t_d).  The global sums are reduced per block in FP64.
+template <bool RN>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, DepoGrads g,
                int* flags)
@@ -273,6 +341,9 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
     // per depo, the FP32 factors of its terms in the three global sums (dL/dsigma_L,
     // sigma_L; dL/dsigma_T, sigma_T; dL/dQ', Q'), zero for depos that add nothing
     __shared__ float s_gt[kDepos][6];
+    // per depo, the renormalisation factors of its rows and ticks: 1 / T, dT/dmu, dT/dsigma
+    // (an instance of its own, so that the plain adjoint keeps its registers)
+    __shared__ float s_rn[RN ? kDepos : 1][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = threadIdx.x % G, grp = threadIdx.x / G;
     const unsigned gmask = ((1u << G) - 1u) << (lane & ~(G - 1));
@@ -286,6 +357,7 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
             r.id = d.id[i];
         }
         s_dec[threadIdx.x] = r;
+        if (RN) renorm_factors(c, r, s_rn[threadIdx.x]);
 #pragma unroll
         for (int k = 0; k < 6; ++k) s_gt[threadIdx.x][k] = 0.0f;
     }
@@ -311,6 +383,9 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
             const float s_t = (dd.st > 0.0f) ? c.dt_f / (1.41421356237309505f * dd.st) : 0.0f;
             const float isp = (dd.sp > 0.0f) ? 1.0f / dd.sp : 0.0f;
             const float ist = (dd.st > 0.0f) ? 1.0f / dd.st : 0.0f;
+            // renormalised weights w / T and their derivatives by the quotient rule,
+            // (dw - (w / T) dT) / T (the identity when renormalisation is off)
+            const float* rn = s_rn[RN ? i : 0];
             for (int32_t r0 = dd.r_lo; r0 <= dd.r_hi; r0 += kTile) {
                 const int nr = min(kTile, dd.r_hi - r0 + 1);
                 for (int32_t k0 = dd.k_lo; k0 <= dd.k_hi; k0 += kTile) {
@@ -337,9 +412,16 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                                 m = -(eP[e + 1] - eP[e]);
                                 sg = -1.41421356237309505f * (eU[e + 1] - eU[e]);
                             }
-                            wp[e] = w;
-                            wpm[e] = m * isp;
-                            wps[e] = sg * isp;
+                            if (RN) {
+                                const float wn = w * rn[0];
+                                wp[e] = wn;
+                                wpm[e] = (m * isp - wn * rn[1]) * rn[0];
+                                wps[e] = (sg * isp - wn * rn[2]) * rn[0];
+                            } else {
+                                wp[e] = w;
+                                wpm[e] = m * isp;
+                                wps[e] = sg * isp;
+                            }
                         } else {
                             const int k = e - nr - koff, a = nr + 1 + k;
                             float w = 0.0f, m = 0.0f, sg = 0.0f;
@@ -352,9 +434,16 @@ k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, De
                                     w = 1.0f;
                                 }
                             }
-                            wt[e - nr] = w;
-                            wtm[e - nr] = m * ist;
-                            wts[e - nr] = sg * ist;
+                            if (RN) {
+                                const float wn = w * rn[3];
+                                wt[e - nr] = wn;
+                                wtm[e - nr] = (m * ist - wn * rn[4]) * rn[3];
+                                wts[e - nr] = (sg * ist - wn * rn[5]) * rn[3];
+                            } else {
+                                wt[e - nr] = w;
+                                wtm[e - nr] = m * ist;
+                                wts[e - nr] = sg * ist;
+                            }
                         }
                     }
                     __syncwarp(gmask);
@@ -497,7 +586,8 @@ cudaError_t launch_depo_adjoint(const RasterConsts& c, const DepoArrays& d, cons
 {
     if (d.n <= 0) return cudaSuccess;
     const int64_t blocks = (d.n + kDepos - 1) / kDepos;
-    k_depo_adjoint<<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, dgrid, g, flags);
+    if (c.renorm) k_depo_adjoint<true><<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, dgrid, g, flags);
+    else k_depo_adjoint<false><<<(unsigned)blocks, kWarps * 32, 0, s>>>(c, d, dgrid, g, flags);
     return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@ struct RasterConsts {
     int64_t n_rows;                         // n_wires * n_imp
     int32_t n_ticks;
     int32_t fluctuate;
+    int32_t renorm;                         // 1: each axis' weights divided by their window sum
     uint32_t key0, key1, plane_id;
     double DL, DT, v, tau;                  // FP64 parameters for the global gradients
     int32_t depos_per_block;                // rasterization CTA size: 32, 64 or 128 depos

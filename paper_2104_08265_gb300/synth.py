@@ -61,7 +61,7 @@ class DriftParams:
     fluctuate: int = 0
     seed: int = 0
     plane_id: int = 0
-    renormalize: int = 0     # 1: the truncated patch is rescaled to carry Q' exactly
+    renormalize: int = 0     # 1: each axis divided by its n-sigma window's mass (unclipped)
 
 
 @dataclasses.dataclass

@@ -44,7 +44,8 @@ class CParams(ctypes.Structure):
     _fields_ = [("v_mm_per_us", ctypes.c_double), ("DL_cm2_s", ctypes.c_double),
                 ("DT_cm2_s", ctypes.c_double), ("lifetime_us", ctypes.c_double),
                 ("nsigma", ctypes.c_double), ("fluctuate", ctypes.c_int32),
-                ("plane_id", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+                ("plane_id", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("renormalize", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class CDepos(ctypes.Structure):
@@ -136,7 +137,8 @@ def c_geometry(g: Geometry) -> CGeometry:
 def c_params(p: DriftParams) -> CParams:
     return CParams(float(p.v_mm_per_us), float(p.DL_cm2_s), float(p.DT_cm2_s),
                    float(p.lifetime_us), float(p.nsigma), int(p.fluctuate),
-                   int(p.plane_id) & 0xFFFFFFFF, int(p.seed) & 0xFFFFFFFFFFFFFFFF)
+                   int(p.plane_id) & 0xFFFFFFFF, int(p.seed) & 0xFFFFFFFFFFFFFFFF,
+                   int(getattr(p, "renormalize", 0)), 0)
 
 
 def _stream_handle(stream) -> int:

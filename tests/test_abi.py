@@ -53,8 +53,42 @@ def test_argument_checks_need_no_gpu(libpath):
                                 ctypes.byref(wcsim.c_params(p)), None, ctypes.byref(h)) == wcsim.ESHAPE
     assert L.wcsim_plane_create(ctypes.byref(wcsim.c_geometry(g)), ctypes.c_void_p(16), 4, 0,
                                 ctypes.byref(wcsim.c_params(p)), None, ctypes.byref(h)) == wcsim.ESHAPE
+    for field, val in (("renormalize", 2), ("reserved", 1)):
+        bp = wcsim.c_params(p); setattr(bp, field, val)
+        assert L.wcsim_plane_create(ctypes.byref(wcsim.c_geometry(g)), ctypes.c_void_p(16), 0, 0,
+                                    ctypes.byref(bp), None, ctypes.byref(h)) == wcsim.EINVAL
+        assert field.encode() in L.wcsim_last_error()
     assert L.wcsim_run(None, None, None, None) == wcsim.EINVAL
     assert L.wcsim_plane_destroy(None) == wcsim.OK
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (a C program
+    compiled against include/wcsim.h prints them)."""
+    import ctypes
+    from paper_2104_08265_gb300 import wcsim
+    mirrors = {"wcsim_geometry": wcsim.CGeometry, "wcsim_drift_params": wcsim.CParams,
+               "wcsim_depos": wcsim.CDepos, "wcsim_depo_grads": wcsim.CDepoGrads,
+               "wcsim_tune_report": wcsim.CTuneReport}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "wcsim.h"', 'int main(void) {']
+    for name, cls in mirrors.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, v = ln.split()
+        got[(a, b)] = int(v)
+    for name, cls in mirrors.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
 
 
 def test_product_path_never_touches_the_oracle():

@@ -386,8 +386,10 @@ def test_depo_grads_match_central_finite_differences():
     G = rng.normal(size=(g.n_wires, g.n_ticks))
     prm = S.DriftParams(DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0)
     checked = 0
-    for trial in range(6):
+    for trial in range(9):
         p = rng.uniform(8, 28); t = rng.uniform(5, 20); td = rng.uniform(20, 40); q = 5000.0
+        if trial >= 6:                                   # windows clipped by the grid border
+            p = rng.uniform(-0.3, 0.3); t = rng.uniform(-td - 0.5, -td + 0.5)
         d = one(p, t, td, q)
         w0 = O.windows(g, prm, d)[0]
         dS, _ = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G)
@@ -454,6 +456,46 @@ def test_renormalized_patch_carries_exactly_the_attenuated_charge():
         assert np.ptp(ratio) <= 1e-12 * ratio.max()
 
 
+def test_renormalization_ignores_the_grid_border():
+    """T is the mass of the n-sigma window before clipping: a depo straddling the border of a
+    small grid gets, on the bins they share, the patch it gets on a large grid that holds its
+    whole window (where it sums to Q'); the charge beyond the border is lost.  Dyadic
+    geometry and positions keep the bin decision identical on both grids."""
+    import dataclasses
+    small = S.Geometry(n_wires=8, n_imp=10, n_ticks=256, pitch_mm=2.5, tick_us=0.5)
+    big = S.Geometry(n_wires=16, n_imp=10, n_ticks=512, pitch_mm=2.5, tick_us=0.5,
+                     p0_mm=-10.0, t0_us=-32.0)
+    cases = [(0.53125, 40.25, 150.0, 3.0), (19.75, 0.375, 300.0, 3.0), (-0.25, -0.25, 80.0, 3.0),
+             (0.0, 60.0, 200.0, 1.0), (10.0, 127.75, 120.0, 2.0)]
+    for p, ta, td, ns in cases:                         # (p, arrival time, t_d, n_sigma)
+        prm = S.DriftParams(nsigma=ns, renormalize=1)
+        d = one(p, ta - td, td, 5000.0)
+        qatt = 5000.0 * np.exp(-td / prm.lifetime_us)
+        a, b = O.rasterize(small, prm, d), O.rasterize(big, prm, d)
+        assert b.sum() == pytest.approx(qatt, rel=1e-12)
+        # the small grid is rows 40..119, ticks 64..319 of the big one
+        sub = b[40:120, 64:320]
+        assert np.abs(a - sub).max() <= 1e-12 * b.max()
+        assert a.sum() < qatt * (1 - 1e-3)                   # the border cut some charge off
+        plain = O.rasterize(small, dataclasses.replace(prm, renormalize=0), d)
+        nz = plain > 0
+        ratio = a[nz] / plain[nz]
+        assert np.ptp(ratio) <= 1e-12 * ratio.max() and ratio.min() > 1.0
+
+
+def test_renormalization_of_a_deep_tail_window_stays_finite():
+    """A depo 20 sigma outside the grid with a 40-sigma window: the bins it reaches carry
+    its far-tail mass, tiny but finite (the window total holds the mean and cannot vanish)."""
+    g = S.Geometry(n_wires=4, n_imp=10, n_ticks=256, pitch_mm=3.0)
+    prm = S.DriftParams(nsigma=40.0, renormalize=1, DT_cm2_s=10.0)
+    sig_t = np.sqrt(2 * 4e-4 * 100.0) / 1.6
+    d = one(6.0, -20 * sig_t - 100.0, 100.0, 5000.0)
+    grid = O.rasterize(g, prm, d)
+    assert np.isfinite(grid).all() and 0.0 < grid.sum() < 1e-70
+    plain = O.rasterize(g, S.DriftParams(nsigma=40.0, DT_cm2_s=10.0), d)
+    assert grid.sum() == pytest.approx(plain.sum(), rel=1e-6)  # T ~ 1: almost no change
+
+
 def test_renormalized_grads_match_central_finite_differences():
     """The quotient-rule gradients of renormalized patches against FP64 finite differences
     (window frozen), in Q, p, t, D_L, D_T and tau."""
@@ -464,8 +506,10 @@ def test_renormalized_grads_match_central_finite_differences():
     G = rng.normal(size=(g.n_wires, g.n_ticks))
     prm = S.DriftParams(DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0, renormalize=1)
     checked = 0
-    for trial in range(6):
+    for trial in range(9):
         p = rng.uniform(8, 28); t = rng.uniform(5, 20); td = rng.uniform(20, 40); q = 5000.0
+        if trial >= 6:                                   # windows clipped by the grid border
+            p = rng.uniform(-0.3, 0.3); t = rng.uniform(-td - 0.5, -td + 0.5)
         d = one(p, t, td, q)
         w0 = O.windows(g, prm, d)[0]
         dS, _ = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G)
