@@ -71,9 +71,12 @@ typedef struct {
     int32_t fluctuate;   /* 1: per-bin charge fluctuation (Sec. 3.3.1, Table 1), 0: mean */
     uint32_t plane_id;   /* 4th Philox counter word */
     uint64_t seed;       /* Philox key (lo, hi words) */
-    int32_t renormalize; /* 1: each axis' weights divided by their sum over the truncated
-                            window, so that a patch carries Q' exactly (the reductions of
-                            the paper's Sec. 4 hint at it); 0: truncated tails are lost */
+    int32_t renormalize; /* 1: each axis' weights divided by their sum over the n-sigma
+                            window before it is clipped to the grid, so that a patch inside
+                            the grid carries Q' exactly and charge beyond the grid's border
+                            stays lost (the reductions of the paper's Sec. 4 hint at a
+                            normalisation); 0: the truncated tails are lost.  0 or 1, else
+                            WCSIM_EINVAL */
     int32_t reserved;    /* must be 0 */
 } wcsim_drift_params;
 
