@@ -12,6 +12,7 @@ only place besides the cpu_baseline leg where this script runs it).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -44,7 +45,8 @@ def parse():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-noise", action="store_true",
-                    help="skip the forwards timed with Eq. 1's noise on and with ADC readout")
+                    help="skip the forwards timed with Eq. 1's noise on, with ADC readout and "
+                         "with the rasterization variants")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-event batched run (wcsim_batch_run vs 64 wcsim_run calls)")
     ap.add_argument("--soak-s", type=float, default=0.5,
@@ -493,6 +495,20 @@ def run_gpu(args):
     tot_ms = max_over_ranks(sum(step_ms), ws, "cuda")
     assert plane.check_flags() == 0
 
+    def time_forward(call):
+        """Mean device time of `call` (one forward) over the timed steps, L2 flushed."""
+        for _ in range(args.warmup):
+            call()
+        ts_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        te_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ts_[i].record(stream)
+            call()
+            te_[i].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in zip(ts_, te_)) / args.steps
+
     # ---- the same forward with Eq. 1's noise on (a low-pass amplitude spectrum): the noise
     # is added while the inverse time FFT stages its input
     noise = None
@@ -500,17 +516,7 @@ def run_gpu(args):
         k = np.arange(g.n_ticks // 2 + 1)
         amp = (np.sqrt(g.n_ticks) / (1.0 + (k / (0.1 * g.n_ticks)) ** 2)).astype(np.float32)
         plane.set_noise(amp, seed=0x0015E)
-        for _ in range(args.warmup):
-            plane.run(dd, out=wave)
-        ns_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ne_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            ns_[i].record(stream)
-            plane.run(dd, out=wave)
-            ne_[i].record(stream)
-        torch.cuda.synchronize()
-        nms = sum(a.elapsed_time(b) for a, b in zip(ns_, ne_)) / args.steps
+        nms = time_forward(lambda: plane.run(dd, out=wave))
         plane.set_noise(None)
         noise = {"ms_per_step": nms, "depos_per_s": len(d) / (nms * 1e-3),
                  "model": "spectral noise per wire, A(k) = sqrt(n_t) / (1 + (k / 0.1 n_t)^2)"}
@@ -520,26 +526,28 @@ def run_gpu(args):
     if not args.no_noise:
         plane.set_digitizer(2.0, 2048.0, 12)
         codes = torch.empty((g.n_wires, g.n_ticks), dtype=torch.int16, device="cuda")
-        for _ in range(args.warmup):
-            plane.run_adc(dd, out=codes)
-        as_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ae_ = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            as_[i].record(stream)
-            plane.run_adc(dd, out=codes)
-            ae_[i].record(stream)
-        torch.cuda.synchronize()
-        ams = sum(a.elapsed_time(b) for a, b in zip(as_, ae_)) / args.steps
+        ams = time_forward(lambda: plane.run_adc(dd, out=codes))
         adc = {"ms_per_step": ams, "depos_per_s": len(d) / (ams * 1e-3),
                "digitizer": "gain 2, pedestal 2048, 12 bits"}
+
+    # ---- the rasterization variants: the exact binomial fluctuation and renormalised
+    # patches, each in the same forward
+    variants = {}
+    if not args.no_noise:
+        for name, prm_v in (("binomial_fluctuation", dataclasses.replace(prm, fluctuate=2)),
+                            ("renormalized", dataclasses.replace(prm, renormalize=1))):
+            plane.set_params(prm_v)
+            vms = time_forward(lambda: plane.run(dd, out=wave))
+            variants[name] = {"ms_per_step": vms, "depos_per_s": len(d) / (vms * 1e-3),
+                              "fluctuate": prm_v.fluctuate, "renormalize": prm_v.renormalize}
+        plane.set_params(prm)
+        assert plane.check_flags() == 0
 
     # ---- forward + backward (loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10,
     # lifetime 8 ms; the backward runs on the mean path and includes dL/dR)
     fb_ms = None
     bwd_stages = None
     if not args.no_backward:
-        import dataclasses
         tgt = dataclasses.replace(prm, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0, fluctuate=0)
         plane.set_params(tgt)
         m_target = plane.run(dd).clone()
@@ -687,6 +695,7 @@ def run_gpu(args):
         "batch64": batch,
         "with_noise": noise,
         "adc_readout": adc,
+        "rasterization_variants": variants or None,
         "autotune": tune,
         "clocks": clk,
     }

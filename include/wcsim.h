@@ -68,13 +68,17 @@ typedef struct {
     double DT_cm2_s;     /* transverse diffusion constant, >= 0 */
     double lifetime_us;  /* electron lifetime, > 0 (may be +inf) */
     double nsigma;       /* patch half-width in sigmas, > 0 */
-    int32_t fluctuate;   /* 1: per-bin charge fluctuation (Sec. 3.3.1, Table 1), 0: mean */
+    int32_t fluctuate;   /* per-bin charge fluctuation (Sec. 4.3.1, 4.3.2, Table 1): 0 the
+                            mean; 1 the normal approximation to Binomial(Q', mean / Q');
+                            2 the exact Binomial(rint Q', mean / Q') drawn by inversion of
+                            its CDF (bins whose variance exceeds 65536 electrons^2 take the
+                            normal approximation).  0, 1 or 2, else WCSIM_EINVAL */
     uint32_t plane_id;   /* 4th Philox counter word */
     uint64_t seed;       /* Philox key (lo, hi words) */
     int32_t renormalize; /* 1: each axis' weights divided by their sum over the n-sigma
                             window before it is clipped to the grid, so that a patch inside
                             the grid carries Q' exactly and charge beyond the grid's border
-                            stays lost (the reductions of the paper's Sec. 4 hint at a
+                            stays lost (the reductions of the paper's Sec. 4.3.2 hint at a
                             normalisation); 0: the truncated tails are lost.  0 or 1, else
                             WCSIM_EINVAL */
     int32_t reserved;    /* must be 0 */

@@ -83,6 +83,10 @@ def _load():
             lib.og_normal.restype = d
             lib.og_bin_normal.argtypes = [i64, i64, u32, u32, P(u32)]
             lib.og_bin_normal.restype = d
+            lib.og_bin_uniform.argtypes = [i64, i64, u32, u32, P(u32)]
+            lib.og_bin_uniform.restype = d
+            lib.og_binomial_draw.argtypes = [i64, d, d]
+            lib.og_binomial_draw.restype = i64
             lib.og_noise_spectrum.argtypes = [ctypes.c_int32, ctypes.c_int32, u32, P(u32),
                                               P(d), P(d)]
             lib.og_noise_spectrum.restype = None
@@ -147,6 +151,18 @@ def bin_normal(r: int, k: int, depo_id: int, plane_id: int, seed: int) -> float:
     key = (ctypes.c_uint32 * 2)(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
     return float(_load().og_bin_normal(int(r), int(k), int(depo_id) & 0xFFFFFFFF,
                                        int(plane_id) & 0xFFFFFFFF, key))
+
+
+def bin_uniform(r: int, k: int, depo_id: int, plane_id: int, seed: int) -> float:
+    """The uniform (23 bits) that draws the exact binomial of bin (row r, tick k) of a depo."""
+    key = (ctypes.c_uint32 * 2)(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    return float(_load().og_bin_uniform(int(r), int(k), int(depo_id) & 0xFFFFFFFF,
+                                        int(plane_id) & 0xFFFFFFFF, key))
+
+
+def binomial_draw(n: int, p: float, u: float) -> int:
+    """Binomial(n, p) by inversion of its CDF at u (the smallest k with u < F(k))."""
+    return int(_load().og_binomial_draw(int(n), float(p), float(u)))
 
 
 # --------------------------------------------------------------------------- a1-a3

@@ -6,7 +6,7 @@
  * test suite, the smoke check and the benchmark's CPU-baseline leg may load it.
  *
  * What it computes (paper Sec. 2.1.1: "rasterization" and "scatter adding"; Fig. 2: drift
- * and diffusion of the electron clouds; Sec. 3.3.1 and Table 1: fluctuation with a
+ * and diffusion of the electron clouds; Sec. 4.3.1 and Table 1: fluctuation with a
  * Box-Muller normal):
  *
  *   a1  drift:      t_a = t + t_d,  Q' = Q exp(-t_d / tau),
@@ -15,7 +15,9 @@
  *                   weight w_k = Phi((e_{k+1}-mu)/sigma) - Phi((e_k-mu)/sigma); patch =
  *                   Q' w^p (x) w^t
  *   a2f fluctuate:  x_b = max(0, mu_b + sqrt(mu_b (1 - mu_b/Q')) z_b), z_b standard normal
- *                   from Philox4x32-10 (Salmon et al., SC'11) and Box-Muller
+ *                   from Philox4x32-10 (Salmon et al., SC'11) and Box-Muller (fluctuate 1);
+ *                   or x_b ~ Binomial(N, p_b) exactly (fluctuate 2), N = Q' in whole
+ *                   electrons, p_b = mu_b / Q', drawn by inversion of its CDF
  *   a3  scatter:    S[r][k] += x_b, in depo order, in double precision
  *   a7  adjoint:    per-depo gradients of L given dL/dS, with the window held fixed
  *
@@ -34,7 +36,13 @@
  *     pairs, u = (x + 0.5) 2^-32, giving four normals
  *       z0 = sqrt(-2 ln u0) cos(2 pi u1),  z1 = sqrt(-2 ln u0) sin(2 pi u1),
  *       z2 = sqrt(-2 ln u2) cos(2 pi u3),  z3 = sqrt(-2 ln u2) sin(2 pi u3);
- *     bin (r, k) takes z_(k mod 4).
+ *     bin (r, k) takes z_(k mod 4);
+ *   - the exact binomial (fluctuate 2; the paper's CPU reference draws from a binomial, Sec.
+ *     4.3.2) takes from the same block the uniform u = (floor(x / 2^9) + 0.5) 2^-23 of word
+ *     k mod 4 and returns the smallest k with u < F(k; N, p_b), F the binomial CDF.  N is
+ *     rint(Q') with Q' formed in FP32 as the kernel forms it (an integer decision taken in
+ *     the kernel's precision).  Above N p (1 - p) = 65536 or N = 2^24 the normal
+ *     approximation above is used instead;
  *
  * Build: cc -O2 -ffp-contract=off -fPIC -shared wcsim_oracle.c -lm
  * (no FMA contraction: the bin decision must be evaluated operation by operation).
@@ -105,6 +113,32 @@ double og_bin_normal(int64_t r, int64_t k, uint32_t id, uint32_t plane_id, const
     return (m < 2) ? og_normal(x[0], x[1], m) : og_normal(x[2], x[3], m - 2);
 }
 
+/* The uniform of bin (row r, tick k) for the exact binomial: word k mod 4 of the same block,
+ * its top 23 bits, (floor(x / 2^9) + 0.5) 2^-23 (exact in FP32 and FP64). */
+double og_bin_uniform(int64_t r, int64_t k, uint32_t id, uint32_t plane_id, const uint32_t key[2])
+{
+    uint32_t ctr[4] = {(uint32_t)(k >> 2), (uint32_t)r, id, plane_id};
+    uint32_t x[4];
+    og_philox4x32_10(ctr, key, x);
+    return ((double)(x[k & 3] >> 9) + 0.5) / 8388608.0;
+}
+
+/* Binomial(n, p) drawn by inversion: the smallest k with u < F(k) = sum_{j <= k} P(j),
+ * P(j) = C(n, j) p^j (1 - p)^(n - j) evaluated through lgamma, summed from j = 0. */
+int64_t og_binomial_draw(int64_t n, double p, double u)
+{
+    if (n <= 0 || !(p > 0.0)) return 0;
+    if (p >= 1.0) return n;
+    const double lnf = lgamma((double)n + 1.0), lp = log(p), lq = log1p(-p);
+    double F = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        F += exp(lnf - lgamma((double)j + 1.0) - lgamma((double)(n - j) + 1.0) +
+                 (double)j * lp + (double)(n - j) * lq);
+        if (u < F) return j;
+    }
+    return n;
+}
+
 /* ---- noise (Eq. 1's additive term N(t, x); the paper gives no model, the readings are):
  *   per wire w, the noise is the normalised inverse DFT over n_ft points of A(k) xi_w(k),
  *   with A the plane's amplitude spectrum (k < n_ft/2 + 1, extended as A(n_ft - k) = A(k))
@@ -140,6 +174,7 @@ void og_noise_spectrum(int32_t n_w, int32_t n_ft, uint32_t plane_id, const uint3
 typedef struct {
     double inv_dp, inv_dt;          /* 1/(pitch/n_imp), 1/tick, FP64 */
     float two_dt_f, two_dl_f, inv_v_f, nsig_f, inv_dp_f, inv_dt_f;
+    float inv_tau_f;                /* 1/lifetime, FP32 (the binomial's trial count) */
 } og_consts;
 
 static og_consts make_consts(const og_geom* g, const og_params* pr)
@@ -154,6 +189,7 @@ static og_consts make_consts(const og_geom* g, const og_params* pr)
     c.nsig_f = (float)pr->nsigma;
     c.inv_dp_f = (float)c.inv_dp;
     c.inv_dt_f = (float)c.inv_dt;
+    c.inv_tau_f = (float)(1.0 / pr->lifetime_us);
     return c;
 }
 
@@ -380,12 +416,23 @@ int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double*
         axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
         if (pr->renormalize && renormalize_depo(g, &d, wp, wt, NULL, NULL, NULL, NULL))
             return -1;
+        /* the exact binomial's trial count: Q' rounded to whole electrons, Q' formed in
+         * FP32 as the kernel forms it */
+        const float qf = q[i] * expf(-(float)td[i] * c.inv_tau_f);
+        const double n_e = rint((double)qf);
         for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
             double* row = grid + r * nt;
             for (int64_t k = d.k_lo; k <= d.k_hi; ++k) {
                 double mean = d.qatt * wp[r - d.r_lo] * wt[k - d.k_lo];
                 double val = mean;
-                if (pr->fluctuate) {
+                double pb = wp[r - d.r_lo] * wt[k - d.k_lo];   /* mu_b / Q' */
+                if (pb > 1.0) pb = 1.0;
+                if (pr->fluctuate == 2 && n_e * pb * (1.0 - pb) <= 65536.0 && n_e <= 16777216.0) {
+                    if (mean > 0.0) {
+                        double u = og_bin_uniform(r, k, id[i], pr->plane_id, key);
+                        val = (double)og_binomial_draw((int64_t)n_e, pb, u);
+                    }
+                } else if (pr->fluctuate) {
                     /* normal approximation to Binomial(Q', mean/Q') */
                     double z = og_bin_normal(r, k, id[i], pr->plane_id, key);
                     double var = mean * (1.0 - mean / d.qatt);

@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -121,7 +122,8 @@ wcsim_status check_params(const wcsim_drift_params* p)
         return fail(WCSIM_EINVAL, "DL_cm2_s and DT_cm2_s must be finite and >= 0");
     if (!(p->lifetime_us > 0.0)) return fail(WCSIM_EINVAL, "lifetime_us must be > 0");
     if (!finite_pos(p->nsigma)) return fail(WCSIM_EINVAL, "nsigma must be finite and > 0");
-    if (p->fluctuate != 0 && p->fluctuate != 1) return fail(WCSIM_EINVAL, "fluctuate must be 0 or 1");
+    if (p->fluctuate < 0 || p->fluctuate > 2)
+        return fail(WCSIM_EINVAL, "fluctuate must be 0, 1 or 2");
     if (p->renormalize != 0 && p->renormalize != 1)
         return fail(WCSIM_EINVAL, "renormalize must be 0 or 1");
     if (p->reserved != 0) return fail(WCSIM_EINVAL, "reserved must be 0");
@@ -172,6 +174,11 @@ RasterConsts make_consts(const wcsim_plane* pl)
     c.DT = p.DT_cm2_s;
     c.v = p.v_mm_per_us;
     c.tau = p.lifetime_us;
+    // Stirling's remainder for the exact binomial's small counts, from log-gamma in FP64
+    c.stirl[0] = 0.0f;
+    for (int m = 1; m < 16; ++m)
+        c.stirl[m] = (float)(std::lgamma(m + 1.0) -
+                             ((m + 0.5) * std::log((double)m) - m + 0.5 * std::log(6.283185307179586477)));
     return c;
 }
 

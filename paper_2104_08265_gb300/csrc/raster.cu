@@ -1,6 +1,6 @@
 // Drift, rasterization, fluctuation and scatter-add of depos into the impact x tick grid
 // (Sec. 2.1.1 "rasterization" and "scatter adding"; drift and diffusion as in Fig. 2;
-// fluctuation with a Box-Muller normal as in Sec. 3.3.1).
+// fluctuation with a Box-Muller normal as in Sec. 4.3.1).
 //
 // Work split.  A block of 8 warps owns KD consecutive depos (32 by default; 64 or 128 when
 // the autotuner finds them faster; the adjoint uses 64).  Threads 0..KD-1 take the FP64 bin
@@ -17,6 +17,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "binomial.cuh"
 #include "rng.cuh"
 #include "wcsim_internal.cuh"
 
@@ -147,13 +148,49 @@ __device__ __forceinline__ float bin_mass(int64_t koff, float frac, float s, flo
     return span_mass(ua, ub, ea, eb);
 }
 
+// Exact binomial fluctuation of the four bins of one 4-tick group: x_b ~ Binomial(N, p_b)
+// with N = rint(Q') whole electrons and p_b = mean_b / Q', drawn by inversion at the 23-bit
+// uniform of word k mod 4 of the bin's Philox block (the block the normal approximation
+// uses).  Bins whose variance N p (1 - p) exceeds 65536, or N above 2^24, take the normal
+// approximation instead; zero-mean bins stay zero.
+__device__ __forceinline__ void fluctuate_binomial(const RasterConsts& c, const Decision& dd, int kq4,
+                                                int64_t r, float inv_q, const float* stirl, float* v)
+{
+    const uint4 x = philox(make_uint4((uint32_t)kq4, (uint32_t)r, dd.id, c.plane_id), c.key0, c.key1);
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+    const float n = rintf(dd.qatt);
+    float z[4];
+    bool normals = false;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (!(v[e] > 0.0f)) continue;
+        const float p = fminf(1.0f, v[e] * inv_q);
+        if (n > 16777216.0f || n * p * (1.0f - p) > 65536.0f) {
+            if (!normals) {
+                box_muller4(x, z);
+                normals = true;
+            }
+            const float var = v[e] * (1.0f - v[e] * inv_q);
+            v[e] = fmaxf(0.0f, fmaf(sqrt_fast(var), z[e], v[e]));
+        } else if (n == 0.0f) {
+            v[e] = 0.0f;
+        } else if (p >= 1.0f) {
+            v[e] = n;
+        } else {
+            v[e] = binomial_inverse(n, p, uniform23(w[e]), stirl);
+        }
+    }
+}
+
 // Lanes per depo group: 8 lanes take one depo, so that the four groups of a warp work on
 // four depos side by side (a patch of ~17 rows x 3 four-tick groups, ~47 items, fills six
 // rounds of 8 lanes better than two rounds of 32).
 constexpr int kGroup = 8;
 
-// The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps.
-template <int KD>
+// The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps.  BIN: the
+// exact binomial fluctuation (an instance of its own, so that the other modes keep their
+// registers).
+template <int KD, bool BIN>
 __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const DepoArrays& d,
                                                 float* __restrict__ grid, int* flags, int64_t blk)
 {
@@ -165,6 +202,11 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     // outside the window), so that an item reads its four weights with one 16-byte load
     __shared__ __align__(16) float s_wt[NG][kWmax + 8];
     __shared__ float s_edge[NG][2 * (kWmax + 1)];        // row edges, then tick edges
+    __shared__ float s_stirl[BIN ? 16 : 1];              // the binomial's small-count table
+    if (BIN && threadIdx.x == 0) {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) s_stirl[m] = c.stirl[m];    // constant indices: no local copy
+    }
     const int gl = threadIdx.x % G, grp = threadIdx.x / G;
     // the lanes of this group within its warp
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
@@ -235,7 +277,7 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                     const float w = wp[ir];
                     const float4 t4 = reinterpret_cast<const float4*>(wt)[iq];
                     float v[4] = {w * t4.x, w * t4.y, w * t4.z, w * t4.w};
-                    if (c.fluctuate) {
+                    if (c.fluctuate == 1) {
                         // normal approximation to Binomial(Q', mean / Q'); zero-mean bins
                         // (outside the window) stay zero
                         float z[4];
@@ -246,6 +288,8 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                             const float var = v[e] * (1.0f - v[e] * inv_q);
                             v[e] = fmaxf(0.0f, fmaf(sqrt_fast(var), z[e], v[e]));
                         }
+                    } else if (BIN) {
+                        fluctuate_binomial(c, dd, q_lo + iq, r, inv_q, s_stirl, v);
                     }
                     float* dst = grid + r * c.n_ticks + kq;
                     if (vec4) {
@@ -264,15 +308,15 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     }
 }
 
-template <int KD>
+template <int KD, bool BIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
 {
-    rasterize_block<KD>(c, d, grid, flags, blockIdx.x);
+    rasterize_block<KD, BIN>(c, d, grid, flags, blockIdx.x);
 }
 
 // Several events of one plane: CTA b belongs to the event whose block range holds b.
-template <int KD>
+template <int KD, bool BIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
 {
@@ -280,7 +324,7 @@ k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
     while (e + 1 < ev.n && ev.block_start[e + 1] <= (int)blockIdx.x) ++e;
     c.key0 = ev.key0[e];
     c.key1 = ev.key1[e];
-    rasterize_block<KD>(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
+    rasterize_block<KD, BIN>(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
 }
 
 // Sum over the G lanes of a lane group (mask: the group's lanes), in every lane of it.
@@ -554,10 +598,18 @@ cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* 
 {
     if (d.n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)rasterize_blocks(d.n, c.depos_per_block);
+    if (c.fluctuate == 2) {
+        switch (c.depos_per_block) {
+            case 32: k_rasterize<32, true><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+            case 128: k_rasterize<128, true><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+            default: k_rasterize<64, true><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+        }
+        return cudaGetLastError();
+    }
     switch (c.depos_per_block) {
-        case 32: k_rasterize<32><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-        case 128: k_rasterize<128><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-        default: k_rasterize<64><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+        case 32: k_rasterize<32, false><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+        case 128: k_rasterize<128, false><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
+        default: k_rasterize<64, false><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
     }
     return cudaGetLastError();
 }
@@ -573,10 +625,18 @@ cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev,
 {
     const int blocks = ev.block_start[ev.n];
     if (blocks <= 0) return cudaSuccess;
+    if (c.fluctuate == 2) {
+        switch (c.depos_per_block) {
+            case 32: k_rasterize_batch<32, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+            case 128: k_rasterize_batch<128, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+            default: k_rasterize_batch<64, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+        }
+        return cudaGetLastError();
+    }
     switch (c.depos_per_block) {
-        case 32: k_rasterize_batch<32><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-        case 128: k_rasterize_batch<128><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-        default: k_rasterize_batch<64><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+        case 32: k_rasterize_batch<32, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+        case 128: k_rasterize_batch<128, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
+        default: k_rasterize_batch<64, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
     }
     return cudaGetLastError();
 }

@@ -25,6 +25,8 @@ struct RasterConsts {
     uint32_t key0, key1, plane_id;
     double DL, DT, v, tau;                  // FP64 parameters for the global gradients
     int32_t depos_per_block;                // rasterization CTA size: 32, 64 or 128 depos
+    float stirl[16];                        // Stirling's remainder log m! - [(m + 1/2) log m
+                                            // - m + 1/2 log 2 pi], m = 0..15 (exact binomial)
 };
 
 struct DepoGrads {

@@ -6,7 +6,7 @@ R(omega_t, omega_x) of Eq. 2.  It holds none of the simulation arithmetic (no dr
 diffusion, no rasterization, no convolution); both the CUDA path and the FP64 oracle take
 what it produces as plain arrays.
 
-The paper's inputs (CORSIKA + Geant4 cosmic-ray depos produced with LArSoft, Sec. 3.3.2) are
+The paper's inputs (CORSIKA + Geant4 cosmic-ray depos produced with LArSoft, Sec. 4.3.2) are
 not available, so tracks of the same shape stand in for them:
 
 * depos lie on straight tracks, ordered along each track;
@@ -58,7 +58,7 @@ class DriftParams:
     DT_cm2_s: float = 8.8
     lifetime_us: float = 10000.0
     nsigma: float = 3.0
-    fluctuate: int = 0
+    fluctuate: int = 0       # 0 mean, 1 normal approximation, 2 exact binomial
     seed: int = 0
     plane_id: int = 0
     renormalize: int = 0     # 1: each axis divided by its n-sigma window's mass (unclipped)

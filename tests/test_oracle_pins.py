@@ -340,6 +340,97 @@ def test_fluctuation_keyed_by_depo_id_and_plane():
     assert not np.array_equal(a, b) and not np.array_equal(a, c)
 
 
+# ------------------------------------------------------------------ a2f: exact binomial
+def test_binomial_draw_is_the_exact_quantile_on_tiny_cases():
+    """Brute force in exact rationals: for n <= 12 and rational p, the draw at u is the
+    smallest k with u < F(k), F summed from the binomial coefficients."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    for n in (1, 2, 5, 12):
+        for p in (Fraction(1, 7), Fraction(1, 2), Fraction(5, 6)):
+            cdf, acc = [], Fraction(0)
+            for k in range(n + 1):
+                acc += math.comb(n, k) * p ** k * (1 - p) ** (n - k)
+                cdf.append(acc)
+            for u in rng.uniform(0, 1, 60):
+                want = next(k for k in range(n + 1) if Fraction(u) < cdf[k])
+                assert O.binomial_draw(n, float(p), float(u)) == want, (n, p, u)
+
+
+def test_binomial_draw_matches_the_library_quantile():
+    """Larger n against scipy's binomial quantile (smallest k with F(k) >= u)."""
+    from scipy import stats
+    rng = np.random.default_rng(6)
+    for n, p in ((40, 0.3), (500, 0.02), (6000, 0.011), (6000, 0.25), (20000, 0.5)):
+        for u in rng.uniform(0, 1, 40):
+            assert O.binomial_draw(n, p, u) == int(stats.binom.ppf(u, n, p)), (n, p, u)
+    assert O.binomial_draw(0, 0.3, 0.5) == 0 and O.binomial_draw(9, 0.0, 0.99) == 0
+    assert O.binomial_draw(9, 1.0, 0.01) == 9
+
+
+def test_binomial_uniforms_are_uniform_and_keyed_like_the_normals():
+    from scipy import stats
+    u = np.array([O.bin_uniform(r, k, 7, 1, 0x5EED) for r in range(40) for k in range(50)])
+    assert np.all((u > 0) & (u < 1))
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    # the top 23 bits of the word the normal of the same bin pairs from
+    x = O.philox4x32_10((5, 3, 11, 2), (0x5EED0001, 0))
+    for k in range(20, 24):
+        assert O.bin_uniform(3, k, 11, 2, 0x5EED0001) * 2 ** 23 == (x[k % 4] >> 9) + 0.5
+
+
+def test_exact_binomial_fluctuation_statistics():
+    """fluctuate = 2: integer counts with mean N p_b and variance N p_b (1 - p_b), and on a
+    low-mean bin the distribution of the counts is the binomial pmf (chi-square)."""
+    from scipy import stats
+    g = S.Geometry(n_wires=2, n_imp=10, n_ticks=32, pitch_mm=3.0)
+    p, t, td, q = 3.05, -50.0, 60.0, 2000.0
+    base = S.DriftParams(fluctuate=0)
+    mean = O.rasterize(g, base, one(p, t, td, q))
+    qa = O.depo_weights(g, base, p, t, td, q)[0]
+    n_e = round(qa)
+    pb = mean / qa
+    n = 400
+    draws = np.stack([O.rasterize(g, S.DriftParams(fluctuate=2, seed=s), one(p, t, td, q))
+                      for s in range(n)])
+    assert np.array_equal(draws, np.round(draws))
+    live = mean > 0
+    assert np.all(draws[:, ~live] == 0)
+    m, v = draws.mean(0), draws.var(0)
+    var = n_e * pb * (1 - pb)
+    big = mean > 5.0
+    assert big.sum() >= 10
+    z = (m[big] - n_e * pb[big]) / np.sqrt(var[big] / n)
+    assert np.abs(z).max() < 4.5
+    assert np.abs(v[big] / var[big] - 1).max() < 5.0 * math.sqrt(2 / n)
+    # one bin with mean ~ 3: histogram against the pmf
+    b = np.unravel_index(np.argmin(np.abs(mean - 3.0)), mean.shape)
+    x = draws[(slice(None),) + b].astype(int)
+    ks = np.arange(0, 9)
+    pmf = stats.binom.pmf(ks, n_e, pb[b])
+    obs = np.array([(x == k).sum() for k in ks[:-1]] + [(x >= ks[-1]).sum()])
+    exp_ = n * np.append(pmf[:-1], 1 - pmf[:-1].sum())
+    chi2 = ((obs - exp_) ** 2 / exp_).sum()
+    assert stats.chi2.sf(chi2, len(ks) - 1) > 1e-3
+
+
+def test_exact_binomial_hands_large_variances_to_the_normal_approximation():
+    """Bins with N p (1 - p) > 65536 take the normal approximation's value; the others are
+    integer counts."""
+    g = S.Geometry(n_wires=2, n_imp=10, n_ticks=32, pitch_mm=3.0)
+    d = one(3.05, -50.0, 60.0, 3.0e6)
+    base = S.DriftParams(fluctuate=0)
+    mean = O.rasterize(g, base, d)
+    qa = O.depo_weights(g, base, 3.05, -50.0, 60.0, 3.0e6)[0]
+    pb = mean / qa
+    wide = round(qa) * pb * (1 - pb) > 65536
+    assert wide.sum() >= 3 and (~wide & (mean > 0)).sum() >= 3
+    ex = O.rasterize(g, S.DriftParams(fluctuate=2, seed=4), d)
+    na = O.rasterize(g, S.DriftParams(fluctuate=1, seed=4), d)
+    assert np.array_equal(ex[wide], na[wide])
+    assert np.array_equal(ex[~wide], np.round(ex[~wide]))
+
+
 # ------------------------------------------------------------------ a7: adjoint
 def test_convolve_adjoint_dot_product_identity():
     """<G, conv(S)> = <dS, S> for the adjoint dS (any real S, G)."""
