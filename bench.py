@@ -199,7 +199,7 @@ def write_traffic(reps):
                      "from ncu --set full captures of the 960-wire x 6000-tick plane with 100k "
                      "depos; valid only while the CUDA sources hash to source_sha256.",
            "capture": ("CMD='python bench.py --steps 2 --warmup 1 --no-autotune --no-batch "
-                       "--no-cpu-baseline --no-cufft --no-e2e --soak-s 0'; ncu --set full "
+                       "--no-cpu-baseline --no-cufft --no-e2e --no-noise --soak-s 0'; ncu --set full "
                        "--import-source no --clock-control none -k 'regex:k_rasterize|"
                        "k_rows_r2c_direct|k_wire_warp|k_rows_c2r' -s 4 -c 4 -o fwd $CMD; ncu --set "
                        "full --import-source no --clock-control none -k 'regex:k_wire_adjoint|"
