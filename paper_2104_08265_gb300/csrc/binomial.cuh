@@ -86,7 +86,7 @@ __device__ __forceinline__ float binomial_step(bool up, float k, float f, int j,
 // n p q (the caller hands larger variances to the normal approximation).  F at the mode
 // m = floor((n + 1) p) is summed (compensated) downwards from P(m); the walk then goes down
 // while u lies below F(k - 1), or up adding P(k + 1), until u < F(k).  Every loop ends
-// within a few standard deviations of the mode (the terms fall below 2^-36 and u >= 2^-24),
+// within a few standard deviations of the mode, where the terms fall below 2^-36 (u >= 2^-24),
 // and the loop counters bound them by n in any case.
 __device__ __noinline__ float binomial_inverse(float n, float p, float u, const float* tab)
 {
@@ -107,8 +107,9 @@ __device__ __noinline__ float binomial_inverse(float n, float p, float u, const 
     f = fm;
     j = 0;
     if (u < C) {
+        // (a u below the rounding residue of the sum, ~1e-7, stops where the terms vanish)
 #pragma unroll 1
-        while (k > 0.0f) {
+        while (k > 0.0f && f >= kBinomTiny) {
             const float c = C - f;
             if (!(u < c)) break;
             C = c;

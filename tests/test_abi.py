@@ -53,7 +53,7 @@ def test_argument_checks_need_no_gpu(libpath):
                                 ctypes.byref(wcsim.c_params(p)), None, ctypes.byref(h)) == wcsim.ESHAPE
     assert L.wcsim_plane_create(ctypes.byref(wcsim.c_geometry(g)), ctypes.c_void_p(16), 4, 0,
                                 ctypes.byref(wcsim.c_params(p)), None, ctypes.byref(h)) == wcsim.ESHAPE
-    for field, val in (("renormalize", 2), ("reserved", 1)):
+    for field, val in (("renormalize", 2), ("reserved", 1), ("fluctuate", 3), ("fluctuate", -1)):
         bp = wcsim.c_params(p); setattr(bp, field, val)
         assert L.wcsim_plane_create(ctypes.byref(wcsim.c_geometry(g)), ctypes.c_void_p(16), 0, 0,
                                     ctypes.byref(bp), None, ctypes.byref(h)) == wcsim.EINVAL
