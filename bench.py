@@ -18,6 +18,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -239,7 +240,9 @@ def peaks():
 class Clocks:
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % os.getpid())
+        # the raw samples (summarised in the JSON line); WCSIM_CLOCKS_DIR keeps them elsewhere
+        out_dir = os.environ.get("WCSIM_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, "bench_clocks_%d.csv" % os.getpid())
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
