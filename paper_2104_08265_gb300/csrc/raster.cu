@@ -148,38 +148,30 @@ __device__ __forceinline__ float bin_mass(int64_t koff, float frac, float s, flo
     return span_mass(ua, ub, ea, eb);
 }
 
-// Exact binomial fluctuation of the four bins of one 4-tick group: x_b ~ Binomial(N, p_b)
-// with N = rint(Q') whole electrons and p_b = mean_b / Q', drawn by inversion at the 23-bit
-// uniform of word k mod 4 of the bin's Philox block (the block the normal approximation
-// uses).  Bins whose variance N p (1 - p) exceeds 65536, or N above 2^24, take the normal
-// approximation instead; zero-mean bins stay zero.
-__device__ __forceinline__ void fluctuate_binomial(const RasterConsts& c, const Decision& dd, int kq4,
-                                                int64_t r, float inv_q, const float* stirl, float* v)
+// Exact binomial fluctuation of the bin (row r, tick k) with mean v: x ~ Binomial(N, p) with
+// N = rint(Q') whole electrons and p = v / Q', drawn by inversion at the 23-bit uniform of
+// word k mod 4 of the bin's Philox block (the block the normal approximation uses).  A bin
+// whose variance N p (1 - p) exceeds 65536, or N above 2^24, takes the normal
+// approximation instead.
+__device__ __forceinline__ float binomial_bin(const RasterConsts& c, const Decision& dd, int k,
+                                              int64_t r, float v, float inv_q, const float* stirl)
 {
-    const uint4 x = philox(make_uint4((uint32_t)kq4, (uint32_t)r, dd.id, c.plane_id), c.key0, c.key1);
-    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+    const uint4 x = philox(make_uint4((uint32_t)(k >> 2), (uint32_t)r, dd.id, c.plane_id),
+                           c.key0, c.key1);
+    const int e = k & 3;
     const float n = rintf(dd.qatt);
-    float z[4];
-    bool normals = false;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        if (!(v[e] > 0.0f)) continue;
-        const float p = fminf(1.0f, v[e] * inv_q);
-        if (n > 16777216.0f || n * p * (1.0f - p) > 65536.0f) {
-            if (!normals) {
-                box_muller4(x, z);
-                normals = true;
-            }
-            const float var = v[e] * (1.0f - v[e] * inv_q);
-            v[e] = fmaxf(0.0f, fmaf(sqrt_fast(var), z[e], v[e]));
-        } else if (n == 0.0f) {
-            v[e] = 0.0f;
-        } else if (p >= 1.0f) {
-            v[e] = n;
-        } else {
-            v[e] = binomial_inverse(n, p, uniform23(w[e]), stirl);
-        }
+    const float p = fminf(1.0f, v * inv_q);
+    if (n > 16777216.0f || n * p * (1.0f - p) > 65536.0f) {
+        float z[4];
+        box_muller4(x, z);
+        const float ze = e == 0 ? z[0] : e == 1 ? z[1] : e == 2 ? z[2] : z[3];
+        const float var = v * (1.0f - v * inv_q);
+        return fmaxf(0.0f, fmaf(sqrt_fast(var), ze, v));
     }
+    if (n == 0.0f) return 0.0f;
+    if (p >= 1.0f) return n;
+    const uint32_t w = e == 0 ? x.x : e == 1 ? x.y : e == 2 ? x.z : x.w;
+    return binomial_inverse(n, p, uniform23(w), stirl);
 }
 
 // Lanes per depo group: 8 lanes take one depo, so that the four groups of a warp work on
@@ -268,6 +260,22 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                     }
                 }
                 __syncwarp(gmask);
+                if constexpr (BIN) {
+                    // one bin per lane: neighbouring ticks cost alike, so the group's lanes
+                    // walk their CDFs side by side, and no lane chains four draws
+                    const float inv_nt = 1.0f / (float)nt;
+                    for (int b = gl; b < nr * nt; b += G) {
+                        const int ir = (int)(((float)b + 0.5f) * inv_nt);
+                        const int ik = b - ir * nt;
+                        const int64_t r = r0 + ir;
+                        const float v = wp[ir] * wt[ik + koff];
+                        if (!(v > 0.0f)) continue;
+                        atomicAdd(grid + r * c.n_ticks + (k0 + ik),
+                                  binomial_bin(c, dd, k0 + ik, r, v, inv_q, s_stirl));
+                    }
+                    __syncwarp(gmask);
+                    continue;
+                }
                 const float inv_nq = 1.0f / (float)nq;
                 for (int item = gl; item < nr * nq; item += G) {
                     const int ir = (int)(((float)item + 0.5f) * inv_nq);
@@ -288,8 +296,6 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
                             const float var = v[e] * (1.0f - v[e] * inv_q);
                             v[e] = fmaxf(0.0f, fmaf(sqrt_fast(var), z[e], v[e]));
                         }
-                    } else if (BIN) {
-                        fluctuate_binomial(c, dd, q_lo + iq, r, inv_q, s_stirl, v);
                     }
                     float* dst = grid + r * c.n_ticks + kq;
                     if (vec4) {
