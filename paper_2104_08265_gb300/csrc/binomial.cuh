@@ -17,8 +17,8 @@
 namespace wcsim {
 
 // Terms of the CDF below this are dropped from the sum at the mode (the uniforms have 23
-// bits, the smallest is 2^-24).
-constexpr float kBinomTiny = 1.4551915e-11f;   // 2^-36
+// bits, the smallest is 2^-24; the dropped tail stays below 1e-8).
+constexpr float kBinomTiny = 2.3283064e-10f;   // 2^-32
 
 // Stirling's remainder d(m) for whole m >= 1: a table (made on the host from log-gamma in
 // FP64) up to 15, the asymptotic series 1/(12 m) - 1/(360 m^3) + 1/(1260 m^5) above
@@ -73,12 +73,12 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x)
 }
 
 // P(k - 1) (down) or P(k + 1) (up) from P(k) = f by the ratio recurrence, re-anchored on the
-// saddle-point form every 16th step (step counter j) so that rounding does not build up
+// saddle-point form every 32nd step (step counter j) so that rounding does not build up
 // along a wide distribution.
 __device__ __forceinline__ float binomial_step(bool up, float k, float f, int j, float n, float p,
                                                float q, float qp, float pq, const float* tab)
 {
-    if ((j & 15) == 0) return binomial_pmf(up ? k + 1.0f : k - 1.0f, n, p, q, tab);
+    if ((j & 31) == 0) return binomial_pmf(up ? k + 1.0f : k - 1.0f, n, p, q, tab);
     return up ? f * __fdividef((n - k) * pq, k + 1.0f) : f * __fdividef(k * qp, n - k + 1.0f);
 }
 
@@ -86,7 +86,7 @@ __device__ __forceinline__ float binomial_step(bool up, float k, float f, int j,
 // n p q (the caller hands larger variances to the normal approximation).  F at the mode
 // m = floor((n + 1) p) is summed (compensated) downwards from P(m); the walk then goes down
 // while u lies below F(k - 1), or up adding P(k + 1), until u < F(k).  Every loop ends
-// within a few standard deviations of the mode, where the terms fall below 2^-36 (u >= 2^-24),
+// within a few standard deviations of the mode, where the terms fall below 2^-32 (u >= 2^-24),
 // and the loop counters bound them by n in any case.
 __device__ __noinline__ float binomial_inverse(float n, float p, float u, const float* tab)
 {
