@@ -12,7 +12,11 @@
 // (row, 4-tick group) items.
 // An item draws one Philox block for its four ticks when fluctuating (four Box-Muller
 // normals), forms Q' w_p w_t per bin and adds the four values into the grid with one
-// vector reduction.
+// vector reduction.  The exact binomial fluctuation (an instance of its own) strides over
+// single bins instead: each draw walks its bin's CDF, and neighbouring ticks, whose walks
+// cost alike, then run side by side in a group.  With renormalisation the weights of each
+// axis are divided by the mass of its unclipped n-sigma window (folded into the per-depo
+// scale of the decision).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
