@@ -95,17 +95,25 @@ __device__ __noinline__ float binomial_inverse(float n, float p, float u, const 
     const float fm = binomial_pmf(m, n, p, q, tab);
     const float qp = __fdividef(q, p), pq = __fdividef(p, q);
     float C = fm, comp = 0.0f, f = fm, k = m;
-    int j = 0;
+    // the sum below the mode in segments: 31 recurrence steps, then the 32nd re-anchored
 #pragma unroll 1
-    while (k > 0.0f && f >= kBinomTiny) {
-        f = binomial_step(false, k, f, ++j, n, p, q, qp, pq, tab);
+    while (true) {
+        int i = 0;
+#pragma unroll 1
+        for (; i < 31 && k > 0.0f && f >= kBinomTiny; ++i) {
+            f *= __fdividef(k * qp, n - k + 1.0f);
+            kahan_add(C, comp, f);
+            k -= 1.0f;
+        }
+        if (i < 31 || !(k > 0.0f && f >= kBinomTiny)) break;
+        f = binomial_pmf(k - 1.0f, n, p, q, tab);
         kahan_add(C, comp, f);
         k -= 1.0f;
     }
     C = __fsub_rn(C, comp);
     k = m;
     f = fm;
-    j = 0;
+    int j = 0;
     if (u < C) {
         // (a u below the rounding residue of the sum, ~1e-7, stops where the terms vanish)
 #pragma unroll 1
