@@ -88,7 +88,7 @@ __device__ __forceinline__ float binomial_step(bool up, float k, float f, int j,
 // while u lies below F(k - 1), or up adding P(k + 1), until u < F(k).  Every loop ends
 // within a few standard deviations of the mode, where the terms fall below 2^-32 (u >= 2^-24),
 // and the loop counters bound them by n in any case.
-__device__ __noinline__ float binomial_inverse(float n, float p, float u, const float* tab)
+__device__ __forceinline__ float binomial_inverse(float n, float p, float u, const float* tab)
 {
     const float q = 1.0f - p;
     const float m = fminf(floorf((n + 1.0f) * p), n);
