@@ -160,3 +160,22 @@ def test_fluctuate_out_of_range_is_rejected(W):
     with pytest.raises(W.WcsimError) as e:
         W.Plane(g, S.DriftParams(fluctuate=3), np.zeros((g.n_imp, g.n_wires, g.n_ticks), np.complex64))
     assert e.value.status == W.EINVAL
+
+
+def test_binomial_full_size_plane_properties(W):
+    """The 960 x 6000 plane with 100k depos, as the bench times it: integer counts, zero
+    outside the patches' windows, and a total within six standard deviations of the mean
+    total (variance sum_b N p_b (1 - p_b) <= sum of the means; the oracle's FP64 mean grid)."""
+    wl = S.make_workload("plane960-100k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=2)
+    got = rasterize(W, g, prm, d)
+    assert np.array_equal(got, np.round(got)) and got.min() >= 0
+    mean = O.rasterize(g, dataclasses.replace(prm, fluctuate=0), d)
+    assert np.all(got[mean == 0] == 0)
+    mu = mean.sum()
+    assert abs(got.sum() - mu) <= 6.0 * np.sqrt(mu) + 1e-4 * mu
+    # and it is not the mean itself: per-bin deviations of the binomial's size
+    live = mean > 50
+    z = (got[live] - mean[live]) / np.sqrt(mean[live])
+    assert 0.5 < z.std() < 1.1
