@@ -120,19 +120,20 @@ def stage_bytes(g, n_depos, mean_bins):
     }
 
 
-def backward_stage_bytes(g, n_depos, mean_bins):
+def backward_stage_bytes(g, n_depos, mean_bins, reused=False):
     """Algorithmic bytes per launch of each backward stage (wcsim_run_backward with dL/dR,
     n_fw = n_wires, n_ft = n_ticks): S recomputed, S and G transformed, the wire adjoint
     (reads S^, G^ and H; writes dL/dR in full [n_imp][n_fw][n_ft] and dL/dS^), the inverse
-    time FFT of dL/dS and the per-depo gather."""
+    time FFT of dL/dS and the per-depo gather.  reused: the backward took the forward's S^
+    (wcsim_plane_set_reuse_forward), so S is neither recomputed nor transformed."""
     rows = g.n_rows
     nh = g.n_ticks // 2 + 1
     spec = rows * nh * 8                    # S^ or dL/dS^, all impact positions
     wspec = g.n_wires * nh * 8              # one plane-wide half spectrum (G^, M~)
     return {
         "bwd_zero": 0,                          # the preceding wcsim_run left the grid clear
-        "bwd_rasterize": n_depos * (32 + 4 * mean_bins),
-        "bwd_r2c_S": rows * g.n_ticks * 4 + spec,
+        "bwd_rasterize": 0 if reused else n_depos * (32 + 4 * mean_bins),
+        "bwd_r2c_S": 0 if reused else rows * g.n_ticks * 4 + spec,
         "bwd_r2c_G": g.n_wires * g.n_ticks * 4 + wspec,
         "bwd_wire_adjoint": (spec + wspec + g.n_imp * g.n_wires * g.n_ticks * 8   # part A
                              + spec + g.n_imp * g.n_wires * nh * 8 + spec),          # part B
@@ -546,15 +547,18 @@ def run_gpu(args):
         plane.set_params(prm)
         assert plane.check_flags() == 0
 
-    # ---- forward + backward (loss 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10,
-    # lifetime 8 ms; the backward runs on the mean path and includes dL/dR)
+    # ---- forward + backward of a fit step on the same plane and depos, fluctuation off (loss
+    # 1/2 |M - M_target|^2, target from D_L = 6, D_T = 10, lifetime 8 ms; the backward
+    # includes dL/dR)
     fb_ms = None
     bwd_stages = None
     if not args.no_backward:
         tgt = dataclasses.replace(prm, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0, fluctuate=0)
         plane.set_params(tgt)
         m_target = plane.run(dd).clone()
-        plane.set_params(prm)
+        plane.set_params(dataclasses.replace(prm, fluctuate=0))
+        # the backward takes the spectra its forward just computed (same depos, mean path)
+        plane.set_reuse_forward(True)
         G = torch.empty_like(wave)
 
         def fb_step():
@@ -579,6 +583,8 @@ def run_gpu(args):
                 if k in bwd_stage_ms:
                     bwd_stage_ms[k].append(v)
         plane.set_timing(False)
+        plane.set_reuse_forward(False)
+        plane.set_params(prm)
         fb_ms = sum(s.elapsed_time(e) for s, e in zip(fs, fe)) / args.steps
         bwd_stages = {k: float(np.mean(v)) for k, v in bwd_stage_ms.items()}
 
@@ -658,7 +664,7 @@ def run_gpu(args):
         return
     hbm, peak_kind = peaks()
     sb = stage_bytes(g, len(d), mean_bins)
-    bsb = backward_stage_bytes(g, len(d), mean_bins)
+    bsb = backward_stage_bytes(g, len(d), mean_bins, reused=True)
     avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     stages = {k: {"ms": avg[k], "GB/s": sb[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None,
                   "alg_bytes": sb[k]} for k in avg}

@@ -192,6 +192,15 @@ wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
                                 const float* grad_wave, wcsim_depo_grads* grads,
                                 void* grad_resp_c64, void* stream);
 
+/* enable = 1: wcsim_run_backward reuses the time-axis spectra of the grid (the FFT of S that
+ * the forward of Eq. 2 computes) when the plane's previous compute call was a successful
+ * wcsim_run or wcsim_run_adc on the same depo arrays (same pointers and count) with the same
+ * parameters and fluctuate = 0, instead of recomputing the mean-path grid and its spectra.
+ * The caller promises not to change the depo arrays between the two calls (as autograd keeps
+ * a forward's activations for its backward).  Any other compute call on the plane drops the
+ * spectra.  enable = 0 (the default): the backward always recomputes.  Host-only. */
+wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* plane, int32_t enable);
+
 /* Choices and best times (ms) found by wcsim_plane_autotune. */
 typedef struct {
     int32_t time_radix[8];     /* radices of the time-axis FFT plan, in pass order, 0-padded */

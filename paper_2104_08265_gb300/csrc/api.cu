@@ -86,6 +86,12 @@ struct wcsim_plane {
     int32_t bcap = 0;
     int device = 0;
     bool grid_clean = false;    // the plane's grid is all zero (consume-and-clear state)
+    // wcsim_plane_set_reuse_forward: shat holds the mean-path spectra of the last run on
+    // (fwd_depos, fwd_prm) while fwd_valid
+    bool reuse_fwd = false;
+    bool fwd_valid = false;
+    wcsim_depos fwd_depos = {};
+    wcsim_drift_params fwd_prm = {};
     bool wire_block = false;    // autotuned: use the block-level wire pass even if the warp one fits
     int32_t kd = 32;            // depos per rasterization CTA (the autotuner may change it)
     bool timing = false;
@@ -233,6 +239,7 @@ inline void markb(wcsim_plane* pl, int i, cudaStream_t s)
 wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaStream_t s,
                          int first_mark)
 {
+    pl->fwd_valid = false;              // the spectra are about to be those of `grid`
     cudaError_t e;
     if ((e = launch_rows_r2c(pl->dims, pl->pt, grid, pl->shat, pl->flags, s)))
         return cuda_fail(e, "rows_r2c launch");
@@ -454,6 +461,7 @@ wcsim_status wcsim_rasterize(wcsim_plane* pl, const wcsim_depos* depos, float* g
     cudaStream_t s = (cudaStream_t)stream;
     mark(pl, 0, s);
     mark(pl, 1, s);
+    pl->fwd_valid = false;
     cudaError_t e = launch_rasterize(make_consts(pl), depo_arrays(depos), grid, pl->flags, s);
     if (e) return cuda_fail(e, "rasterize launch");
     for (int i = 2; i <= kStages; ++i) mark(pl, i, s);
@@ -512,6 +520,11 @@ static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* o
     pl->dims.noise_amp = nullptr;
     pl->dims.adc_max = 0;
     if (st == WCSIM_OK && pl->dims.rows_variant == 0) pl->grid_clean = true;
+    if (st == WCSIM_OK && pl->reuse_fwd && pl->prm.fluctuate == 0) {
+        pl->fwd_valid = true;           // shat: the mean-path spectra of these depos
+        pl->fwd_depos = *depos;
+        pl->fwd_prm = pl->prm;
+    }
     return st;
 }
 
@@ -537,8 +550,11 @@ wcsim_status wcsim_plane_set_digitizer(wcsim_plane* pl, float gain, float pedest
     return WCSIM_OK;
 }
 
-wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, const float* grid,
-                                    float* dgrid, void* grad_resp_c64, void* stream)
+// have_shat: the plane's spectra already hold the time-axis FFT of `grid` (a forward on the
+// same grid just computed them), so that transform is skipped
+static wcsim_status convolve_adjoint(wcsim_plane* pl, const float* grad_wave, const float* grid,
+                                     float* dgrid, void* grad_resp_c64, void* stream,
+                                     bool have_shat)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
     if (!grad_wave || !grid || !dgrid) return fail(WCSIM_EINVAL, "grad_wave, grid or dgrid is NULL");
@@ -552,7 +568,9 @@ wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, con
     ConvDims dG = d;                    // G's rows: one "impact position" per wire
     dG.n_imp = 1;
     cudaError_t e;
-    if ((e = launch_rows_r2c(d, pl->pt, grid, pl->shat, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
+    pl->fwd_valid = false;              // the adjoint overwrites the spectra
+    if (!have_shat && (e = launch_rows_r2c(d, pl->pt, grid, pl->shat, pl->flags, s)))
+        return cuda_fail(e, "rows_r2c launch");
     markb(pl, 3, s);
     if ((e = launch_rows_r2c(dG, pl->pt, grad_wave, pl->mt, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
     markb(pl, 4, s);
@@ -566,6 +584,12 @@ wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, con
     return WCSIM_OK;
 }
 
+wcsim_status wcsim_convolve_adjoint(wcsim_plane* pl, const float* grad_wave, const float* grid,
+                                    float* dgrid, void* grad_resp_c64, void* stream)
+{
+    return convolve_adjoint(pl, grad_wave, grid, dgrid, grad_resp_c64, stream, false);
+}
+
 wcsim_status wcsim_rasterize_adjoint(wcsim_plane* pl, const wcsim_depos* depos, const float* dgrid,
                                      wcsim_depo_grads* grads, void* stream)
 {
@@ -577,6 +601,7 @@ wcsim_status wcsim_rasterize_adjoint(wcsim_plane* pl, const wcsim_depos* depos, 
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
+    pl->fwd_valid = false;
     if (grads->dglobal && (e = cudaMemsetAsync(grads->dglobal, 0, 3 * sizeof(double), s)))
         return cuda_fail(e, "gradient reset");
     DepoGrads g{grads->dq, grads->dp, grads->dt, grads->dsigma_L, grads->dsigma_T, grads->dglobal};
@@ -601,19 +626,28 @@ wcsim_status wcsim_run_backward(wcsim_plane* pl, const wcsim_depos* depos, const
     cudaStream_t s = (cudaStream_t)stream;
     const ConvDims& d = pl->dims;
     cudaError_t e = cudaSuccess;
+    // the spectra of the mean-path grid are still in place after a forward on the same depos
+    // and parameters (wcsim_plane_set_reuse_forward): no need to recompute them
+    const bool reuse = pl->reuse_fwd && pl->fwd_valid &&
+                       memcmp(&pl->fwd_depos, depos, sizeof(wcsim_depos)) == 0 &&
+                       memcmp(&pl->fwd_prm, &pl->prm, sizeof(wcsim_drift_params)) == 0;
+    pl->fwd_valid = false;
     markb(pl, 0, s);
-    if (!pl->grid_clean) {
+    if (!reuse && !pl->grid_clean) {
         e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
         if (e) return cuda_fail(e, "grid reset");
     }
     pl->grid_clean = false;             // the grid ends up holding dL/dS
     markb(pl, 1, s);
-    RasterConsts c = make_consts(pl);
-    c.fluctuate = 0;                    // the gradient is that of the mean waveform
-    if ((e = launch_rasterize(c, depo_arrays(depos), pl->grid, pl->flags, s)))
-        return cuda_fail(e, "rasterize launch");
+    if (!reuse) {
+        RasterConsts c = make_consts(pl);
+        c.fluctuate = 0;                // the gradient is that of the mean waveform
+        if ((e = launch_rasterize(c, depo_arrays(depos), pl->grid, pl->flags, s)))
+            return cuda_fail(e, "rasterize launch");
+    }
     markb(pl, 2, s);
-    if ((st = wcsim_convolve_adjoint(pl, grad_wave, pl->grid, pl->grid, grad_resp_c64, stream))) return st;
+    if ((st = convolve_adjoint(pl, grad_wave, pl->grid, pl->grid, grad_resp_c64, stream, reuse)))
+        return st;
     return wcsim_rasterize_adjoint(pl, depos, pl->grid, grads, stream);
 }
 
@@ -641,6 +675,7 @@ wcsim_status wcsim_batch_run(int32_t n_events, wcsim_plane* const* planes,
         if (planes[i]->device != planes[0]->device)
             return fail(WCSIM_EINVAL, "all planes of a batch must live on one device");
     }
+    for (int i = 0; i < n_events; ++i) planes[i]->fwd_valid = false;
     DeviceGuard dg(planes[0]->device);
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
@@ -665,6 +700,7 @@ wcsim_status wcsim_plane_autotune(wcsim_plane* pl, const wcsim_depos* depos, voi
                                   wcsim_tune_report* report)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    pl->fwd_valid = false;
     wcsim_status st = check_depos(depos);
     if (st) return st;
     DeviceGuard dg(pl->device);
@@ -788,6 +824,7 @@ wcsim_status wcsim_windows(wcsim_plane* pl, const wcsim_depos* depos, int32_t* o
     if (st) return st;
     if (!out && depos->n > 0) return fail(WCSIM_EINVAL, "out is NULL");
     if (((uintptr_t)out & 15) != 0) return fail(WCSIM_EINVAL, "out must be 16-byte aligned");
+    pl->fwd_valid = false;
     DeviceGuard dg(pl->device);
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaError_t e = launch_windows(make_consts(pl), depo_arrays(depos), out, pl->flags,
@@ -841,6 +878,14 @@ wcsim_status wcsim_plane_set_noise(wcsim_plane* pl, const float* amp, int32_t n_
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "noise spectrum upload");
     pl->noise_seed = seed;
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* pl, int32_t enable)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    pl->reuse_fwd = enable != 0;
+    pl->fwd_valid = false;
     return WCSIM_OK;
 }
 

@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_set_noise": [vp, vp, i32, ctypes.c_uint64, vp],
         "wcsim_run_adc": [vp, P(CDepos), vp, vp],
         "wcsim_plane_set_digitizer": [vp, ctypes.c_float, ctypes.c_float, i32],
+        "wcsim_plane_set_reuse_forward": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -354,6 +355,12 @@ class Plane:
     def set_wait_limit(self, ns: int):
         """Limit (ns) of the device-side waits for bulk copies; see wcsim_plane_set_wait_limit."""
         check(lib().wcsim_plane_set_wait_limit(self._h, ctypes.c_uint64(int(ns))))
+
+    def set_reuse_forward(self, enable: bool = True):
+        """Let backward() reuse the spectra of the preceding mean-path run() on the same depos
+        and parameters (the depos must not change in between); see
+        wcsim_plane_set_reuse_forward."""
+        check(lib().wcsim_plane_set_reuse_forward(self._h, 1 if enable else 0))
 
     def set_timing(self, enable: bool = True):
         check(lib().wcsim_plane_set_timing(self._h, 1 if enable else 0))

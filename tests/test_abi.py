@@ -58,6 +58,7 @@ def test_argument_checks_need_no_gpu(libpath):
         assert L.wcsim_plane_create(ctypes.byref(wcsim.c_geometry(g)), ctypes.c_void_p(16), 0, 0,
                                     ctypes.byref(bp), None, ctypes.byref(h)) == wcsim.EINVAL
         assert field.encode() in L.wcsim_last_error()
+    assert L.wcsim_plane_set_reuse_forward(None, 1) == wcsim.EINVAL
     assert L.wcsim_run(None, None, None, None) == wcsim.EINVAL
     assert L.wcsim_plane_destroy(None) == wcsim.OK
 

@@ -149,3 +149,60 @@ def test_autograd_function_gradients_and_a_fit_step(W):
         new = [x - 0.02 * s * x.grad / gnorm for x, s in zip(step, scale)]
         loss2 = 0.5 * ((simulate(pl, dd, *new) - target) ** 2).sum()
     assert float(loss2) < float(loss)
+
+
+def test_backward_reusing_the_forward_spectra_matches_oracle(W):
+    """set_reuse_forward: the backward after a mean-path run on the same depos takes the
+    run's spectra; gradients as the oracle's and as the recomputing backward's."""
+    import torch
+    wl = S.make_workload("fit960-100k")
+    g, prm, kind, d = wl.planes[0]
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    dd = W.DeviceDepos.from_host(d)
+    G = torch.from_numpy(np.random.default_rng(91).normal(size=(g.n_wires, g.n_ticks))
+                         .astype(np.float32)).cuda()
+    plain = pl.backward(dd, G, want_resp=True)
+    pl.set_reuse_forward(True)
+    pl.run(dd)
+    got = pl.backward(dd, G, want_resp=True)
+    ref, rdR = _oracle_backward(g, prm, R, d, G.cpu().numpy().astype(np.float64))
+    _grads_close(got, ref, "reused spectra")
+    assert_close(got["response"].cpu().numpy(), rdR, what="reused spectra dR")
+    for k in ("q", "p", "t", "sigma_L", "sigma_T", "response"):
+        assert_close(got[k].cpu().numpy(), plain[k].cpu().numpy(), what="reuse vs recompute " + k)
+
+
+def test_reuse_is_dropped_when_the_forward_does_not_apply(W):
+    """Changed parameters, a fluctuating forward, another call in between, other depo arrays:
+    each backward recomputes, and its gradients are the oracle's for its own inputs."""
+    import torch
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=0, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=8000.0)
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    pl.set_reuse_forward(True)
+    dd = W.DeviceDepos.from_host(d)
+    G = torch.from_numpy(np.random.default_rng(92).normal(size=(g.n_wires, g.n_ticks))
+                         .astype(np.float32)).cuda()
+    Gh = G.cpu().numpy().astype(np.float64)
+    other = dataclasses.replace(prm, DT_cm2_s=4.0)
+    # 1. parameters changed after the run
+    pl.run(dd)
+    pl.set_params(other)
+    _grads_close(pl.backward(dd, G), _oracle_backward(g, other, R, d, Gh)[0], "params changed")
+    # 2. a fluctuating forward: the backward stays on the mean path
+    pl.set_params(dataclasses.replace(prm, fluctuate=1))
+    pl.run(dd)
+    _grads_close(pl.backward(dd, G), _oracle_backward(g, prm, R, d, Gh)[0], "fluctuating run")
+    # 3. another compute call in between
+    pl.set_params(prm)
+    pl.run(dd)
+    pl.convolve(torch.zeros((g.n_rows, g.n_ticks), dtype=torch.float32, device="cuda"))
+    _grads_close(pl.backward(dd, G), _oracle_backward(g, prm, R, d, Gh)[0], "call in between")
+    # 4. other depo arrays (a copy holding other values)
+    d2 = dataclasses.replace(d, q=(d.q * 0.5).astype(np.float32))
+    pl.run(dd)
+    _grads_close(pl.backward(W.DeviceDepos.from_host(d2), G),
+                 _oracle_backward(g, prm, R, d2, Gh)[0], "other depos")
