@@ -5,7 +5,11 @@ response spectrum.  Forward and backward both run in the CUDA library
 
 The backward pass differentiates the mean (fluctuation-free) waveform with every depo's bin
 window held fixed, so a plane created with fluctuation on still gets the gradient of the
-expected frame.
+expected frame.  It runs with the parameters and the response of its own forward, even when
+later forwards on the same plane changed them.  The depo tensors are saved for backward, so
+autograd reports an in-place change made between the two; with
+plane.set_reuse_forward(True) the backward of the plane's latest forward also reuses that
+forward's spectra (fluctuation off).
 """
 from __future__ import annotations
 
@@ -37,13 +41,25 @@ class WcsimFn(torch.autograd.Function):
         wave = plane.run(depos)
         ctx.plane = plane
         ctx.depos = depos
+        ctx.prm = prm
+        ctx.response_serial = getattr(plane, "response_serial", 0)
+        ctx.save_for_backward(q, p, t, td, ids, response)
         ctx.want_resp = response is not None and response.requires_grad
         ctx.scalar_meta = [(x.dtype, x.device) for x in (DL, DT, lifetime)]
         return wave
 
     @staticmethod
     def backward(ctx, grad_wave):
-        g = ctx.plane.backward(ctx.depos, grad_wave.contiguous().float(), want_resp=ctx.want_resp)
+        plane = ctx.plane
+        *_, response = ctx.saved_tensors          # (also checks the depos were not changed)
+        if plane.params != ctx.prm:
+            plane.set_params(ctx.prm)
+        if getattr(plane, "response_serial", 0) != ctx.response_serial:
+            if response is None:
+                raise RuntimeError("the plane's response changed after this forward, which "
+                                   "used the response the plane had then; pass it to simulate")
+            plane.set_response(response)
+        g = plane.backward(ctx.depos, grad_wave.contiguous().float(), want_resp=ctx.want_resp)
         (dl_t, dl_d), (dt_t, dt_d), (tau_t, tau_d) = ctx.scalar_meta
         return (None, g["q"], g["p"].double(), g["t"].double(), None, None,
                 g["DL"].to(dl_t).to(dl_d), g["DT"].to(dt_t).to(dt_d),

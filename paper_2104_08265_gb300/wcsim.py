@@ -217,6 +217,7 @@ class Plane:
     def set_response(self, response, stream=None):
         check(lib().wcsim_plane_set_response(self._h, response.contiguous().data_ptr(),
                                              _stream_handle(stream)))
+        self.response_serial = getattr(self, "response_serial", 0) + 1
 
     def _wave(self, out):
         import torch

@@ -148,7 +148,7 @@ def test_autograd_function_gradients_and_a_fit_step(W):
         scale = [4.0, 8.8, 10000.0]
         new = [x - 0.02 * s * x.grad / gnorm for x, s in zip(step, scale)]
         loss2 = 0.5 * ((simulate(pl, dd, *new) - target) ** 2).sum()
-    assert float(loss2) < float(loss)
+    assert float(loss2) < float(loss.detach())
 
 
 def test_backward_reusing_the_forward_spectra_matches_oracle(W):
@@ -206,3 +206,46 @@ def test_reuse_is_dropped_when_the_forward_does_not_apply(W):
     pl.run(dd)
     _grads_close(pl.backward(W.DeviceDepos.from_host(d2), G),
                  _oracle_backward(g, prm, R, d2, Gh)[0], "other depos")
+
+
+def test_autograd_backward_uses_its_own_forward_parameters(W):
+    """Two forwards on one plane with different (D_L, D_T, tau) and one loss over both: each
+    backward runs with its own forward's parameters (autograd runs the second's first)."""
+    import torch
+    from paper_2104_08265_gb300.autograd import simulate
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=0)
+    R = torch.from_numpy(S.make_response(g, kind)).cuda()
+    pl = W.Plane(g, prm, R)
+    dd = W.DeviceDepos.from_host(d)
+    t64 = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda", requires_grad=True)
+    sets = [(4.0, 8.8, 10000.0), (6.0, 10.0, 8000.0)]
+    rng = np.random.default_rng(93)
+    Gs = [torch.from_numpy(rng.normal(size=(g.n_wires, g.n_ticks)).astype(np.float32)).cuda()
+          for _ in sets]
+    leaves, loss = [], 0.0
+    for (a, b, c), G in zip(sets, Gs):
+        q = dd.q.clone().requires_grad_()
+        x = [t64(a), t64(b), t64(c)]
+        wave = simulate(pl, W.DeviceDepos(dd.p, dd.t, dd.td, q, dd.id), *x)
+        loss = loss + (wave * G).sum()
+        leaves.append((q, x))
+    loss.backward()
+    for ((a, b, c), G, (q, x)) in zip(sets, Gs, leaves):
+        pl.set_params(dataclasses.replace(prm, DL_cm2_s=a, DT_cm2_s=b, lifetime_us=c))
+        ref = pl.backward(dd, G)
+        rel = float(torch.linalg.vector_norm(q.grad - ref["q"]) / torch.linalg.vector_norm(ref["q"]))
+        assert rel < 1e-6, (a, b, c, rel)
+        for xx, k in zip(x, ("DL", "DT", "lifetime")):
+            assert float(xx.grad) == pytest.approx(float(ref[k]), rel=1e-5), (a, b, c, k)
+    # with the plane's spectra reused, the same gradients
+    pl.set_params(prm)
+    pl.set_reuse_forward(True)
+    q = dd.q.clone().requires_grad_()
+    x = [t64(4.0), t64(8.8), t64(10000.0)]
+    (simulate(pl, W.DeviceDepos(dd.p, dd.t, dd.td, q, dd.id), *x) * Gs[0]).sum().backward()
+    q0, x0 = leaves[0]
+    assert float(torch.linalg.vector_norm(q.grad - q0.grad) / torch.linalg.vector_norm(q0.grad)) < 1e-5
+    for a_, b_ in zip(x, x0):
+        assert float(a_.grad) == pytest.approx(float(b_.grad), rel=1e-4)
