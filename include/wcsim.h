@@ -185,7 +185,8 @@ wcsim_status wcsim_rasterize_adjoint(wcsim_plane* plane, const wcsim_depos* depo
                                      const float* dgrid, wcsim_depo_grads* grads, void* stream);
 
 /* Backward pass of wcsim_run for L with dL/dwave = grad_wave: recompute the grid on the
- * mean path (fluctuation off: the gradient is that of the expected waveform), run
+ * mean path (fluctuation off: the gradient is that of the expected waveform; skipped, with
+ * the time-axis FFT of the grid, when wcsim_plane_set_reuse_forward applies), run
  * wcsim_convolve_adjoint and wcsim_rasterize_adjoint.  grad_resp_c64 as in
  * wcsim_convolve_adjoint (NULL skips it).  Uses the plane's scratch and grid. */
 wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
