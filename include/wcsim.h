@@ -302,6 +302,15 @@ wcsim_status wcsim_convolve_noalloc(const wcsim_geometry* geom, const void* resp
                                     int32_t n_fw, int32_t n_ft, const float* grid, float* wave,
                                     void* stream);
 
+/* Status of the last wcsim_convolve_noalloc call on the current device, without allocating:
+ * waits for `stream` (the stream of that call), then copies the call's device flag word from
+ * the static scratch to the host.  *flags (may be NULL) receives the bits (bit 1: a bounded
+ * device-side wait for an asynchronous copy gave up, so part of that call's output was never
+ * written).  Returns WCSIM_ETIMEOUT if bit 1 is set, else WCSIM_OK.  Like the entry point it
+ * checks, it has no counterpart in the paper.  The next wcsim_convolve_noalloc call on the
+ * device clears the word. */
+wcsim_status wcsim_convolve_noalloc_check(void* stream, int32_t* flags);
+
 /* Release the plane and everything it owns.  NULL is accepted. */
 wcsim_status wcsim_plane_destroy(wcsim_plane* plane);
 

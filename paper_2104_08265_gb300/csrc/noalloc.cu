@@ -17,6 +17,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include "async_copy.cuh"
 #include "wcsim_internal.cuh"
 
 // The scratch of every wcsim_convolve_noalloc call on this device.
@@ -31,6 +32,36 @@ constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices];   // device address of g_scratch per device ordinal
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The flag word sits at the start of the scratch (offset 0 in every call's carving).
+constexpr size_t kFlagsOffset = 0;
+
+// The device address of g_scratch on the current device, looked up once per device (with
+// that device current).  Returns a CUDA error code or cudaSuccess.
+cudaError_t scratch_base(unsigned char** out, char* msg, size_t msg_len)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        snprintf(msg, msg_len, "cudaGetDevice: %s", cudaGetErrorString(e));
+        return e;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        snprintf(msg, msg_len, "device ordinal %d out of range", dev);
+        return cudaErrorInvalidDevice;
+    }
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            snprintf(msg, msg_len, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return cudaSuccess;
+}
 
 // Twiddle table of a plan: entry (r - 1) ns + k of pass p = exp(-2 pi i r k / (ns R)),
 // FP64 sincospi rounded to FP32.
@@ -101,7 +132,7 @@ extern "C" wcsim_status wcsim_convolve_noalloc(const wcsim_geometry* geom, const
     // carve the static scratch: flag word, twiddles, H, Shat, Mt
     const size_t cols = (size_t)d.nkb * kBlockCols;
     size_t off = 0;
-    const size_t o_flags = off;  off += 256;
+    const size_t o_flags = kFlagsOffset;  off += 256;
     const size_t o_twt = off;    off += up256((size_t)len_t * sizeof(float2));
     const size_t o_tww = off;    off += up256((size_t)len_w * sizeof(float2));
     const size_t o_twarp = off;  off += warp ? up256(2 * (size_t)n_fw * sizeof(float2)) : 0;
@@ -117,20 +148,9 @@ extern "C" wcsim_status wcsim_convolve_noalloc(const wcsim_geometry* geom, const
     }
 
     // set-up, once per device: the device address of the static array
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return report_error(WCSIM_ECUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return report_error(WCSIM_ECUDA, "device ordinal out of range");
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            snprintf(msg, sizeof(msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            return report_error(WCSIM_ECUDA, msg);
-        }
-        g_scratch_addr[dev] = p;
-    }
-    unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    unsigned char* base = nullptr;
+    cudaError_t e = scratch_base(&base, msg, sizeof(msg));
+    if (e != cudaSuccess) return report_error(WCSIM_ECUDA, msg);
     int* flags = reinterpret_cast<int*>(base + o_flags);
     float2* tw_t = reinterpret_cast<float2*>(base + o_twt);
     float2* tw_w = reinterpret_cast<float2*>(base + o_tww);
@@ -155,5 +175,30 @@ extern "C" wcsim_status wcsim_convolve_noalloc(const wcsim_geometry* geom, const
                   : launch_wire_pass(d, pw, shat, H, mt, flags, s)) ||
         (e = launch_rows_c2r(d, pt, mt, wave, s)))
         return report_error(WCSIM_ECUDA, cudaGetErrorString(e));
+    return WCSIM_OK;
+}
+
+extern "C" wcsim_status wcsim_convolve_noalloc_check(void* stream, int32_t* flags)
+{
+    char msg[256];
+    unsigned char* base = nullptr;
+    cudaError_t e = scratch_base(&base, msg, sizeof(msg));
+    if (e != cudaSuccess) return report_error(WCSIM_ECUDA, msg);
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t h = 0;
+    // a copy into pageable host memory: the runtime stages it itself, nothing is allocated here
+    e = cudaMemcpyAsync(&h, base + kFlagsOffset, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof(msg), "flag read: %s", cudaGetErrorString(e));
+        return report_error(WCSIM_ECUDA, msg);
+    }
+    if (flags) *flags = h;
+    if (h & kErrTimeout) {
+        snprintf(msg, sizeof(msg),
+                 "a device-side wait for an asynchronous copy gave up in the last "
+                 "wcsim_convolve_noalloc call (flags 0x%x); its output is incomplete", h);
+        return report_error(WCSIM_ETIMEOUT, msg);
+    }
     return WCSIM_OK;
 }

@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_stage_times": [vp, P(ctypes.c_float), i32],
         "wcsim_plane_destroy": [vp],
         "wcsim_convolve_noalloc": [P(CGeometry), vp, i32, i32, vp, vp, vp],
+        "wcsim_convolve_noalloc_check": [vp, P(i32)],
         "wcsim_convolve_adjoint": [vp, vp, vp, vp, vp, vp],
         "wcsim_rasterize_adjoint": [vp, P(CDepos), vp, P(CDepoGrads), vp],
         "wcsim_run_backward": [vp, P(CDepos), vp, P(CDepoGrads), vp, vp],
@@ -388,6 +389,15 @@ def convolve_noalloc(geom: Geometry, response, grid, out=None, n_fw: int = 0, n_
                                        grid.contiguous().data_ptr(), out.data_ptr(),
                                        _stream_handle(stream)))
     return out
+
+
+def convolve_noalloc_check(stream=None) -> int:
+    """Flag bits of the last convolve_noalloc call on the current device (waits for its
+    stream; allocates nothing).  Raises WcsimError (ETIMEOUT) when a device-side wait of that
+    call gave up, so part of its output is missing."""
+    f = ctypes.c_int32(0)
+    check(lib().wcsim_convolve_noalloc_check(_stream_handle(stream), ctypes.byref(f)))
+    return int(f.value)
 
 
 MAX_BATCH = 64
