@@ -49,8 +49,8 @@ def build(force: bool = False) -> str:
     """Compile the C part of the oracle (plain gcc, no FMA contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        cmd = [os.environ.get("CC", "gcc"), "-std=c11", "-O2", "-ffp-contract=off", "-fPIC",
-               "-shared", _SRC, "-o", tmp, "-lm"]
+        cmd = [os.environ.get("CC", "gcc"), "-std=c11", "-O2", "-ffp-contract=off", "-fopenmp",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
@@ -101,6 +101,17 @@ def _load():
             lib.og_depo_grads.argtypes = [P(_Geom), P(_Params), i64, P(d), P(d), P(d), P(f),
                                           P(d), P(d), P(d), P(d), P(d), P(d), P(d)]
             lib.og_depo_grads.restype = ctypes.c_int
+            lib.og_rasterize_rows.argtypes = [P(_Geom), P(_Params), i64, P(d), P(d), P(d), P(f),
+                                              P(u32), i64, P(i64), P(i64), P(d)]
+            lib.og_rasterize_rows.restype = ctypes.c_int
+            lib.og_bin_terms.argtypes = [P(_Geom), P(_Params), i64, P(d), P(d), P(d), P(f),
+                                         P(u32), i64, i64, i64, P(i64), P(d), P(d), P(d), P(d)]
+            lib.og_bin_terms.restype = i64
+            lib.og_rasterize_mt.argtypes = [P(_Geom), P(_Params), i64, P(d), P(d), P(d), P(f),
+                                            P(u32), ctypes.c_int, ctypes.c_void_p, P(d)]
+            lib.og_rasterize_mt.restype = ctypes.c_int
+            lib.og_patch_bytes.argtypes = []
+            lib.og_patch_bytes.restype = i64
             _lib = lib
     return _lib
 
@@ -200,18 +211,63 @@ class _One:
         self.id = np.zeros(1, np.uint32)
 
 
-def rasterize(geom, params, depos) -> np.ndarray:
-    """Grid S [n_wires*n_imp][n_ticks] (float64) with every depo's patch added."""
+def rasterize(geom, params, depos, threads: int = 1) -> np.ndarray:
+    """Grid S [n_wires*n_imp][n_ticks] (float64) with every depo's patch added, in depo order.
+    threads != 1 fills bands of rows on that many host threads (0: all), bit for bit the
+    same grid."""
     lib = _load()
     p, t, td, q, ids = _depo_arrays(depos)
     grid = np.zeros((geom.n_wires * geom.n_imp, geom.n_ticks), np.float64)
-    rc = lib.og_rasterize(ctypes.byref(_geom(geom)), ctypes.byref(_params(params)),
-                          p.shape[0], _ptr(p, ctypes.c_double), _ptr(t, ctypes.c_double),
-                          _ptr(td, ctypes.c_double), _ptr(q, ctypes.c_float),
-                          _ptr(ids, ctypes.c_uint32), _ptr(grid, ctypes.c_double))
+    args = (ctypes.byref(_geom(geom)), ctypes.byref(_params(params)), p.shape[0],
+            _ptr(p, ctypes.c_double), _ptr(t, ctypes.c_double), _ptr(td, ctypes.c_double),
+            _ptr(q, ctypes.c_float), _ptr(ids, ctypes.c_uint32))
+    if threads == 1:
+        rc = lib.og_rasterize(*args, _ptr(grid, ctypes.c_double))
+    else:
+        scratch = np.empty(max(1, p.shape[0]) * int(lib.og_patch_bytes()), np.uint8)
+        rc = lib.og_rasterize_mt(*args, int(threads), scratch.ctypes.data,
+                                 _ptr(grid, ctypes.c_double))
     if rc != 0:
         raise ValueError("oracle: patch larger than its fixed buffer")
     return grid
+
+
+def rasterize_rows(geom, params, depos, rows) -> np.ndarray:
+    """Rows `rows` (distinct) of the grid rasterize() makes, bit for bit: [len(rows)][n_ticks]."""
+    lib = _load()
+    p, t, td, q, ids = _depo_arrays(depos)
+    rows = np.ascontiguousarray(rows, np.int64)
+    out = np.zeros((rows.shape[0], geom.n_ticks), np.float64)
+    slot = np.empty(geom.n_wires * geom.n_imp, np.int64)
+    rc = lib.og_rasterize_rows(ctypes.byref(_geom(geom)), ctypes.byref(_params(params)),
+                               p.shape[0], _ptr(p, ctypes.c_double), _ptr(t, ctypes.c_double),
+                               _ptr(td, ctypes.c_double), _ptr(q, ctypes.c_float),
+                               _ptr(ids, ctypes.c_uint32), rows.shape[0],
+                               _ptr(rows, ctypes.c_int64), _ptr(slot, ctypes.c_int64),
+                               _ptr(out, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle: bad rows or patch larger than its fixed buffer")
+    return out
+
+
+def bin_terms(geom, params, depos, r: int, k: int, max_terms: int = 4096) -> dict:
+    """The terms of grid bin (r, k), one per depo whose window holds it, in depo order:
+    depo index, value added, and the trial count, p_b and uniform of its exact binomial draw
+    (n_e = -1 where no draw is made)."""
+    lib = _load()
+    p, t, td, q, ids = _depo_arrays(depos)
+    idx = np.zeros(max_terms, np.int64)
+    val, n_e, pb, u = (np.zeros(max_terms) for _ in range(4))
+    m = lib.og_bin_terms(ctypes.byref(_geom(geom)), ctypes.byref(_params(params)), p.shape[0],
+                         _ptr(p, ctypes.c_double), _ptr(t, ctypes.c_double),
+                         _ptr(td, ctypes.c_double), _ptr(q, ctypes.c_float),
+                         _ptr(ids, ctypes.c_uint32), int(r), int(k), max_terms,
+                         _ptr(idx, ctypes.c_int64), _ptr(val, ctypes.c_double),
+                         _ptr(n_e, ctypes.c_double), _ptr(pb, ctypes.c_double),
+                         _ptr(u, ctypes.c_double))
+    if m < 0:
+        raise ValueError("oracle: more terms than max_terms")
+    return {"idx": idx[:m], "val": val[:m], "n_e": n_e[:m], "p": pb[:m], "u": u[:m]}
 
 
 # --------------------------------------------------------------------------- a4-a6
@@ -239,9 +295,9 @@ def convolve(geom, response, grid) -> np.ndarray:
     return M[: geom.n_wires, : geom.n_ticks].copy()
 
 
-def run(geom, params, response, depos) -> np.ndarray:
-    """Depos to per-wire waveforms: rasterize, then convolve."""
-    return convolve(geom, response, rasterize(geom, params, depos))
+def run(geom, params, response, depos, threads: int = 1) -> np.ndarray:
+    """Depos to per-wire waveforms: rasterize (on `threads` host threads), then convolve."""
+    return convolve(geom, response, rasterize(geom, params, depos, threads))
 
 
 # --------------------------------------------------------------------------- noise

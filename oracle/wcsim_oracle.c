@@ -44,10 +44,12 @@
  *     the kernel's precision).  Above N p (1 - p) = 65536 or N = 2^24 the normal
  *     approximation above is used instead;
  *
- * Build: cc -O2 -ffp-contract=off -fPIC -shared wcsim_oracle.c -lm
- * (no FMA contraction: the bin decision must be evaluated operation by operation).
+ * Build: cc -O2 -ffp-contract=off -fopenmp -fPIC -shared wcsim_oracle.c -lm
+ * (no FMA contraction: the bin decision must be evaluated operation by operation; OpenMP
+ * only spreads og_rasterize_mt's row bands over host threads).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -316,7 +318,7 @@ static void axis_weight_derivs(double mu, double sig, int delta, double origin, 
 static int axis_sums(double mu, double sig, int delta, double origin, double bin, int64_t lo,
                      int64_t hi, double* T, double* sm, double* ss)
 {
-    static double w[OG_MAXB], dm[OG_MAXB], ds[OG_MAXB];
+    double w[OG_MAXB], dm[OG_MAXB], ds[OG_MAXB];    /* on the stack: called from threads */
     *T = 0.0;
     if (sm) *sm = 0.0;
     if (ss) *ss = 0.0;
@@ -398,54 +400,205 @@ int og_depo_weights(const og_geom* g, const og_params* pr, double p, double t, d
     return 1;
 }
 
-/* a1-a3 (+a2f): accumulate every depo's patch into grid[n_rows][n_ticks] (FP64). */
-int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double* p,
-                 const double* t, const double* td, const float* q, const uint32_t* id,
-                 double* grid)
+/* What one depo adds, prepared once: its drift and window (d), the exact binomial's trial
+ * count n_e = rint(Q') with Q' formed in FP32 as the kernel forms it (an integer decision
+ * taken in the kernel's precision). */
+typedef struct {
+    og_depo d;
+    double n_e;
+} og_patch;
+
+static og_patch prepare_patch(const og_geom* g, const og_params* pr, const og_consts* c,
+                              double p, double t, double td, float q)
+{
+    og_patch pt;
+    pt.d = drift_and_window(g, pr, c, p, t, td, q);
+    const float qf = q * expf(-(float)td * c->inv_tau_f);
+    pt.n_e = rint((double)qf);
+    return pt;
+}
+
+/* FP64 weights of rows r0..r1 and ticks k0..k1 of the patch (sub-ranges of its window),
+ * renormalised over the unclipped window when asked.  Returns 0, or -1 for a window the
+ * fixed buffers cannot hold. */
+static int patch_weights(const og_geom* g, const og_params* pr, const og_depo* d, int64_t r0,
+                         int64_t r1, int64_t k0, int64_t k1, double* wp, double* wt)
+{
+    const double dp = g->pitch_mm / (double)g->n_imp;
+    if (r1 - r0 + 1 > OG_MAXB || k1 - k0 + 1 > OG_MAXB) return -1;
+    axis_weights(d->mu_p, d->sig_p, d->delta_p, g->p0_mm, dp, r0, r1, wp);
+    axis_weights(d->mu_t, d->sig_t, d->delta_t, g->t0_us, g->tick_us, k0, k1, wt);
+    if (d->delta_p && r0 != d->r_lo) wp[0] = 0.0;   /* the one bin is the window's first */
+    if (d->delta_t && k0 != d->k_lo) wt[0] = 0.0;
+    if (pr->renormalize) {
+        double T;
+        if (axis_sums(d->mu_p, d->sig_p, d->delta_p, g->p0_mm, dp, d->r_lo_u, d->r_hi_u, &T,
+                      NULL, NULL))
+            return -1;
+        renormalize_axis(r1 - r0 + 1, wp, NULL, NULL, T, 0.0, 0.0);
+        if (axis_sums(d->mu_t, d->sig_t, d->delta_t, g->t0_us, g->tick_us, d->k_lo_u,
+                      d->k_hi_u, &T, NULL, NULL))
+            return -1;
+        renormalize_axis(k1 - k0 + 1, wt, NULL, NULL, T, 0.0, 0.0);
+    }
+    return 0;
+}
+
+/* The value a depo adds to bin (r, k) given its weights there: the mean Q' wp wt, or its
+ * normal approximation (fluctuate 1), or the exact binomial draw (fluctuate 2).  When n_out
+ * is not NULL it receives the draw's trial count, p_b and uniform (n_out = -1: no draw). */
+static double bin_value(const og_params* pr, const og_patch* pt, double wpr, double wtk,
+                        int64_t r, int64_t k, uint32_t id, const uint32_t key[2],
+                        double* n_out, double* p_out, double* u_out)
+{
+    const og_depo* d = &pt->d;
+    double mean = d->qatt * wpr * wtk;
+    double val = mean;
+    double pb = wpr * wtk;                       /* mu_b / Q' */
+    if (pb > 1.0) pb = 1.0;
+    if (n_out) { *n_out = -1.0; *p_out = pb; *u_out = 0.0; }
+    if (pr->fluctuate == 2 && pt->n_e * pb * (1.0 - pb) <= 65536.0 && pt->n_e <= 16777216.0) {
+        if (mean > 0.0) {
+            double u = og_bin_uniform(r, k, id, pr->plane_id, key);
+            val = (double)og_binomial_draw((int64_t)pt->n_e, pb, u);
+            if (n_out) { *n_out = pt->n_e; *u_out = u; }
+        }
+    } else if (pr->fluctuate) {
+        /* normal approximation to Binomial(Q', mean/Q') */
+        double z = og_bin_normal(r, k, id, pr->plane_id, key);
+        double var = mean * (1.0 - mean / d->qatt);
+        if (var < 0.0) var = 0.0;
+        val = mean + sqrt(var) * z;
+        if (val < 0.0) val = 0.0;
+    }
+    return val;
+}
+
+/* a1-a3 (+a2f): accumulate every depo's patch into grid[n_rows][n_ticks] (FP64), in depo
+ * order.  row_slot (may be NULL) restricts it to rows r with row_slot[r] >= 0, written to
+ * row row_slot[r] of grid instead. */
+static int rasterize_into(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                          const double* t, const double* td, const float* q,
+                          const uint32_t* id, const int64_t* row_slot, double* grid)
 {
     static double wp[OG_MAXB], wt[OG_MAXB];
     og_consts c = make_consts(g, pr);
-    double dp = g->pitch_mm / (double)g->n_imp;
     const int64_t nt = g->n_ticks;
     const uint32_t key[2] = {(uint32_t)pr->seed, (uint32_t)(pr->seed >> 32)};
     for (int64_t i = 0; i < n; ++i) {
-        og_depo d = drift_and_window(g, pr, &c, p[i], t[i], td[i], q[i]);
-        if (!d.ok || !(d.qatt > 0.0)) continue;   /* Q' underflowed: adds nothing */
-        if (d.r_hi - d.r_lo + 1 > OG_MAXB || d.k_hi - d.k_lo + 1 > OG_MAXB) return -1;
-        axis_weights(d.mu_p, d.sig_p, d.delta_p, g->p0_mm, dp, d.r_lo, d.r_hi, wp);
-        axis_weights(d.mu_t, d.sig_t, d.delta_t, g->t0_us, g->tick_us, d.k_lo, d.k_hi, wt);
-        if (pr->renormalize && renormalize_depo(g, &d, wp, wt, NULL, NULL, NULL, NULL))
-            return -1;
-        /* the exact binomial's trial count: Q' rounded to whole electrons, Q' formed in
-         * FP32 as the kernel forms it */
-        const float qf = q[i] * expf(-(float)td[i] * c.inv_tau_f);
-        const double n_e = rint((double)qf);
-        for (int64_t r = d.r_lo; r <= d.r_hi; ++r) {
-            double* row = grid + r * nt;
-            for (int64_t k = d.k_lo; k <= d.k_hi; ++k) {
-                double mean = d.qatt * wp[r - d.r_lo] * wt[k - d.k_lo];
-                double val = mean;
-                double pb = wp[r - d.r_lo] * wt[k - d.k_lo];   /* mu_b / Q' */
-                if (pb > 1.0) pb = 1.0;
-                if (pr->fluctuate == 2 && n_e * pb * (1.0 - pb) <= 65536.0 && n_e <= 16777216.0) {
-                    if (mean > 0.0) {
-                        double u = og_bin_uniform(r, k, id[i], pr->plane_id, key);
-                        val = (double)og_binomial_draw((int64_t)n_e, pb, u);
-                    }
-                } else if (pr->fluctuate) {
-                    /* normal approximation to Binomial(Q', mean/Q') */
-                    double z = og_bin_normal(r, k, id[i], pr->plane_id, key);
-                    double var = mean * (1.0 - mean / d.qatt);
-                    if (var < 0.0) var = 0.0;
-                    val = mean + sqrt(var) * z;
-                    if (val < 0.0) val = 0.0;
-                }
-                row[k] += val;
-            }
+        og_patch pt = prepare_patch(g, pr, &c, p[i], t[i], td[i], q[i]);
+        const og_depo* d = &pt.d;
+        if (!d->ok || !(d->qatt > 0.0)) continue;   /* Q' underflowed: adds nothing */
+        if (patch_weights(g, pr, d, d->r_lo, d->r_hi, d->k_lo, d->k_hi, wp, wt)) return -1;
+        for (int64_t r = d->r_lo; r <= d->r_hi; ++r) {
+            if (row_slot && row_slot[r] < 0) continue;
+            double* row = grid + (row_slot ? row_slot[r] : r) * nt;
+            for (int64_t k = d->k_lo; k <= d->k_hi; ++k)
+                row[k] += bin_value(pr, &pt, wp[r - d->r_lo], wt[k - d->k_lo], r, k, id[i],
+                                    key, NULL, NULL, NULL);
         }
     }
     return 0;
 }
+
+int og_rasterize(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                 const double* t, const double* td, const float* q, const uint32_t* id,
+                 double* grid)
+{
+    return rasterize_into(g, pr, n, p, t, td, q, id, NULL, grid);
+}
+
+/* og_rasterize restricted to the n_sel rows rows[] (distinct): out[j][n_ticks] receives row
+ * rows[j] of the grid og_rasterize would produce, bit for bit.  row_slot: scratch of
+ * n_wires * n_imp entries. */
+int og_rasterize_rows(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                      const double* t, const double* td, const float* q, const uint32_t* id,
+                      int64_t n_sel, const int64_t* rows, int64_t* row_slot, double* out)
+{
+    const int64_t n_rows = (int64_t)g->n_wires * g->n_imp;
+    for (int64_t r = 0; r < n_rows; ++r) row_slot[r] = -1;
+    for (int64_t j = 0; j < n_sel; ++j) {
+        if (rows[j] < 0 || rows[j] >= n_rows || row_slot[rows[j]] >= 0) return -2;
+        row_slot[rows[j]] = j;
+    }
+    return rasterize_into(g, pr, n, p, t, td, q, id, row_slot, out);
+}
+
+/* The terms of bin (r, k): for each depo whose window holds the bin, in depo order, its
+ * index, the value it adds, and the trial count, p_b and uniform of its binomial draw
+ * (n_e = -1 where it draws none).  At most max_out terms; returns their count, or -1. */
+int64_t og_bin_terms(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                     const double* t, const double* td, const float* q, const uint32_t* id,
+                     int64_t r, int64_t k, int64_t max_out, int64_t* idx, double* val,
+                     double* n_e, double* pb, double* u)
+{
+    double wpr, wtk;
+    og_consts c = make_consts(g, pr);
+    const uint32_t key[2] = {(uint32_t)pr->seed, (uint32_t)(pr->seed >> 32)};
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        og_patch pt = prepare_patch(g, pr, &c, p[i], t[i], td[i], q[i]);
+        const og_depo* d = &pt.d;
+        if (!d->ok || !(d->qatt > 0.0)) continue;
+        if (r < d->r_lo || r > d->r_hi || k < d->k_lo || k > d->k_hi) continue;
+        if (m >= max_out) return -1;
+        if (patch_weights(g, pr, d, r, r, k, k, &wpr, &wtk)) return -1;
+        idx[m] = i;
+        val[m] = bin_value(pr, &pt, wpr, wtk, r, k, id[i], key, &n_e[m], &pb[m], &u[m]);
+        ++m;
+    }
+    return m;
+}
+
+/* og_rasterize on n_threads host threads (OpenMP; 0: the runtime's default), bit for bit
+ * the same grid: the depos' drift and windows are prepared in parallel, then each thread
+ * fills whole bands of rows, adding every depo that reaches the band in depo order, so that
+ * every bin sums its terms in the same order as the serial loop (no reduction). */
+int og_rasterize_mt(const og_geom* g, const og_params* pr, int64_t n, const double* p,
+                    const double* t, const double* td, const float* q, const uint32_t* id,
+                    int n_threads, og_patch* scratch, double* grid)
+{
+    og_consts c = make_consts(g, pr);
+    const int64_t nt = g->n_ticks, n_rows = (int64_t)g->n_wires * g->n_imp;
+    const uint32_t key[2] = {(uint32_t)pr->seed, (uint32_t)(pr->seed >> 32)};
+    const int64_t band = 32;
+    const int64_t n_bands = (n_rows + band - 1) / band;
+    int rc = 0;
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for num_threads(n_threads) schedule(static)
+    for (int64_t i = 0; i < n; ++i) scratch[i] = prepare_patch(g, pr, &c, p[i], t[i], td[i], q[i]);
+#pragma omp parallel num_threads(n_threads)
+    {
+        double wp[OG_MAXB], wt[OG_MAXB];
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t b = 0; b < n_bands; ++b) {
+            const int64_t b0 = b * band, b1 = (b0 + band - 1 < n_rows) ? b0 + band - 1 : n_rows - 1;
+            for (int64_t i = 0; i < n; ++i) {
+                const og_patch* pt = &scratch[i];
+                const og_depo* d = &pt->d;
+                if (!d->ok || !(d->qatt > 0.0)) continue;
+                if (d->r_hi < b0 || d->r_lo > b1) continue;
+                const int64_t r0 = d->r_lo > b0 ? d->r_lo : b0;
+                const int64_t r1 = d->r_hi < b1 ? d->r_hi : b1;
+                if (patch_weights(g, pr, d, r0, r1, d->k_lo, d->k_hi, wp, wt)) {
+#pragma omp atomic write
+                    rc = -1;
+                    continue;
+                }
+                for (int64_t r = r0; r <= r1; ++r) {
+                    double* row = grid + r * nt;
+                    for (int64_t k = d->k_lo; k <= d->k_hi; ++k)
+                        row[k] += bin_value(pr, pt, wp[r - r0], wt[k - d->k_lo], r, k, id[i],
+                                            key, NULL, NULL, NULL);
+                }
+            }
+        }
+    }
+    return rc;
+}
+
+/* Size of one og_rasterize_mt scratch entry, for the caller's allocation. */
+int64_t og_patch_bytes(void) { return (int64_t)sizeof(og_patch); }
 
 /* a7, per-depo part: given dS = dL/dS (FP64 grid), the gradients of L with respect to
  * each depo's charge Q, pitch position p, time t, sigma_L [mm], sigma_T [mm] (mean path,
