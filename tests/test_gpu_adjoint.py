@@ -3,7 +3,8 @@
 The oracle's adjoint is pinned on CPU (finite differences, dot-product identity, torch
 autograd); here the GPU gradients must match it per output with relative L2 <= 1e-5 and
 max |err| <= 1e-4 x peak.  The three global sums (dL/dD_L, dL/dD_T, dL/dtau) add up
-terms of both signs over every depo, so they are compared with a relative error of 1e-4.
+terms of both signs over every depo: each is held to 1e-5 x the sum of its terms' magnitudes
+(1e-5 per term, times the sum's condition number; see gradcheck.py).
 """
 import dataclasses
 
@@ -13,11 +14,12 @@ import pytest
 from oracle import oracle as O
 from paper_2104_08265_gb300 import synth as S
 
+from gradcheck import assert_globals_close
+
 pytestmark = pytest.mark.gpu
 
 REL_L2 = 1e-5
 MAX_PEAK = 1e-4
-GLOBAL_REL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -66,12 +68,10 @@ def test_convolve_adjoint_matches_oracle(W, shape):
     assert_close(dR.cpu().numpy(), rdR, what="dR %s" % (shape,))
 
 
-def _grads_close(got, ref, what):
+def _grads_close(got, ref, what, prm, depos):
     for k in ("q", "p", "t", "sigma_L", "sigma_T"):
         assert_close(got[k].cpu().numpy(), ref[k], what="%s %s" % (what, k))
-    for k in ("DL", "DT", "lifetime"):
-        a, b = float(got[k].cpu()), float(ref[k])
-        assert abs(a - b) <= GLOBAL_REL * abs(b), (what, k, a, b)
+    assert_globals_close(got, ref, prm, depos, what)
 
 
 def test_rasterize_adjoint_matches_oracle(W):
@@ -84,7 +84,7 @@ def test_rasterize_adjoint_matches_oracle(W):
     pl = plane_for(W, g, prm, S.make_response(g, kind))
     got = pl.rasterize_adjoint(W.DeviceDepos.from_host(d), torch.from_numpy(dS).cuda())
     ref = O.depo_grads(g, prm, d, dS.astype(np.float64))
-    _grads_close(got, ref, "rasterize_adjoint")
+    _grads_close(got, ref, "rasterize_adjoint", prm, d)
 
 
 def _oracle_backward(g, prm, R, d, G):
@@ -111,7 +111,7 @@ def test_run_backward_matches_oracle(W, name):
     G = (M - M_target).contiguous()
     got = pl.backward(dd, G, want_resp=True)
     ref, rdR = _oracle_backward(g, prm, R, d, G.cpu().numpy().astype(np.float64))
-    _grads_close(got, ref, name)
+    _grads_close(got, ref, name, prm, d)
     assert_close(got["response"].cpu().numpy(), rdR, what=name + " dR")
 
 
@@ -167,7 +167,7 @@ def test_backward_reusing_the_forward_spectra_matches_oracle(W):
     pl.run(dd)
     got = pl.backward(dd, G, want_resp=True)
     ref, rdR = _oracle_backward(g, prm, R, d, G.cpu().numpy().astype(np.float64))
-    _grads_close(got, ref, "reused spectra")
+    _grads_close(got, ref, "reused spectra", prm, d)
     assert_close(got["response"].cpu().numpy(), rdR, what="reused spectra dR")
     for k in ("q", "p", "t", "sigma_L", "sigma_T", "response"):
         assert_close(got[k].cpu().numpy(), plain[k].cpu().numpy(), what="reuse vs recompute " + k)
@@ -191,21 +191,24 @@ def test_reuse_is_dropped_when_the_forward_does_not_apply(W):
     # 1. parameters changed after the run
     pl.run(dd)
     pl.set_params(other)
-    _grads_close(pl.backward(dd, G), _oracle_backward(g, other, R, d, Gh)[0], "params changed")
+    _grads_close(pl.backward(dd, G), _oracle_backward(g, other, R, d, Gh)[0], "params changed",
+                 other, d)
     # 2. a fluctuating forward: the backward stays on the mean path
     pl.set_params(dataclasses.replace(prm, fluctuate=1))
     pl.run(dd)
-    _grads_close(pl.backward(dd, G), _oracle_backward(g, prm, R, d, Gh)[0], "fluctuating run")
+    _grads_close(pl.backward(dd, G), _oracle_backward(g, prm, R, d, Gh)[0], "fluctuating run",
+                 prm, d)
     # 3. another compute call in between
     pl.set_params(prm)
     pl.run(dd)
     pl.convolve(torch.zeros((g.n_rows, g.n_ticks), dtype=torch.float32, device="cuda"))
-    _grads_close(pl.backward(dd, G), _oracle_backward(g, prm, R, d, Gh)[0], "call in between")
+    _grads_close(pl.backward(dd, G), _oracle_backward(g, prm, R, d, Gh)[0], "call in between",
+                 prm, d)
     # 4. other depo arrays (a copy holding other values)
     d2 = dataclasses.replace(d, q=(d.q * 0.5).astype(np.float32))
     pl.run(dd)
     _grads_close(pl.backward(W.DeviceDepos.from_host(d2), G),
-                 _oracle_backward(g, prm, R, d2, Gh)[0], "other depos")
+                 _oracle_backward(g, prm, R, d2, Gh)[0], "other depos", prm, d2)
 
 
 def test_autograd_backward_uses_its_own_forward_parameters(W):

@@ -7,7 +7,15 @@ mass at the mode and the ratio recurrence) with p_b from its FP32 patch weights,
 in FP64 from log-gamma, so the two pick the same count except where the uniform falls
 within FP32 rounding of a CDF step; there they differ by one.  Counts are integers, so the
 grid sums are exact and the grids are compared bin by bin: all equal but at most 1e-4 of
-the draws (depo x bin), and those by exactly one count (measured: about 1e-5).
+the draws (depo x bin), those by exactly one count, and each such bin must hold a draw of
+the oracle whose uniform lies within FP32 rounding of the CDF step between the two counts:
+    |u - F(x; N, p_b)| <= max over p' = p_b (1 +- 2^-20) of |F(x; N, p') - F(x; N, p_b)|
+                          + 2^-21,
+x the oracle's count (GPU one above) or x - 1 (GPU one below).  2^-20 bounds the relative
+error of the kernel's p_b (a product of two FP32 bin masses, each a few ulp from its FP64
+value: 16 ulp of FP32), and 2^-21 (4 ulp of 1) the kernel's FP32 sum of the mass function
+(compensated and re-anchored).  The full-size plane (960 x 6000, 100k depos, the bench's
+launch) is compared the same way on 48 sampled rows, which the oracle computes row by row.
 """
 import dataclasses
 
@@ -47,12 +55,44 @@ def draws(g, prm, d):
     return int(((w[ok, 1] - w[ok, 0] + 1) * (w[ok, 3] - w[ok, 2] + 1)).sum())
 
 
-def assert_counts_match(got, ref, n_draws, what):
+P_REL = 2.0 ** -20      # relative error bound of the kernel's FP32 p_b
+F_ABS = 2.0 ** -21      # error bound of the kernel's FP32 CDF sum
+
+
+def _near_step(F, n, p, x, u):
+    """Whether u lies within FP32 rounding (of p_b and of the CDF sum) of F(x; n, p)."""
+    f = F(x, n, p)
+    tol = max(abs(F(x, n, p * (1 + P_REL)) - f), abs(F(x, n, min(1.0, p * (1 - P_REL))) - f))
+    return abs(u - f) <= tol + F_ABS
+
+
+def assert_counts_match(got, ref, n_draws, what, g=None, prm=None, d=None, rows=None):
+    """Integer counts equal bin by bin but for at most 1e-4 of the draws, each off by one at a
+    CDF step of one of the bin's draws (checked through the oracle's terms of that bin when
+    g, prm and d are given; rows maps the compared rows to grid rows)."""
+    from scipy.stats import binom
     assert np.array_equal(got, np.round(got)), what
     diff = got - ref
     bad = np.count_nonzero(diff)
     assert np.abs(diff).max(initial=0) <= 1, what
     assert bad <= max(2, 1e-4 * n_draws), "%s: %d bins differ, %d draws" % (what, bad, n_draws)
+    if g is None:
+        return bad
+    F = lambda x, n, p: float(binom.cdf(x, n, p))
+    for i, k in np.argwhere(diff != 0):
+        r = int(rows[i]) if rows is not None else int(i)
+        t = O.bin_terms(g, prm, d, r, int(k))
+        up = diff[i, k] > 0
+        ok = False
+        for n_e, p, u, x in zip(t["n_e"], t["p"], t["u"], t["val"]):
+            if n_e < 0:
+                continue
+            step = x if up else x - 1            # the CDF step between the two counts
+            if step >= 0 and _near_step(F, int(n_e), p, int(step), u):
+                ok = True
+                break
+        assert ok, "%s: bin (%d, %d) differs by %+d, no draw at a CDF step: %s" % (
+            what, r, k, diff[i, k], {kk: v.tolist() for kk, v in t.items()})
     return bad
 
 
@@ -64,7 +104,8 @@ def test_binomial_grid_matches_oracle(W, renorm):
     got = rasterize(W, g, prm, d)
     ref = O.rasterize(g, prm, d)
     assert np.array_equal(ref, np.round(ref))
-    assert_counts_match(got, ref, draws(g, prm, d), "plane128-2k renormalize %d" % renorm)
+    assert_counts_match(got, ref, draws(g, prm, d), "plane128-2k renormalize %d" % renorm,
+                        g, prm, d)
     # not the normal approximation, and not the mean
     assert not np.array_equal(got, rasterize(W, g, dataclasses.replace(prm, fluctuate=1), d))
 
@@ -83,7 +124,7 @@ def test_binomial_small_charges_and_edge_cases(W):
                 id=np.arange(n, dtype=np.uint32))
     prm = S.DriftParams(fluctuate=2, seed=77, plane_id=2)
     assert_counts_match(rasterize(W, g, prm, d), O.rasterize(g, prm, d), draws(g, prm, d),
-                        "edge cases")
+                        "edge cases", g, prm, d)
 
 
 def test_binomial_large_variance_bins_take_the_normal_approximation(W):
@@ -160,6 +201,24 @@ def test_fluctuate_out_of_range_is_rejected(W):
     with pytest.raises(W.WcsimError) as e:
         W.Plane(g, S.DriftParams(fluctuate=3), np.zeros((g.n_imp, g.n_wires, g.n_ticks), np.complex64))
     assert e.value.status == W.EINVAL
+
+
+def test_binomial_full_size_plane_bin_by_bin(W):
+    """The 960 x 6000 plane with 100k depos, rasterized as the bench's forward does, against
+    the oracle on 48 sampled rows (every bin of those rows): equal integer counts but at
+    CDF steps, as above."""
+    wl = S.make_workload("plane960-100k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=2)
+    got = rasterize(W, g, prm, d)
+    rows = np.sort(np.random.default_rng(2101).choice(g.n_rows, 48, replace=False))
+    ref = O.rasterize_rows(g, prm, d, rows)
+    w = O.windows(g, prm, d)
+    ok = w[:, 0] >= 0
+    in_rows = sum(((w[ok, 0] <= r) & (r <= w[ok, 1])) * (w[ok, 3] - w[ok, 2] + 1) for r in rows)
+    n_draws = int(in_rows.sum())
+    assert n_draws > 20000 and ref.sum() > 0
+    assert_counts_match(got[rows], ref, n_draws, "full size", g, prm, d, rows)
 
 
 def test_binomial_full_size_plane_properties(W):
