@@ -105,19 +105,35 @@ def config(name, g, d, prm, extra=None):
 
 
 # ---------------------------------------------------------------- byte / flop models
-def stage_bytes(g, n_depos, mean_bins):
-    """Algorithmic (compulsory) bytes per launch of each forward stage.  The grid is cleared
-    inside rows_r2c as it is read (consume and clear), so after the first run the zero stage
-    moves nothing; the clearing writes are not counted in rows_r2c either."""
+DECISION_BYTES = 64        # one binned depo decision
+WEIGHT_SLOT_BYTES = 96     # its stored tick weights (24 floats)
+
+
+def stage_bytes(g, n_depos, mean_bins, fused=True):
+    """Algorithmic bytes per forward, by stage (summed over the launches of a stage).
+
+    fused (the default forward): prep = the depo binning (depos read; decisions and slots
+    written, read back and written in bucket order), no separate rasterization, rows_r2c =
+    the binned decisions and weights read once and the time-axis spectra written, wire_pass =
+    those spectra read, the response half-spectrum read and the wire-summed spectrum written.
+    plain: prep = 0 (the grid is cleared inside rows_r2c as it is read), rasterize = depos in
+    and 4 bytes per patch bin, rows_r2c = the grid read and its spectra written."""
     rows = g.n_rows
     nh = g.n_ticks // 2 + 1
-    return {
-        "zero": 0,
-        "rasterize": n_depos * (32 + 4 * mean_bins),
-        "rows_r2c": rows * g.n_ticks * 4 + rows * nh * 8,
-        "wire_pass": rows * nh * 8 + g.n_imp * g.n_wires * nh * 8 + g.n_wires * nh * 8,
+    spec = rows * nh * 8
+    out = {
+        "wire_pass": spec + g.n_imp * g.n_wires * nh * 8 + g.n_wires * nh * 8,
         "rows_c2r": g.n_wires * nh * 8 + g.n_wires * g.n_ticks * 4,
     }
+    if fused:
+        dec = DECISION_BYTES + 4
+        out.update({"prep": n_depos * (32 + dec + dec + DECISION_BYTES + WEIGHT_SLOT_BYTES),
+                    "rasterize": 0,
+                    "rows_r2c": n_depos * (DECISION_BYTES + WEIGHT_SLOT_BYTES) + spec})
+    else:
+        out.update({"prep": 0, "rasterize": n_depos * (32 + 4 * mean_bins),
+                    "rows_r2c": rows * g.n_ticks * 4 + spec})
+    return out
 
 
 def backward_stage_bytes(g, n_depos, mean_bins, reused=False):
@@ -160,8 +176,8 @@ def fft_flops(g):
     return fwd_rows + wire + mult + inv_rows
 
 
-STAGE_KERNEL = {"rows_r2c": "k_rows_r2c_direct", "wire_pass": "k_wire_warp",
-                "rasterize": "k_rasterize", "rows_c2r": "k_rows_c2r"}
+STAGE_KERNEL = {"rows_r2c": "k_rows_r2c_fused", "wire_pass": "k_wire_warp",
+                "rows_c2r": "k_rows_c2r"}
 
 
 def source_hash():
@@ -668,7 +684,8 @@ def run_gpu(args):
     avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     stages = {k: {"ms": avg[k], "GB/s": sb[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None,
                   "alg_bytes": sb[k]} for k in avg}
-    stages["zero"]["note"] = "no-op: the grid is cleared inside rows_r2c (consume and clear)"
+    stages["prep"]["note"] = "depo binning (decide, count, scan, fill)"
+    stages["rasterize"]["note"] = "inside rows_r2c (fused forward)"
     dom = max(avg, key=avg.get)
     ach = sb[dom] / (avg[dom] * 1e-3) / 1e9
     per_step = tot_ms / args.steps

@@ -202,6 +202,18 @@ wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
  * spectra.  enable = 0 (the default): the backward always recomputes.  Host-only. */
 wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* plane, int32_t enable);
 
+/* Forward variant of wcsim_run / wcsim_run_adc.  fused = 0 (the default): the flow of Sec.
+ * 2.1.1, rasterize and scatter-add into the plane's grid S, then Eq. 2 on the grid.
+ * fused = 1: the depos are binned by wire, and each time-axis transform CTA rasterizes the
+ * depos that reach its two grid rows straight into shared memory, so the grid is never
+ * written to device memory (this pays on sparse frames, where the plain transform would read
+ * a mostly empty grid; wcsim_plane_autotune times both).  Both give the same frame up to
+ * floating-point summation order.  The exact binomial (fluctuate = 2) always takes the plain
+ * flow.  The fused flow keeps depo binning scratch (about 230 bytes per depo), allocated by
+ * the first wcsim_run with more depos than before.  WCSIM_EINVAL for fused outside 0..1.
+ * Host-only. */
+wcsim_status wcsim_plane_set_forward(wcsim_plane* plane, int32_t fused);
+
 /* Choices and best times (ms) found by wcsim_plane_autotune. */
 typedef struct {
     int32_t time_radix[8];     /* radices of the time-axis FFT plan, in pass order, 0-padded */
@@ -210,11 +222,14 @@ typedef struct {
     int32_t depos_per_block;   /* rasterization CTA size: 32, 64 or 128 depos */
     int32_t candidates_timed;  /* configurations timed */
     float ms_rasterize, ms_rows, ms_wire;
+    int32_t forward_fused;     /* forward variant kept (wcsim_plane_set_forward) */
+    float ms_forward_plain, ms_forward_fused;   /* whole forward, each variant (0: not timed) */
 } wcsim_tune_report;
 
 /* Time the kernel variants of this plane on `depos` (DEVICE) and keep the fastest: the
  * rasterization CTA size, the radices and order of the time-axis FFT plan (the cheapest
- * plans with the fewest passes), the time-axis forward kernel and the wire-pass kernel.
+ * plans with the fewest passes), the time-axis forward kernel, the wire-pass kernel and the
+ * forward variant (plain or fused, wcsim_plane_set_forward).
  * Results are unchanged up to floating-point rounding order.  Synchronizes `stream`,
  * allocates temporary plan tables, overwrites the plane's scratch; report may be NULL. */
 wcsim_status wcsim_plane_autotune(wcsim_plane* plane, const wcsim_depos* depos, void* stream,

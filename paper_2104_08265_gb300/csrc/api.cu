@@ -57,7 +57,10 @@ bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
 }  // namespace
 
-constexpr int kStages = 5;       // forward: zero, rasterize, rows_r2c, wire_pass, rows_c2r
+constexpr int kStages = 5;       // forward: prep (zero grid or bin depos), rasterize,
+                                 // rows_r2c (with the rasterization when fused), wire_pass,
+                                 // rows_c2r
+constexpr int kMarks = 32;       // forward timeline events
 constexpr int kBwdStages = 7;    // backward: zero, rasterize, r2c(S), r2c(G), wire adjoint,
                                  // c2r of dL/dS, depo adjoint
 
@@ -94,8 +97,19 @@ struct wcsim_plane {
     wcsim_drift_params fwd_prm = {};
     bool wire_block = false;    // autotuned: use the block-level wire pass even if the warp one fits
     int32_t kd = 32;            // depos per rasterization CTA (the autotuner may change it)
+    // forward with rasterization fused into the time-axis transform: depo binning scratch,
+    // and the impact positions per wire-pass launch (the time-axis spectra of that many
+    // impact positions are alive at a time)
+    bool fused = false;
+    bool fused_fits = false;    // the fused transform fits shared memory for the time plan
+    FusedScratch fs;
     bool timing = false;
-    cudaEvent_t ev[kStages + 1] = {};
+    // forward stage timeline: events, and spans (kind, begin event, end event) between them
+    cudaEvent_t ev[kMarks] = {};
+    int32_t tl_n = 0;           // events recorded
+    int32_t tl_last = -1;       // last event of the sequential marks on the caller's stream
+    int32_t sp_kind[kMarks] = {}, sp_b[kMarks] = {}, sp_e[kMarks] = {};
+    int32_t sp_n = 0;
     cudaEvent_t evb[kBwdStages + 1] = {};
     bool ev_valid = false;
     bool bwd_recorded = false;
@@ -216,6 +230,12 @@ void plane_free(wcsim_plane* pl)
     cudaFree(pl->bgrid);
     cudaFree(pl->bshat);
     cudaFree(pl->bmt);
+    cudaFree(pl->fs.dec);
+    cudaFree(pl->fs.pos);
+    cudaFree(pl->fs.cnt);
+    cudaFree(pl->fs.off);
+    cudaFree(pl->fs.sorted);
+    cudaFree(pl->fs.wts);
     if (pl->ev_valid) {
         for (auto& e : pl->ev) cudaEventDestroy(e);
         for (auto& e : pl->evb) cudaEventDestroy(e);
@@ -223,9 +243,40 @@ void plane_free(wcsim_plane* pl)
     delete pl;
 }
 
+// Forward timeline.  tl_record records an event on s (index, or -1 when timing is off or
+// the events are used up); tl_span adds a span of stage kind k between two events.
+// Stage kinds: 0 prep, 1 rasterize, 2 rows_r2c, 3 wire_pass, 4 rows_c2r; spans of one kind
+// are summed by wcsim_plane_stage_times.
+inline int tl_record(wcsim_plane* pl, cudaStream_t s)
+{
+    if (!pl->timing || pl->tl_n >= kMarks) return -1;
+    cudaEventRecord(pl->ev[pl->tl_n], s);
+    return pl->tl_n++;
+}
+
+inline void tl_span(wcsim_plane* pl, int kind, int b, int e)
+{
+    if (b < 0 || e < 0 || pl->sp_n >= kMarks) return;
+    pl->sp_kind[pl->sp_n] = kind;
+    pl->sp_b[pl->sp_n] = b;
+    pl->sp_e[pl->sp_n] = e;
+    ++pl->sp_n;
+}
+
+// Sequential marks on one stream: mark(pl, 0) starts a forward's timeline, mark(pl, i > 0)
+// closes a span of stage kind i - 1 since the previous mark.
 inline void mark(wcsim_plane* pl, int i, cudaStream_t s)
 {
-    if (pl->timing) cudaEventRecord(pl->ev[i], s);
+    if (!pl->timing) return;
+    if (i == 0) {
+        pl->tl_n = 0;
+        pl->sp_n = 0;
+        pl->tl_last = tl_record(pl, s);
+        return;
+    }
+    const int e = tl_record(pl, s);
+    tl_span(pl, i - 1, pl->tl_last, e);
+    pl->tl_last = e;
 }
 
 inline void markb(wcsim_plane* pl, int i, cudaStream_t s)
@@ -236,22 +287,99 @@ inline void markb(wcsim_plane* pl, int i, cudaStream_t s)
     }
 }
 
-wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaStream_t s,
-                         int first_mark)
+// Eq. 2 after the rasterization: the time-axis transform of every grid row (r2c(s)), the
+// wire pass and the inverse time FFT, one launch each on s, with timeline spans around them.
+template <class R2C>
+wcsim_status convolve_stages(wcsim_plane* pl, R2C r2c, float* wave, cudaStream_t s)
+{
+    const ConvDims& d = pl->dims;
+    cudaError_t e;
+    int b = tl_record(pl, s);
+    if ((e = r2c(s))) return cuda_fail(e, "rows_r2c launch");
+    int t = tl_record(pl, s);
+    tl_span(pl, 2, b, t);
+    if (pl->tw_warp && !pl->wire_block)
+        e = launch_wire_warp(d, pl->tw_warp, pl->shat, pl->H, pl->mt, pl->flags, s);
+    else
+        e = launch_wire_pass(d, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s);
+    if (e) return cuda_fail(e, "wire_pass launch");
+    b = t;
+    t = tl_record(pl, s);
+    tl_span(pl, 3, b, t);
+    if ((e = launch_rows_c2r(d, pl->pt, pl->mt, wave, s))) return cuda_fail(e, "rows_c2r launch");
+    tl_span(pl, 4, t, tl_record(pl, s));
+    return WCSIM_OK;
+}
+
+wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaStream_t s)
 {
     pl->fwd_valid = false;              // the spectra are about to be those of `grid`
-    cudaError_t e;
-    if ((e = launch_rows_r2c(pl->dims, pl->pt, grid, pl->shat, pl->flags, s)))
-        return cuda_fail(e, "rows_r2c launch");
-    mark(pl, first_mark, s);
-    if (pl->tw_warp && !pl->wire_block)
-        e = launch_wire_warp(pl->dims, pl->tw_warp, pl->shat, pl->H, pl->mt, pl->flags, s);
-    else
-        e = launch_wire_pass(pl->dims, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s);
-    if (e) return cuda_fail(e, "wire_pass launch");
-    mark(pl, first_mark + 1, s);
-    if ((e = launch_rows_c2r(pl->dims, pl->pt, pl->mt, wave, s))) return cuda_fail(e, "rows_c2r launch");
-    mark(pl, first_mark + 2, s);
+    const ConvDims d = pl->dims;
+    const FftPlan pt = pl->pt;
+    int* flags = pl->flags;
+    float2* shat = pl->shat;
+    auto r2c = [&](cudaStream_t strm) {
+        return launch_rows_r2c(d, pt, grid, shat, flags, strm);
+    };
+    return convolve_stages(pl, r2c, wave, s);
+}
+
+// Binning scratch for n depos (grown, never shrunk; allocates only when n exceeds it).
+wcsim_status fused_reserve(wcsim_plane* pl, int64_t n)
+{
+    FusedScratch& f = pl->fs;
+    if (n <= f.cap) return WCSIM_OK;
+    cudaFree(f.dec);
+    cudaFree(f.pos);
+    cudaFree(f.sorted);
+    cudaFree(f.wts);
+    f.dec = f.sorted = nullptr;
+    f.pos = nullptr;
+    f.wts = nullptr;
+    f.cap = 0;
+    const int64_t cap = (n + 4095) & ~(int64_t)4095;
+    cudaError_t e = cudaMalloc(&f.dec, (size_t)cap * kDecisionBytes);
+    if (!e) e = cudaMalloc(&f.sorted, (size_t)cap * kDecisionBytes);
+    if (!e) e = cudaMalloc(&f.pos, (size_t)cap * sizeof(int32_t));
+    if (!e) e = cudaMalloc(&f.wts, (size_t)cap * kFusedSlots * sizeof(float));
+    if (e) return cuda_fail(e, "depo binning scratch allocation");
+    f.cap = cap;
+    return WCSIM_OK;
+}
+
+// The fused forward applies: not the exact binomial (its draws stay in the plain
+// rasterizer), depo counts that fit the binning's 32-bit slots.
+bool fused_applies(const wcsim_plane* pl, const wcsim_depos* depos)
+{
+    return pl->fused && pl->fused_fits && pl->prm.fluctuate != 2 &&
+           depos->n < ((int64_t)1 << 31);
+}
+
+// wcsim_run's forward with the rasterization inside the time-axis transform (the grid is
+// never written): depo binning, then convolve_stages with the fused transform.
+wcsim_status fused_forward(wcsim_plane* pl, const wcsim_depos* depos, void* out, cudaStream_t s)
+{
+    wcsim_status st = fused_reserve(pl, depos->n);
+    if (st) return st;
+    const ConvDims& d = pl->dims;
+    RasterConsts c = make_consts(pl);
+    cudaError_t e = launch_bin_depos(c, depo_arrays(depos), d.n_imp, d.n_w, pl->fs, pl->flags, s);
+    if (e) return cuda_fail(e, "depo binning launch");
+    mark(pl, 1, s);
+    const FftPlan pt = pl->pt;
+    const FusedScratch fs = pl->fs;
+    float2* shat = pl->shat;
+    auto r2c = [&](cudaStream_t strm) {
+        return launch_rows_r2c_fused(d, pt, c, fs, shat, strm);
+    };
+    st = convolve_stages(pl, r2c, static_cast<float*>(out), s);
+    if (st) return st;
+    pl->fwd_valid = false;
+    if (pl->reuse_fwd && pl->prm.fluctuate == 0) {
+        pl->fwd_valid = true;           // shat: the mean-path spectra of these depos
+        pl->fwd_depos = *depos;
+        pl->fwd_prm = pl->prm;
+    }
     return WCSIM_OK;
 }
 
@@ -415,6 +543,12 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     WC_TRY(cudaMalloc(&pl->shat, n_rows * cols * sizeof(float2)), "spectrum allocation");
     WC_TRY(cudaMalloc(&pl->mt, (size_t)d.n_w * cols * sizeof(float2)), "spectrum allocation");
     WC_TRY(cudaMalloc(&pl->flags, sizeof(int)), "flag allocation");
+    WC_TRY(cudaMalloc(&pl->fs.cnt, (size_t)(d.n_w + 1) * sizeof(int32_t)), "bin count allocation");
+    WC_TRY(cudaMalloc(&pl->fs.off, (size_t)(d.n_w + 2) * sizeof(int32_t)), "bin offset allocation");
+    WC_TRY(cudaMemsetAsync(pl->fs.cnt, 0, (size_t)(d.n_w + 1) * sizeof(int32_t), s), "bin count reset");
+    pl->fused_fits = fused_supported(pl->pt);
+    // forward variant; WCSIM_FORWARD=fused|plain overrides the default (plain)
+    if (const char* v = getenv("WCSIM_FORWARD")) pl->fused = strcmp(v, "fused") == 0;
     WC_TRY(cudaMemsetAsync(pl->flags, 0, sizeof(int), s), "flag reset");
     WC_TRY(launch_make_hermitian(d, (const float2*)resp_c64, pl->H,
                                  (float)(1.0 / ((double)n_fw * (double)n_ft)), s),
@@ -460,11 +594,10 @@ wcsim_status wcsim_rasterize(wcsim_plane* pl, const wcsim_depos* depos, float* g
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
     mark(pl, 0, s);
-    mark(pl, 1, s);
     pl->fwd_valid = false;
     cudaError_t e = launch_rasterize(make_consts(pl), depo_arrays(depos), grid, pl->flags, s);
     if (e) return cuda_fail(e, "rasterize launch");
-    for (int i = 2; i <= kStages; ++i) mark(pl, i, s);
+    mark(pl, 2, s);
     return WCSIM_OK;
 }
 
@@ -476,9 +609,7 @@ wcsim_status wcsim_convolve(wcsim_plane* pl, const float* grid, float* wave, voi
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
     mark(pl, 0, s);
-    mark(pl, 1, s);
-    mark(pl, 2, s);
-    return do_convolve(pl, grid, wave, s, 3);
+    return do_convolve(pl, grid, wave, s);
 }
 
 // wcsim_run and wcsim_run_adc: rasterize into the plane's grid, then convolve (with the
@@ -497,6 +628,18 @@ static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* o
     const ConvDims& d = pl->dims;
     mark(pl, 0, s);
     cudaError_t e = cudaSuccess;
+    if (fused_applies(pl, depos)) {
+        with_noise(pl, pl->dims);
+        if (adc) {
+            pl->dims.adc_gain = pl->adc_gain;
+            pl->dims.adc_pedestal = pl->adc_pedestal;
+            pl->dims.adc_max = pl->adc_max;
+        }
+        st = fused_forward(pl, depos, out, s);
+        pl->dims.noise_amp = nullptr;
+        pl->dims.adc_max = 0;
+        return st;
+    }
     if (!pl->grid_clean) {
         e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
         if (e) return cuda_fail(e, "grid reset");
@@ -515,7 +658,7 @@ static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* o
         pl->dims.adc_pedestal = pl->adc_pedestal;
         pl->dims.adc_max = pl->adc_max;
     }
-    st = do_convolve(pl, pl->grid, static_cast<float*>(out), s, 3);
+    st = do_convolve(pl, pl->grid, static_cast<float*>(out), s);
     pl->dims.clear_input = 0;
     pl->dims.noise_amp = nullptr;
     pl->dims.adc_max = 0;
@@ -775,6 +918,7 @@ wcsim_status wcsim_plane_autotune(wcsim_plane* pl, const wcsim_depos* depos, voi
         if (bi >= 0 && !err) {
             cudaFree(pl->tw_t);
             pl->pt = bp;
+            pl->fused_fits = fused_supported(pl->pt);
             pl->tw_t = btw;
         } else {
             cudaFree(btw);
@@ -807,6 +951,36 @@ wcsim_status wcsim_plane_autotune(wcsim_plane* pl, const wcsim_depos* depos, voi
         pl->wire_block = !(warp <= block);
         rep.wire_variant = pl->wire_block ? 1 : 0;
         rep.ms_wire = pl->wire_block ? block : warp;
+    }
+    // 5. forward variant: the whole wcsim_run, plain and fused (into a temporary frame)
+    rep.forward_fused = pl->fused ? 1 : 0;
+    if (!err && pl->fused_fits && pl->prm.fluctuate != 2 && depos->n < ((int64_t)1 << 31)) {
+        float* wave = nullptr;
+        err = cudaMalloc(&wave, (size_t)d.n_w * d.n_t * sizeof(float));
+        if (!err) {
+            const bool keep_timing = pl->timing;
+            pl->timing = false;
+            wcsim_status st2 = WCSIM_OK;
+            auto fwd = [&](bool fused) {
+                pl->fused = fused;
+                return [&, fused]() -> cudaError_t {
+                    pl->fused = fused;
+                    st2 = wcsim_run(pl, depos, wave, stream);
+                    return st2 == WCSIM_OK ? cudaSuccess : cudaErrorLaunchFailure;
+                };
+            };
+            rep.ms_forward_plain = time_it(fwd(false));
+            if (!err) rep.ms_forward_fused = time_it(fwd(true));
+            pl->fused = !err && rep.ms_forward_fused < rep.ms_forward_plain;
+            rep.forward_fused = pl->fused ? 1 : 0;
+            pl->timing = keep_timing;
+            cudaFree(wave);
+            if (st2 != WCSIM_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st2;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -881,6 +1055,15 @@ wcsim_status wcsim_plane_set_noise(wcsim_plane* pl, const float* amp, int32_t n_
     return WCSIM_OK;
 }
 
+wcsim_status wcsim_plane_set_forward(wcsim_plane* pl, int32_t fused)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (fused != 0 && fused != 1) return fail(WCSIM_EINVAL, "fused must be 0 or 1 (got %d)", fused);
+    pl->fused = fused != 0;
+    pl->fwd_valid = false;
+    return WCSIM_OK;
+}
+
 wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* pl, int32_t enable)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
@@ -909,14 +1092,18 @@ wcsim_status wcsim_plane_stage_times(wcsim_plane* pl, float* ms, int32_t n)
     if (!pl->timing) return fail(WCSIM_EINVAL, "timing is not enabled on this plane");
     DeviceGuard dg(pl->device);
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
-    cudaError_t e = cudaEventSynchronize(pl->ev[kStages]);
-    if (e) return cuda_fail(e, "event synchronize");
-    for (int i = 0; i < n && i < kStages; ++i) {
+    cudaError_t e = cudaSuccess;
+    float sum[kStages] = {};
+    for (int i = 0; i < pl->tl_n; ++i)
+        if ((e = cudaEventSynchronize(pl->ev[i]))) return cuda_fail(e, "event synchronize");
+    for (int i = 0; i < pl->sp_n; ++i) {
         float t = 0.f;
-        e = cudaEventElapsedTime(&t, pl->ev[i], pl->ev[i + 1]);
-        if (e) return cuda_fail(e, "event elapsed time");
-        ms[i] = t;
+        if ((e = cudaEventElapsedTime(&t, pl->ev[pl->sp_b[i]], pl->ev[pl->sp_e[i]])))
+            return cuda_fail(e, "event elapsed time");
+        const int k = pl->sp_kind[i];
+        if (k >= 0 && k < kStages) sum[k] += t;
     }
+    for (int i = 0; i < n && i < kStages; ++i) ms[i] = sum[i];
     for (int i = 0; i < kBwdStages && kStages + i < n; ++i) {
         float t = 0.f;
         if (pl->bwd_recorded) {

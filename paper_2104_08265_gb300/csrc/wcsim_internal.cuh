@@ -187,6 +187,46 @@ cudaError_t launch_rows_c2r(const ConvDims& d, const FftPlan& pt, const float2* 
 cudaError_t launch_rows_c2r_batch(const ConvDims& d, const FftPlan& pt, const float2* mt,
                                   const WavePtrs& waves, int n_ev, cudaStream_t s);
 
+// ------------------------------------------------------------------ fused rasterization
+// Rasterization inside the time-axis transform: depos are binned by the first wire their rows
+// reach, and each transform CTA rasterizes the depos of its wire's neighbourhood straight into
+// its shared-memory rows, so that the grid S is never written.
+struct Decision;
+constexpr size_t kDecisionBytes = 64;   // sizeof(Decision)
+constexpr int kFusedSpan = 4;     // a depo reaching over more wires goes to the "wide" bucket
+constexpr int kFusedSlots = 24;   // tick weights stored per binned depo (6 four-tick groups)
+
+// Scratch of the binning pass, cap depos.
+struct FusedScratch {
+    Decision* dec = nullptr;      // [cap] decisions in depo order
+    int32_t* pos = nullptr;       // [cap] slot within its bucket, -1 if the depo adds nothing
+    int32_t* cnt = nullptr;       // [n_w + 1] bucket counts (zero between calls)
+    int32_t* off = nullptr;       // [n_w + 2] bucket offsets, off[n_w + 1] = binned depos
+    Decision* sorted = nullptr;   // [cap] decisions in bucket order
+    float* wts = nullptr;         // [cap][kFusedSlots] tick weights of `sorted`
+    int64_t cap = 0;
+};
+
+// What the transform reads of the binning (passed by value).
+struct FusedBins {
+    const Decision* sorted;
+    const float* wts;
+    const int32_t* off;
+    int32_t n_w;                  // index of the wide bucket
+    int64_t cap;                  // entries of sorted / wts
+};
+
+// The fused transform fits shared memory for this time-axis plan.
+bool fused_supported(const FftPlan& pt);
+// Decide and bin every depo (three launches); c.depos_per_block is ignored.
+cudaError_t launch_bin_depos(const RasterConsts& c, const DepoArrays& d, int n_imp, int n_w,
+                             const FusedScratch& s, int* flags, cudaStream_t st);
+// Rasterize the binned depos into every grid row (two rows of one wire per CTA) and
+// transform the rows; writes the half spectra to shat (blocked [n_imp][nkb][n_w][4]) as the
+// plain transform does.
+cudaError_t launch_rows_r2c_fused(const ConvDims& d, const FftPlan& pt, const RasterConsts& c,
+                                  const FusedScratch& s, float2* shat, cudaStream_t st);
+
 // Streaming multiprocessors of the current device (cached).
 int sm_count();
 

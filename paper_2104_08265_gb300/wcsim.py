@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "wcsim.h")
 OK, EINVAL, ESHAPE, ENOMEM, ECUDA, ETIMEOUT, EDEVICE_CHECK = range(7)
 STATUS_NAMES = {0: "WCSIM_OK", 1: "WCSIM_EINVAL", 2: "WCSIM_ESHAPE", 3: "WCSIM_ENOMEM",
                 4: "WCSIM_ECUDA", 5: "WCSIM_ETIMEOUT", 6: "WCSIM_EDEVICE_CHECK"}
-STAGES = ("zero", "rasterize", "rows_r2c", "wire_pass", "rows_c2r")
+STAGES = ("prep", "rasterize", "rows_r2c", "wire_pass", "rows_c2r")
 BWD_STAGES = ("bwd_zero", "bwd_rasterize", "bwd_r2c_S", "bwd_r2c_G", "bwd_wire_adjoint",
               "bwd_c2r_dS", "bwd_depo_adjoint")
 
@@ -67,7 +67,9 @@ class CTuneReport(ctypes.Structure):
     _fields_ = [("time_radix", ctypes.c_int32 * 8), ("rows_variant", ctypes.c_int32),
                 ("wire_variant", ctypes.c_int32), ("depos_per_block", ctypes.c_int32),
                 ("candidates_timed", ctypes.c_int32), ("ms_rasterize", ctypes.c_float),
-                ("ms_rows", ctypes.c_float), ("ms_wire", ctypes.c_float)]
+                ("ms_rows", ctypes.c_float), ("ms_wire", ctypes.c_float),
+                ("forward_fused", ctypes.c_int32), ("ms_forward_plain", ctypes.c_float),
+                ("ms_forward_fused", ctypes.c_float)]
 
 _lib = None
 
@@ -106,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_run_adc": [vp, P(CDepos), vp, vp],
         "wcsim_plane_set_digitizer": [vp, ctypes.c_float, ctypes.c_float, i32],
         "wcsim_plane_set_reuse_forward": [vp, i32],
+        "wcsim_plane_set_forward": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -326,7 +329,8 @@ class Plane:
         return {"time_radix": [x for x in r.time_radix if x], "rows_variant": r.rows_variant,
                 "wire_variant": r.wire_variant, "depos_per_block": r.depos_per_block,
                 "candidates_timed": r.candidates_timed, "ms_rasterize": r.ms_rasterize,
-                "ms_rows": r.ms_rows, "ms_wire": r.ms_wire}
+                "ms_rows": r.ms_rows, "ms_wire": r.ms_wire, "forward_fused": r.forward_fused,
+                "ms_forward_plain": r.ms_forward_plain, "ms_forward_fused": r.ms_forward_fused}
 
     def windows(self, depos: DeviceDepos, stream=None):
         import torch
@@ -363,6 +367,12 @@ class Plane:
         and parameters (the depos must not change in between); see
         wcsim_plane_set_reuse_forward."""
         check(lib().wcsim_plane_set_reuse_forward(self._h, 1 if enable else 0))
+
+    def set_forward(self, fused: bool = True):
+        """Forward variant of run(): the rasterization fused into the time-axis transform
+        (the grid never written), or the plain flow through the grid; see
+        wcsim_plane_set_forward."""
+        check(lib().wcsim_plane_set_forward(self._h, 1 if fused else 0))
 
     def set_timing(self, enable: bool = True):
         check(lib().wcsim_plane_set_timing(self._h, 1 if enable else 0))
