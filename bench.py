@@ -1,13 +1,17 @@
 """Throughput of the LArTPC signal-simulation hot path on GB300.
 
-One step = one whole forward pass (zero grid, drift + rasterize + fluctuate + scatter-add,
-time-axis FFT, wire-axis FFT x response x sum over impacts x inverse, time-axis inverse
-FFT) over the 960-wire x 6000-tick plane with 100,000 depos (fluctuation on).
+One step = one whole forward pass (drift + rasterize + fluctuate + scatter-add, time-axis
+FFT, wire-axis FFT x response x sum over impacts x inverse, time-axis inverse FFT; the
+forward variant the autotuner keeps) over the 960-wire x 6000-tick plane with 100,000 depos
+(fluctuation on).
 
 Prints one JSON line.  `value` is depos/s of the device-resident step; `e2e` is the same
 through the public API with the depos copied from pinned host memory and the waveforms
-copied back inside the timed region.  `--impl reference` times the FP64 CPU oracle (the
-only place besides the cpu_baseline leg where this script runs it).
+copied back inside the timed region; `error_vs_fp64` compares the bench frame with the FP64
+oracle's.  Further legs: the fit step (forward + backward), Eq. 1's noise, ADC readout, the
+rasterization variants, the 64-event batch and the three-plane 1,000,000-depo event.  The
+headline numbers close the line (`summary`).  `--impl reference` times the FP64 CPU oracle
+(the only place besides the cpu_baseline legs where this script runs it).
 """
 from __future__ import annotations
 
@@ -50,6 +54,8 @@ def parse():
                          "with the rasterization variants")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-event batched run (wcsim_batch_run vs 64 wcsim_run calls)")
+    ap.add_argument("--no-event", action="store_true",
+                    help="skip the three-plane 1,000,000-depo event")
     ap.add_argument("--soak-s", type=float, default=0.5,
                     help="untimed load before the timed loop, so the clock sampler sees the GPU busy")
     ap.add_argument("--write-traffic", nargs="+", metavar="NCU_REP",
@@ -94,14 +100,12 @@ def workload(name):
     return wl, g, prm, kind, d
 
 
-def config(name, g, d, prm, extra=None):
-    c = {"workload": name, "n_wires": g.n_wires, "n_imp": g.n_imp, "n_ticks": g.n_ticks,
-         "pitch_mm": g.pitch_mm, "tick_us": g.tick_us, "n_depos": len(d),
-         "fluctuate": prm.fluctuate, "l2": "flushed between timed steps (256 MB write); "
-         "response + grid working set 690 MB > L2"}
-    if extra:
-        c.update(extra)
-    return c
+def config(name, g, d, prm):
+    """The workload, identical in both arms of the benchmark."""
+    return {"workload": name, "n_wires": g.n_wires, "n_imp": g.n_imp, "n_ticks": g.n_ticks,
+            "pitch_mm": g.pitch_mm, "tick_us": g.tick_us, "n_depos": len(d),
+            "fluctuate": prm.fluctuate, "l2": "flushed between timed steps (256 MB write); "
+            "response + grid working set 690 MB > L2"}
 
 
 # ---------------------------------------------------------------- byte / flop models
@@ -109,7 +113,7 @@ DECISION_BYTES = 64        # one binned depo decision
 WEIGHT_SLOT_BYTES = 96     # its stored tick weights (24 floats)
 
 
-def stage_bytes(g, n_depos, mean_bins, fused=True):
+def stage_bytes(g, n_depos, mean_bins, fused=False):
     """Algorithmic bytes per forward, by stage (summed over the launches of a stage).
 
     fused (the default forward): prep = the depo binning (depos read; decisions and slots
@@ -176,8 +180,10 @@ def fft_flops(g):
     return fwd_rows + wire + mult + inv_rows
 
 
-STAGE_KERNEL = {"rows_r2c": "k_rows_r2c_fused", "wire_pass": "k_wire_warp",
-                "rows_c2r": "k_rows_c2r"}
+STAGE_KERNEL = {"rows_r2c": "k_rows_r2c_direct", "wire_pass": "k_wire_warp",
+                "rasterize": "k_rasterize", "rows_c2r": "k_rows_c2r"}
+STAGE_KERNEL_FUSED = {"rows_r2c": "k_rows_r2c_fused", "wire_pass": "k_wire_warp",
+                      "rows_c2r": "k_rows_c2r"}
 
 
 def source_hash():
@@ -216,13 +222,11 @@ def write_traffic(reps):
     rec = {"_about": "DRAM bytes (read + write) per launch, mean over the captured launches, "
                      "from ncu --set full captures of the 960-wire x 6000-tick plane with 100k "
                      "depos; valid only while the CUDA sources hash to source_sha256.",
-           "capture": ("CMD='python bench.py --steps 2 --warmup 1 --no-autotune --no-batch "
-                       "--no-cpu-baseline --no-cufft --no-e2e --no-noise --soak-s 0'; ncu --set full "
-                       "--import-source no --clock-control none -k 'regex:k_rasterize|"
-                       "k_rows_r2c_direct|k_wire_warp|k_rows_c2r' -s 4 -c 4 -o fwd $CMD; ncu --set "
-                       "full --import-source no --clock-control none -k 'regex:k_wire_adjoint|"
-                       "k_rows_c2r_grid|k_depo_adjoint' -c 4 -o bwd $CMD; then "
-                       "python bench.py --write-traffic fwd.ncu-rep bwd.ncu-rep"),
+           "capture": ("CMD='python bench.py --steps 1 --warmup 1 --no-autotune --no-batch "
+                       "--no-event --no-cpu-baseline --no-cufft --no-e2e --no-noise --soak-s 0'; "
+                       "for K in <each kernel>; do ncu --metrics dram__bytes_read.sum,"
+                       "dram__bytes_write.sum --clock-control none -k regex:$K -s 1 -c 1 -o $K "
+                       "$CMD; done; then python bench.py --write-traffic <the reports>"),
            "reports": [os.path.basename(r) for r in reps],
            "source_sha256": source_hash(),
            "bytes_per_launch": {k: float(np.mean(v)) for k, v in sorted(acc.items())}}
@@ -233,16 +237,17 @@ def write_traffic(reps):
     print(json.dumps(rec["bytes_per_launch"]))
 
 
-def ncu_traffic(stage):
+def ncu_traffic(stage, fused=False):
     """DRAM bytes per launch of the stage's kernel from the committed ncu record, or None
     when the CUDA sources changed since the counters were taken."""
+    kernels = STAGE_KERNEL_FUSED if fused else STAGE_KERNEL
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
-    if not os.path.exists(path) or stage not in STAGE_KERNEL:
+    if not os.path.exists(path) or stage not in kernels:
         return None
     rec = json.load(open(path))
     if source_hash() != rec.get("source_sha256"):
         return None
-    return rec["bytes_per_launch"].get(STAGE_KERNEL[stage])
+    return rec["bytes_per_launch"].get(kernels[stage])
 
 
 def peaks():
@@ -302,23 +307,47 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_step(g, prm, R, d):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_step(g, prm, R, d, threads=1):
+    """Seconds of one oracle forward (rasterize on `threads` host threads, 0 = all; numpy's
+    FFT for Eq. 2, one thread), and its frame."""
     from oracle import oracle as O
     t0 = time.perf_counter()
-    O.run(g, prm, R, d)
-    return time.perf_counter() - t0
+    M = O.run(g, prm, R, d, threads=threads)
+    return time.perf_counter() - t0, M
 
 
 def cpu_baseline(g, prm, R, d):
-    """The FP64 oracle as it stands, single-threaded, on one full plane-frame."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    dt = oracle_step(g, prm, R, d)
-    return {"value": len(d) / dt, "unit": "depos/s", "cores": 1, "kind": "oracle",
-            "sample": "1 full forward of the same workload (%d depos, %dx%d plane), "
-                      "%.1f s wall" % (len(d), g.n_wires, g.n_ticks, dt)}
+    """The FP64 oracle as it stands on one full plane-frame of the workload: its rasterization
+    on all host cores (bands of rows, no reduction: bit for bit the serial grid) and on one,
+    numpy's single-threaded FFT for Eq. 2 in both.  Returns the record and the frame."""
+    cores = host_cores()
+    dt_mt, M = oracle_step(g, prm, R, d, threads=0)
+    dt_1, _ = oracle_step(g, prm, R, d, threads=1)
+    rec = {"value": len(d) / dt_mt, "unit": "depos/s", "cores": cores, "kind": "oracle",
+           "sample": "1 full forward of the same workload (%d depos, %dx%d plane): "
+                     "rasterization on %d threads, FFTs on one; %.2f s wall" %
+                     (len(d), g.n_wires, g.n_ticks, cores, dt_mt),
+           "single_thread": {"value": len(d) / dt_1, "unit": "depos/s", "cores": 1,
+                             "wall_s": dt_1}}
+    return rec, M
 
 
-REFERENCE_BUDGET_STEPS = 60     # full-workload oracle steps (about 2 s each) per run, at most
+def frame_error(got, ref):
+    """Relative L2 and max |err| / peak of a frame against the FP64 oracle's."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_over_peak": float(np.abs(got - ref).max() / np.abs(ref).max())}
+
+
+REFERENCE_BUDGET_STEPS = 60     # full-workload oracle steps (one or two s each) per run, at most
 
 
 def reference_sample(d, steps, warmup):
@@ -335,27 +364,29 @@ def reference_sample(d, steps, warmup):
 
 def run_reference(args):
     """The oracle on the host cores (rank 0 only; the other ranks exit without work): W
-    untimed and exactly K timed steps, each one forward of a bounded sample of the workload."""
+    untimed and exactly K timed steps, each one forward of a bounded sample of the workload,
+    its rasterization on every host core."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     wl, g, prm, kind, d = workload(args.workload)
     R = synth.make_response(g, kind)
     ds = reference_sample(d, args.steps, args.warmup)
     for _ in range(args.warmup):
-        oracle_step(g, prm, R, ds)
-    times = [oracle_step(g, prm, R, ds) for _ in range(args.steps)]
+        oracle_step(g, prm, R, ds, threads=0)
+    times = [oracle_step(g, prm, R, ds, threads=0)[0] for _ in range(args.steps)]
     tot = sum(times)
     v = args.steps * len(ds) / tot
+    cores = host_cores()
     sample = ("%d of the workload's %d depos per step (full %dx%d frame and convolution), "
-              "single thread" % (len(ds), len(d), g.n_wires, g.n_ticks))
+              "rasterization on %d threads, FFTs on one" % (len(ds), len(d), g.n_wires,
+                                                            g.n_ticks, cores))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "depos/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args.workload, g, d, prm),
-            "cpu_baseline": {"value": v, "unit": "depos/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "depos/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "depos/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -442,6 +473,72 @@ def batch_comparison(args, wcsim, steps=5):
                     "(the batch adds the event index), same kernels otherwise" % steps}
 
 
+# ---------------------------------------------------------------- full event
+def event_leg(args, wcsim, flush, oracle=True):
+    """The full three-plane event (800 U + 800 V + 960 W wires x 6000 ticks, 1,000,000 depos
+    projected on each plane, fluctuation on): one step = the three plane forwards, device
+    time with L2 flushed before each step.  Also its compulsory-byte roofline, the oracle on
+    all host cores (one run: rasterization threaded, FFTs on one thread) and each plane's
+    frame error against it."""
+    import torch
+    wl = synth.make_workload("event3p-1m")
+    planes, depos, waves, Rs = [], [], [], []
+    for g, prm, kind, d in wl.planes:
+        R = synth.make_response(g, kind)
+        Rs.append(R)
+        pl = wcsim.Plane(g, prm, torch.from_numpy(R).cuda())
+        dd = wcsim.DeviceDepos.from_host(d)
+        if not args.no_autotune:
+            pl.autotune(dd)
+        planes.append(pl)
+        depos.append(dd)
+        waves.append(torch.empty((g.n_wires, g.n_ticks), dtype=torch.float32, device="cuda"))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for pl, dd, w in zip(planes, depos, waves):
+            pl.run(dd, out=w)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    te = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ts[i].record(stream)
+        step()
+        te[i].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ts, te)) / args.steps
+    n_event = len(wl.planes[0][3])
+    bmin = sum(bmin_bytes(g, len(d)) for g, _, _, d in wl.planes)
+    hbm, peak_kind = peaks()
+    rec = {"planes": [g.n_wires for g, *_ in wl.planes], "n_ticks": wl.planes[0][0].n_ticks,
+           "depos": n_event, "ms_per_event": ms, "depos_per_s": n_event / (ms * 1e-3),
+           "plane_depos_per_s": sum(len(d) for *_, d in wl.planes) / (ms * 1e-3),
+           "event_frames_per_s": 1e3 / ms,
+           "step_roofline": {"bmin_bytes": bmin, "bmin_GBps": bmin / (ms * 1e-3) / 1e9,
+                             "frac_of_hbm": bmin / (ms * 1e-3) / 1e9 / hbm,
+                             "peak_kind": peak_kind}}
+    if oracle:
+        t0 = time.perf_counter()
+        errs = []
+        from oracle import oracle as O
+        for (g, prm, kind, d), R, w in zip(wl.planes, Rs, waves):
+            errs.append(frame_error(w.cpu().numpy(), O.run(g, prm, R, d, threads=0)))
+        dt = time.perf_counter() - t0
+        cores = host_cores()
+        rec["cpu_baseline"] = {"value": n_event / dt, "unit": "depos/s", "cores": cores,
+                               "kind": "oracle", "sample": "the whole event once (3 planes, "
+                               "1,000,000 depos each): rasterization on %d threads, FFTs on "
+                               "one; %.1f s wall" % (cores, dt)}
+        rec["error_vs_fp64"] = errs
+    for pl in planes:
+        pl.close()
+    return rec
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
@@ -459,13 +556,14 @@ def run_gpu(args):
     prm = rank_params(prm, rank)
     R = synth.make_response(g, kind)
 
-    cpu = None
+    cpu, M_oracle = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, prm, R, d)
+        cpu, M_oracle = cpu_baseline(g, prm, R, d)
 
     plane = wcsim.Plane(g, prm, torch.from_numpy(R).cuda())
     dd = wcsim.DeviceDepos.from_host(d)
     tune = None if args.no_autotune else plane.autotune(dd)
+    fused = bool(tune and tune["forward_fused"])
     wave = torch.empty((g.n_wires, g.n_ticks), dtype=torch.float32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -475,6 +573,8 @@ def run_gpu(args):
     for _ in range(args.warmup):
         plane.run(dd, out=wave)
     torch.cuda.synchronize()
+    # the bench frame against the FP64 oracle's (same seed, same Philox draws)
+    err = frame_error(wave.cpu().numpy(), M_oracle) if M_oracle is not None else None
     if ws > 1:
         dist.barrier()
 
@@ -673,57 +773,76 @@ def run_gpu(args):
     if rank == 0 and not args.no_batch:
         batch = batch_comparison(args, wcsim)
 
+    event = None
+    if rank == 0 and not args.no_event:
+        event = event_leg(args, wcsim, flush, oracle=not args.no_cpu_baseline)
+
     cufft = None
     if rank == 0 and not args.no_cufft:
         cufft = cufft_comparison(g)
     if rank != 0:
         return
     hbm, peak_kind = peaks()
-    sb = stage_bytes(g, len(d), mean_bins)
+    sb = stage_bytes(g, len(d), mean_bins, fused=fused)
     bsb = backward_stage_bytes(g, len(d), mean_bins, reused=True)
     avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     stages = {k: {"ms": avg[k], "GB/s": sb[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None,
                   "alg_bytes": sb[k]} for k in avg}
-    stages["prep"]["note"] = "depo binning (decide, count, scan, fill)"
-    stages["rasterize"]["note"] = "inside rows_r2c (fused forward)"
+    if fused:
+        stages["prep"]["note"] = "depo binning (decide, count, scan, fill)"
+        stages["rasterize"]["note"] = "inside rows_r2c (fused forward)"
+    else:
+        stages["prep"]["note"] = "no-op: the grid is cleared inside rows_r2c (consume and clear)"
     dom = max(avg, key=avg.get)
     ach = sb[dom] / (avg[dom] * 1e-3) / 1e9
     per_step = tot_ms / args.steps
+    kernel = STAGE_KERNEL_FUSED.get(dom) if fused else STAGE_KERNEL.get(dom)
+    launches = (6 if fused else 4) * args.steps
+    step_roof = {"bmin_bytes": bmin_bytes(g, len(d)),
+                 "bmin_GBps": bmin_bytes(g, len(d)) / (per_step * 1e-3) / 1e9,
+                 "frac_of_hbm": bmin_bytes(g, len(d)) / (per_step * 1e-3) / 1e9 / hbm,
+                 "fft_gflop": fft_flops(g) / 1e9,
+                 "fft_tflops": fft_flops(g) / (per_step * 1e-3) / 1e12}
+    # details first, the headline numbers last (a truncated tail of the line still shows them)
     line = {
         "metric": METRIC, "value": job_throughput(ws, args.steps, len(d), tot_ms), "unit": "depos/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config(args.workload, g, d, prm,
-                                              {"parallelism": "replicas" if ws > 1 else "1 gpu"}),
-        "plane_frames_per_s": {"fwd": ws * 1e3 / per_step,
-                               "fwd_bwd": (ws * 1e3 / fb_ms) if fb_ms else None},
-        "fwd_bwd_ms_per_step": fb_ms,
-        "backward_stages_ms": bwd_stages,
+        "data": "synthetic", "config": config(args.workload, g, d, prm),
+        "parallelism": "replicas" if ws > 1 else "1 gpu",
+        "stages": stages,
         "backward_stages": ({k: {"ms": v, "alg_bytes": bsb[k],
                                  "GB/s": bsb[k] / (v * 1e-3) / 1e9 if v > 0 else None}
                              for k, v in bwd_stages.items()} if bwd_stages else None),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm,
-                     "unit": "GB/s", "frac": ach / hbm, "traffic": ncu_traffic(dom),
-                     "alg_bytes": sb[dom],
-                     "peak_kind": peak_kind + " (burst copy)"},
-        "step_roofline": {"bmin_bytes": bmin_bytes(g, len(d)),
-                          "bmin_GBps": bmin_bytes(g, len(d)) / (per_step * 1e-3) / 1e9,
-                          "frac_of_hbm": bmin_bytes(g, len(d)) / (per_step * 1e-3) / 1e9 / hbm,
-                          "fft_gflop": fft_flops(g) / 1e9,
-                          "fft_tflops": fft_flops(g) / (per_step * 1e-3) / 1e12},
-        "stages": stages,
         "mean_bins_per_depo": mean_bins,
-        "gpu_launches": 4 * args.steps,
         "wall_s_timed_loop": wall,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
         "cufft_comparison": cufft,
+        "autotune": tune,
         "batch64": batch,
         "with_noise": noise,
         "adc_readout": adc,
         "rasterization_variants": variants or None,
-        "autotune": tune,
+        "event3p_1m": event,
+        "forward_variant": "fused" if fused else "plain",
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
         "clocks": clk,
+        "roofline": {"bound": "hbm", "kernel": kernel, "stage": dom, "achieved": ach,
+                     "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": ncu_traffic(dom, fused), "alg_bytes": sb[dom],
+                     "peak_kind": peak_kind + " (burst copy)"},
+        "step_roofline": step_roof,
+        "error_vs_fp64": err,
+        "plane_frames_per_s": {"fwd": ws * 1e3 / per_step,
+                               "fwd_bwd": (ws * 1e3 / fb_ms) if fb_ms else None},
+        "fwd_bwd_ms_per_step": fb_ms,
+        "summary": {"fwd_ms": per_step, "fwd_bwd_ms": fb_ms,
+                    "step_frac_of_hbm": step_roof["frac_of_hbm"],
+                    "dominant": [dom, ach / hbm],
+                    "event3p_1m_ms": event["ms_per_event"] if event else None,
+                    "batch64_speedup": batch["speedup"] if batch else None,
+                    "rel_l2_vs_fp64": err["rel_l2"] if err else None},
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
