@@ -214,20 +214,29 @@ wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* plane, int32_t enable);
  * Host-only. */
 wcsim_status wcsim_plane_set_forward(wcsim_plane* plane, int32_t fused);
 
+/* Rasterization tile of this plane (the autotuner's first choice, settable by hand):
+ * depos_per_block depos per CTA of 256 threads, each rasterized by lanes_per_depo lanes.
+ * Supported: (32, 8), (64, 8), (128, 8), (64, 16), (128, 16), (64, 32), (128, 32),
+ * (256, 32); WCSIM_EINVAL otherwise.  Results are unchanged up to summation order.
+ * Host-only. */
+wcsim_status wcsim_plane_set_raster_tile(wcsim_plane* plane, int32_t depos_per_block,
+                                         int32_t lanes_per_depo);
+
 /* Choices and best times (ms) found by wcsim_plane_autotune. */
 typedef struct {
     int32_t time_radix[8];     /* radices of the time-axis FFT plan, in pass order, 0-padded */
     int32_t rows_variant;      /* time-axis forward kernel: 0 direct loads, 1 bulk-staged */
     int32_t wire_variant;      /* wire pass: 0 one warp per time frequency, 1 block-level */
-    int32_t depos_per_block;   /* rasterization CTA size: 32, 64 or 128 depos */
+    int32_t depos_per_block;   /* rasterization tile: depos per CTA, 32..256 */
     int32_t candidates_timed;  /* configurations timed */
     float ms_rasterize, ms_rows, ms_wire;
     int32_t forward_fused;     /* forward variant kept (wcsim_plane_set_forward) */
     float ms_forward_plain, ms_forward_fused;   /* whole forward, each variant (0: not timed) */
+    int32_t lanes_per_depo;    /* rasterization tile: lanes that rasterize one depo, 8..32 */
 } wcsim_tune_report;
 
 /* Time the kernel variants of this plane on `depos` (DEVICE) and keep the fastest: the
- * rasterization CTA size, the radices and order of the time-axis FFT plan (the cheapest
+ * rasterization tile (depos per CTA, lanes per depo), the radices and order of the time-axis FFT plan (the cheapest
  * plans with the fewest passes), the time-axis forward kernel, the wire-pass kernel and the
  * forward variant (plain or fused, wcsim_plane_set_forward).
  * Results are unchanged up to floating-point rounding order.  Synchronizes `stream`,

@@ -96,7 +96,8 @@ struct wcsim_plane {
     wcsim_depos fwd_depos = {};
     wcsim_drift_params fwd_prm = {};
     bool wire_block = false;    // autotuned: use the block-level wire pass even if the warp one fits
-    int32_t kd = 32;            // depos per rasterization CTA (the autotuner may change it)
+    int32_t kd = 32;            // rasterization tile: depos per CTA and lanes per depo (the
+    int32_t kg = 8;             // autotuner may change them)
     // forward with rasterization fused into the time-axis transform: depo binning scratch,
     // and the impact positions per wire-pass launch (the time-axis spectra of that many
     // impact positions are alive at a time)
@@ -190,6 +191,7 @@ RasterConsts make_consts(const wcsim_plane* pl)
     c.key1 = (uint32_t)(p.seed >> 32);
     c.plane_id = p.plane_id;
     c.depos_per_block = pl->kd;
+    c.lanes_per_depo = pl->kg;
     c.DL = p.DL_cm2_s;
     c.DT = p.DT_cm2_s;
     c.v = p.v_mm_per_us;
@@ -872,17 +874,20 @@ wcsim_status wcsim_plane_autotune(wcsim_plane* pl, const wcsim_depos* depos, voi
         return best;
     };
     wcsim_tune_report rep{};
-    // 1. rasterization CTA size
+    // 1. rasterization tile: depos per CTA, lanes per depo
     {
-        const int kds[3] = {32, 64, 128};
+        const int tiles[][2] = {{32, 8}, {64, 8}, {128, 8}, {64, 16}, {128, 16}, {64, 32},
+                                {128, 32}, {256, 32}};
         float best = 1e30f;
-        for (int kd : kds) {
-            pl->kd = kd;
+        for (const auto& t : tiles) {
+            pl->kd = t[0];
+            pl->kg = t[1];
             RasterConsts c = make_consts(pl);
             const float ms = time_it([&] { return launch_rasterize(c, depo_arrays(depos), pl->grid, pl->flags, s); });
-            if (ms < best) { best = ms; rep.depos_per_block = kd; }
+            if (ms < best) { best = ms; rep.depos_per_block = t[0]; rep.lanes_per_depo = t[1]; }
         }
         pl->kd = rep.depos_per_block;
+        pl->kg = rep.lanes_per_depo;
         rep.ms_rasterize = best;
         // a representative grid for the FFT stages
         if (!err) err = cudaMemsetAsync(pl->grid, 0, grid_bytes, s);
@@ -1052,6 +1057,18 @@ wcsim_status wcsim_plane_set_noise(wcsim_plane* pl, const float* amp, int32_t n_
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(e, "noise spectrum upload");
     pl->noise_seed = seed;
+    return WCSIM_OK;
+}
+
+wcsim_status wcsim_plane_set_raster_tile(wcsim_plane* pl, int32_t depos_per_block,
+                                         int32_t lanes_per_depo)
+{
+    if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
+    if (!raster_tile_supported(depos_per_block, lanes_per_depo))
+        return fail(WCSIM_EINVAL, "no rasterization tile of %d depos per CTA and %d lanes per depo",
+                    depos_per_block, lanes_per_depo);
+    pl->kd = depos_per_block;
+    pl->kg = lanes_per_depo;
     return WCSIM_OK;
 }
 

@@ -59,20 +59,23 @@ __device__ __forceinline__ float binomial_bin(const RasterConsts& c, const Decis
     return binomial_inverse(n, p, uniform23(w), stirl);
 }
 
-// Lanes per depo group: 8 lanes take one depo, so that the four groups of a warp work on
-// four depos side by side (a patch of ~17 rows x 3 four-tick groups, ~47 items, fills six
-// rounds of 8 lanes better than two rounds of 32).
-constexpr int kGroup = 8;
+// The rasterization tiles (KD depos per CTA, G lanes per depo) the autotuner chooses from.
+// With G = 8 the four groups of a warp work on four depos side by side (a patch of ~17 rows x
+// 3 four-tick groups, ~47 items, fills six rounds of 8 lanes); with G = 32 a warp takes one
+// depo at a time (two rounds, but no groups diverging inside the warp).
+#define WCSIM_RASTER_TILES(X) X(32, 8) X(64, 8) X(128, 8) X(64, 16) X(128, 16) X(64, 32) \
+    X(128, 32) X(256, 32)
 
-// The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps.  BIN: the
-// exact binomial fluctuation (an instance of its own, so that the other modes keep their
-// registers).
-template <int KD, bool BIN>
+// The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps, G lanes per
+// depo.  BIN: the exact binomial fluctuation (an instance of its own, so that the other
+// modes keep their registers).
+template <int KD, int G, bool BIN>
 __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const DepoArrays& d,
                                                 float* __restrict__ grid, int* flags, int64_t blk)
 {
     static_assert(KD <= kWarps * 32, "one deciding thread per depo");
-    constexpr int G = kGroup, NG = kWarps * 32 / G;
+    static_assert(G == 8 || G == 16 || G == 32, "lanes per depo");
+    constexpr int NG = kWarps * 32 / G;
     __shared__ Decision s_dec[KD];
     __shared__ float s_wp[NG][kWmax];
     // tick weights of a tile laid out on 4-tick groups: slot p is tick 4 q_lo + p (zero
@@ -199,15 +202,15 @@ __device__ __forceinline__ void rasterize_block(const RasterConsts& c, const Dep
     }
 }
 
-template <int KD, bool BIN>
+template <int KD, int G, bool BIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_rasterize(RasterConsts c, DepoArrays d, float* __restrict__ grid, int* flags)
 {
-    rasterize_block<KD, BIN>(c, d, grid, flags, blockIdx.x);
+    rasterize_block<KD, G, BIN>(c, d, grid, flags, blockIdx.x);
 }
 
 // Several events of one plane: CTA b belongs to the event whose block range holds b.
-template <int KD, bool BIN>
+template <int KD, int G, bool BIN>
 __global__ void __launch_bounds__(kWarps * 32)
 k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
 {
@@ -215,7 +218,8 @@ k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
     while (e + 1 < ev.n && ev.block_start[e + 1] <= (int)blockIdx.x) ++e;
     c.key0 = ev.key0[e];
     c.key1 = ev.key1[e];
-    rasterize_block<KD, BIN>(c, ev.d[e], ev.grid[e], flags, (int64_t)blockIdx.x - ev.block_start[e]);
+    rasterize_block<KD, G, BIN>(c, ev.d[e], ev.grid[e], flags,
+                                (int64_t)blockIdx.x - ev.block_start[e]);
 }
 
 // Sum over the G lanes of a lane group (mask: the group's lanes), in every lane of it.
@@ -484,30 +488,35 @@ __global__ void k_windows(RasterConsts c, DepoArrays d, int32_t* __restrict__ ou
 
 }  // namespace
 
+bool raster_tile_supported(int depos_per_block, int lanes_per_depo)
+{
+#define WCSIM_TILE_CASE(KD, G) if (depos_per_block == KD && lanes_per_depo == G) return true;
+    WCSIM_RASTER_TILES(WCSIM_TILE_CASE)
+#undef WCSIM_TILE_CASE
+    return false;
+}
+
 cudaError_t launch_rasterize(const RasterConsts& c, const DepoArrays& d, float* grid,
                              int* flags, cudaStream_t s)
 {
     if (d.n <= 0) return cudaSuccess;
+    if (!raster_tile_supported(c.depos_per_block, c.lanes_per_depo)) return cudaErrorInvalidValue;
     const unsigned blocks = (unsigned)rasterize_blocks(d.n, c.depos_per_block);
-    if (c.fluctuate == 2) {
-        switch (c.depos_per_block) {
-            case 32: k_rasterize<32, true><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-            case 128: k_rasterize<128, true><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-            default: k_rasterize<64, true><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-        }
-        return cudaGetLastError();
+#define WCSIM_TILE_CASE(KD, G)                                                                 \
+    if (c.depos_per_block == KD && c.lanes_per_depo == G) {                                    \
+        if (c.fluctuate == 2)                                                                  \
+            k_rasterize<KD, G, true><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags);        \
+        else                                                                                   \
+            k_rasterize<KD, G, false><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags);       \
     }
-    switch (c.depos_per_block) {
-        case 32: k_rasterize<32, false><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-        case 128: k_rasterize<128, false><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-        default: k_rasterize<64, false><<<blocks, kWarps * 32, 0, s>>>(c, d, grid, flags); break;
-    }
+    WCSIM_RASTER_TILES(WCSIM_TILE_CASE)
+#undef WCSIM_TILE_CASE
     return cudaGetLastError();
 }
 
 int rasterize_blocks(int64_t n_depos, int depos_per_block)
 {
-    const int kd = (depos_per_block == 32 || depos_per_block == 128) ? depos_per_block : 64;
+    const int kd = depos_per_block > 0 ? depos_per_block : 64;
     return (int)((n_depos + kd - 1) / kd);
 }
 
@@ -516,19 +525,16 @@ cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev,
 {
     const int blocks = ev.block_start[ev.n];
     if (blocks <= 0) return cudaSuccess;
-    if (c.fluctuate == 2) {
-        switch (c.depos_per_block) {
-            case 32: k_rasterize_batch<32, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-            case 128: k_rasterize_batch<128, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-            default: k_rasterize_batch<64, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-        }
-        return cudaGetLastError();
+    if (!raster_tile_supported(c.depos_per_block, c.lanes_per_depo)) return cudaErrorInvalidValue;
+#define WCSIM_TILE_CASE(KD, G)                                                                 \
+    if (c.depos_per_block == KD && c.lanes_per_depo == G) {                                    \
+        if (c.fluctuate == 2)                                                                  \
+            k_rasterize_batch<KD, G, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags);       \
+        else                                                                                   \
+            k_rasterize_batch<KD, G, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags);      \
     }
-    switch (c.depos_per_block) {
-        case 32: k_rasterize_batch<32, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-        case 128: k_rasterize_batch<128, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-        default: k_rasterize_batch<64, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags); break;
-    }
+    WCSIM_RASTER_TILES(WCSIM_TILE_CASE)
+#undef WCSIM_TILE_CASE
     return cudaGetLastError();
 }
 

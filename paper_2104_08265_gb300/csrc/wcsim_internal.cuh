@@ -24,7 +24,8 @@ struct RasterConsts {
     int32_t renorm;                         // 1: each axis' weights divided by their window sum
     uint32_t key0, key1, plane_id;
     double DL, DT, v, tau;                  // FP64 parameters for the global gradients
-    int32_t depos_per_block;                // rasterization CTA size: 32, 64 or 128 depos
+    int32_t depos_per_block;                // rasterization tile: depos per CTA and lanes
+    int32_t lanes_per_depo;                 // per depo (raster_tile_supported)
     float stirl[16];                        // Stirling's remainder log m! - [(m + 1/2) log m
                                             // - m + 1/2 log 2 pi], m = 0..15 (exact binomial)
 };
@@ -67,6 +68,8 @@ cudaError_t launch_windows(const RasterConsts& c, const DepoArrays& d, int32_t* 
 cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev, int* flags,
                                    cudaStream_t s);
 int rasterize_blocks(int64_t n_depos, int depos_per_block);
+// Whether the rasterizers have an instance for this tile (depos per CTA, lanes per depo).
+bool raster_tile_supported(int depos_per_block, int lanes_per_depo);
 // Adjoint of drift + rasterization (mean path, windows fixed): dgrid -> per-depo and global
 // gradients (dglobal must be zeroed by the caller).
 cudaError_t launch_depo_adjoint(const RasterConsts& c, const DepoArrays& d, const float* dgrid,

@@ -69,7 +69,7 @@ class CTuneReport(ctypes.Structure):
                 ("candidates_timed", ctypes.c_int32), ("ms_rasterize", ctypes.c_float),
                 ("ms_rows", ctypes.c_float), ("ms_wire", ctypes.c_float),
                 ("forward_fused", ctypes.c_int32), ("ms_forward_plain", ctypes.c_float),
-                ("ms_forward_fused", ctypes.c_float)]
+                ("ms_forward_fused", ctypes.c_float), ("lanes_per_depo", ctypes.c_int32)]
 
 _lib = None
 
@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_set_digitizer": [vp, ctypes.c_float, ctypes.c_float, i32],
         "wcsim_plane_set_reuse_forward": [vp, i32],
         "wcsim_plane_set_forward": [vp, i32],
+        "wcsim_plane_set_raster_tile": [vp, i32, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -330,7 +331,8 @@ class Plane:
                 "wire_variant": r.wire_variant, "depos_per_block": r.depos_per_block,
                 "candidates_timed": r.candidates_timed, "ms_rasterize": r.ms_rasterize,
                 "ms_rows": r.ms_rows, "ms_wire": r.ms_wire, "forward_fused": r.forward_fused,
-                "ms_forward_plain": r.ms_forward_plain, "ms_forward_fused": r.ms_forward_fused}
+                "ms_forward_plain": r.ms_forward_plain, "ms_forward_fused": r.ms_forward_fused,
+                "lanes_per_depo": r.lanes_per_depo}
 
     def windows(self, depos: DeviceDepos, stream=None):
         import torch
@@ -373,6 +375,12 @@ class Plane:
         (the grid never written), or the plain flow through the grid; see
         wcsim_plane_set_forward."""
         check(lib().wcsim_plane_set_forward(self._h, 1 if fused else 0))
+
+    def set_raster_tile(self, depos_per_block: int, lanes_per_depo: int):
+        """Rasterization tile (depos per CTA, lanes per depo); see
+        wcsim_plane_set_raster_tile."""
+        check(lib().wcsim_plane_set_raster_tile(self._h, int(depos_per_block),
+                                                int(lanes_per_depo)))
 
     def set_timing(self, enable: bool = True):
         check(lib().wcsim_plane_set_timing(self._h, 1 if enable else 0))

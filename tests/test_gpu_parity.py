@@ -345,3 +345,34 @@ def test_autotune_picks_variants_without_changing_results(W):
     assert rep["candidates_timed"] >= 6 and rep["ms_rows"] > 0
     got = pl.run(dd).cpu().numpy()
     assert_close(got, O.run(g, prm, R, d), what="after autotune %s" % rep)
+
+
+RASTER_TILES = [(32, 8), (64, 8), (128, 8), (64, 16), (128, 16), (64, 32), (128, 32), (256, 32)]
+
+
+@pytest.mark.parametrize("fluct", [0, 1, 2])
+def test_every_rasterization_tile_matches_oracle(W, fluct):
+    """Each tile (depos per CTA, lanes per depo) the autotuner may keep: the grid against
+    the oracle's (the exact binomial's counts equal but at CDF steps, at most 1e-4 of the
+    draws off by one), and the plain and batched rasterizers alike."""
+    import torch
+    g = S.Geometry(n_wires=64, n_imp=10, n_ticks=800, pitch_mm=3.0, p0_mm=-3.0, t0_us=-10.0)
+    prm = S.DriftParams(fluctuate=fluct, seed=0x71E + fluct, DT_cm2_s=20.0)
+    d = edge_case_depos(g, np.random.default_rng(7 + fluct), n=900)
+    ref = O.rasterize(g, prm, d)
+    pl = plane_for(W, g, prm, np.zeros((g.n_imp, g.n_wires, g.n_ticks), np.complex64))
+    dd = to_dev(W, d)
+    for kd, kg in RASTER_TILES:
+        pl.set_raster_tile(kd, kg)
+        grid = torch.zeros((g.n_rows, g.n_ticks), dtype=torch.float32, device="cuda")
+        pl.rasterize(dd, grid)
+        got = grid.cpu().numpy()
+        what = "tile %d x %d fluct %d" % (kd, kg, fluct)
+        if fluct == 2:
+            diff = got - ref
+            assert np.abs(diff).max() <= 1 and np.count_nonzero(diff) <= max(2, 1e-4 * got.size), what
+        else:
+            assert_close(got, ref, what=what)
+    with pytest.raises(W.WcsimError):
+        pl.set_raster_tile(48, 8)
+    pl.close()
