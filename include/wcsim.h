@@ -170,8 +170,9 @@ typedef struct {
  * dgrid = dL/dS = Re IFFT2(conj(R_j) . FFT2(G)) per impact row (DEVICE float32, same shape
  * as S; may alias `grid`) and, if grad_resp is not NULL, dL/dR_j = conj(FFT2(S_j)) .
  * FFT2(G) / (n_fw n_ft) (DEVICE complex64 [n_imp][n_fw][n_ft], the PyTorch convention for
- * complex gradients: dL/dRe + i dL/dIm).  Requires n_fw = 32 M with M in {4, 8, 15, 16,
- * 20, 24, 25, 30} (WCSIM_ESHAPE otherwise).  Uses the plane's scratch. */
+ * complex gradients: dL/dRe + i dL/dIm).  Any spectrum size the plane accepts (one warp per
+ * time frequency for n_fw = 32 M with M in {4, 8, 15, 16, 20, 24, 25, 30}, the block-level
+ * engine otherwise).  Uses the plane's scratch. */
 wcsim_status wcsim_convolve_adjoint(wcsim_plane* plane, const float* grad_wave, const float* grid,
                                     float* dgrid, void* grad_resp_c64, void* stream);
 

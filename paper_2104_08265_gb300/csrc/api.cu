@@ -703,9 +703,6 @@ static wcsim_status convolve_adjoint(wcsim_plane* pl, const float* grad_wave, co
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
     if (!grad_wave || !grid || !dgrid) return fail(WCSIM_EINVAL, "grad_wave, grid or dgrid is NULL");
-    if (!pl->tw_warp)
-        return fail(WCSIM_ESHAPE, "the adjoint needs a wire FFT size of 32 M, M in {4, 8, 15, 16, "
-                                  "20, 24, 25, 30} (got %d)", pl->dims.n_fw);
     DeviceGuard dg(pl->device);
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
@@ -719,10 +716,14 @@ static wcsim_status convolve_adjoint(wcsim_plane* pl, const float* grad_wave, co
     markb(pl, 3, s);
     if ((e = launch_rows_r2c(dG, pl->pt, grad_wave, pl->mt, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
     markb(pl, 4, s);
-    if ((e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, pl->g2d,
-                                      (float2*)grad_resp_c64,
-                                      (float)(1.0 / ((double)d.n_fw * (double)d.n_ft)), s)))
-        return cuda_fail(e, "wire adjoint launch");
+    const float inv_n = (float)(1.0 / ((double)d.n_fw * (double)d.n_ft));
+    if (pl->tw_warp)
+        e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, pl->g2d,
+                                     (float2*)grad_resp_c64, inv_n, s);
+    else
+        e = launch_wire_adjoint_block(d, pl->pw, pl->mt, pl->shat, pl->H, (float2*)grad_resp_c64,
+                                      inv_n, s);
+    if (e) return cuda_fail(e, "wire adjoint launch");
     markb(pl, 5, s);
     if ((e = launch_rows_c2r_grid(d, pl->pt, pl->shat, dgrid, s))) return cuda_fail(e, "rows_c2r_grid launch");
     markb(pl, 6, s);
@@ -763,9 +764,6 @@ wcsim_status wcsim_run_backward(wcsim_plane* pl, const wcsim_depos* depos, const
     wcsim_status st = check_depos(depos);
     if (st) return st;
     if (!grad_wave || !grads) return fail(WCSIM_EINVAL, "grad_wave or grads is NULL");
-    if (!pl->tw_warp)
-        return fail(WCSIM_ESHAPE, "the adjoint needs a wire FFT size of 32 M, M in {4, 8, 15, 16, "
-                                  "20, 24, 25, 30} (got %d)", pl->dims.n_fw);
     DeviceGuard dg(pl->device);
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;

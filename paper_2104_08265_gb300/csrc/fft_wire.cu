@@ -183,6 +183,74 @@ k_wire_direct(ConvDims d, FftPlan p, const float2* __restrict__ shat, const floa
     }
 }
 
+// First-pass source of the inverse wire FFT of the adjoint: conj(H_j(kt0 + c, kw)) G^(kw)
+// for column c, G^ held in shared memory in the padded layout of a plan's output.
+template <int LG>
+struct ConjHGLd {
+    const float2* hj;    // H_j's rows kt0 .. kt0 + 2^LG - 1 (time-frequency major, n_fw each)
+    const float2* gh;
+    int n_fw;
+    __device__ __forceinline__ float2 operator()(int c, int kw) const
+    {
+        const float2 h = __ldg(hj + (int64_t)c * n_fw + kw);
+        const float2 g = gh[(pad16(kw) << LG) + c];
+        return make_float2(h.x * g.x + h.y * g.y, h.x * g.y - h.y * g.x);
+    }
+};
+
+// Adjoint of the wire pass for any wire FFT size (the one-warp-per-column kernels of
+// adjoint.cu take n_fw = 32 M): one CTA per group of 2^LG time frequencies.  G^ = the wire
+// FFT of G's time-axis spectrum stays in shared memory; for every j the CTA transforms S_j's
+// columns and writes dL/dR_j = conj(S^_j) G^ / (n_fw n_ft) at (kw, kt) and its mirror
+// (-kw, -kt) (when dR is not null), then transforms conj(H_j) G^ back along the wires and
+// writes it over S_j's columns (the time-axis spectrum of dL/dS_j).
+template <int LG>
+__global__ void __launch_bounds__(256, 1)
+k_wire_adjoint_block(ConvDims d, FftPlan p, const float2* __restrict__ gt,
+                     float2* __restrict__ shat, const float2* __restrict__ H,
+                     float2* __restrict__ dR, float inv_n)
+{
+    constexpr int B = 1 << LG;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const int N = p.n;
+    const int plen = padded_len(N) << LG;
+    float2* X = reinterpret_cast<float2*>(smraw);
+    float2* Y = X + plen;
+    float2* gh = Y + plen;
+    const int kt0 = blockIdx.x * B;        // B divides 4: a group never straddles blocks
+    {
+        const float2* z = run_plan<false, LG>(p, BlockedColLd<LG>{gt, d.n_w, kt0}, X, Y);
+        for (int e = threadIdx.x; e < plen; e += blockDim.x) gh[e] = z[e];
+        __syncthreads();
+    }
+    for (int j = 0; j < d.n_imp; ++j) {
+        float2* sj = shat + (int64_t)j * d.nkb * d.n_w * kBlockCols;
+        if (dR) {
+            const float2* z = run_plan<false, LG>(p, BlockedColLd<LG>{sj, d.n_w, kt0}, X, Y);
+            float2* dRj = dR + (int64_t)j * N * d.n_ft;
+            for (int e = threadIdx.x; e < (N << LG); e += blockDim.x) {
+                const int c = e & (B - 1), kw = e >> LG, kt = kt0 + c;
+                if (kt >= d.nh) continue;
+                const int idx = (pad16(kw) << LG) + c;
+                const float2 u = z[idx], g = gh[idx];
+                const float2 v = make_float2(inv_n * (u.x * g.x + u.y * g.y),
+                                             inv_n * (u.x * g.y - u.y * g.x));
+                dRj[(int64_t)kw * d.n_ft + kt] = v;
+                if (kt >= 1 && d.n_ft - kt >= d.nh)
+                    dRj[(int64_t)((N - kw) % N) * d.n_ft + (d.n_ft - kt)] = make_float2(v.x, -v.y);
+            }
+            __syncthreads();
+        }
+        const float2* hj = H + ((int64_t)j * d.nkb * kBlockCols + kt0) * N;
+        const float2* m = run_plan<true, LG>(p, ConjHGLd<LG>{hj, gh, N}, X, Y);
+        for (int e = threadIdx.x; e < (d.n_w << LG); e += blockDim.x) {
+            const int c = e & (B - 1), w = e >> LG;
+            sj[blk_index(kt0 + c, w, d.n_w)] = m[(pad16(w) << LG) + c];
+        }
+        __syncthreads();
+    }
+}
+
 // H[j][kt][kw] = scale (R_j[kw][kt] + conj R_j[-kw][-kt]) / 2 for kt < nh, zero for the
 // padding rows nh <= kt < 4 nkb.  A 32 x 32 tile of (kw, kt) per CTA, transposed through
 // shared memory so that both the reads of R (along kt) and the writes of H (along kw) are
@@ -265,6 +333,28 @@ cudaError_t launch_wire_pass(const ConvDims& d, const FftPlan& pw, const float2*
         k_wire_direct<0><<<d.nkb * kBlockCols, 256, 3 * (size_t)padded_len(pw.n) * sizeof(float2), s>>>(
             d, pw, shat, H, mt);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wire_adjoint_block(const ConvDims& d, const FftPlan& pw, const float2* gt,
+                                      float2* shat, const float2* H, float2* dR, float inv_n,
+                                      cudaStream_t s)
+{
+    static DeviceOnce attr;
+    if (attr.pending()) {
+        cudaError_t e = cudaFuncSetAttribute(k_wire_adjoint_block<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (!e) e = cudaFuncSetAttribute(k_wire_adjoint_block<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        if (e) return e;
+        attr.mark();
+    }
+    const size_t four = 3 * (size_t)(padded_len(pw.n) << 2) * sizeof(float2);
+    const size_t one = 3 * (size_t)padded_len(pw.n) * sizeof(float2);
+    if (four <= kMaxSmem)
+        k_wire_adjoint_block<2><<<d.nkb, 256, four, s>>>(d, pw, gt, shat, H, dR, inv_n);
+    else if (one <= kMaxSmem)
+        k_wire_adjoint_block<0><<<d.nkb * kBlockCols, 256, one, s>>>(d, pw, gt, shat, H, dR, inv_n);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -181,6 +181,11 @@ cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2*
 cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const float2* gt,
                                      float2* shat, const float2* H, float2* g2d, float2* dR,
                                      float inv_n, cudaStream_t s);
+// The same adjoint for any wire FFT size, block-level engine (plan pw): gt, shat, dR as above;
+// no 2D spectrum of G is kept.
+cudaError_t launch_wire_adjoint_block(const ConvDims& d, const FftPlan& pw, const float2* gt,
+                                      float2* shat, const float2* H, float2* dR, float inv_n,
+                                      cudaStream_t s);
 // Inverse time-axis FFT of every grid row from blocked spectra [n_imp][nkb][n_w][4].
 cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const float2* shat,
                                  float* grid, cudaStream_t s);

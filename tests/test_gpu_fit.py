@@ -5,7 +5,8 @@ A single process runs every event: the gradients of the summed loss with respect
 D_T, the lifetime and the response are the sums of the events' wcsim_run_backward
 gradients, and must match the FP64 oracle's sums (the response per output at relative
 L2 <= 1e-5 and max |err| <= 1e-4 x peak; the three globals to 1e-5 x the sum of their
-per-depo terms' magnitudes over all events); a step lowers the loss.
+per-depo terms' magnitudes over all events), for the dL/dM = M - T the library saw; a step
+lowers the loss.
 """
 import dataclasses
 
@@ -40,25 +41,30 @@ def test_single_process_fit_matches_the_oracle_sum_over_events():
     f = fit.ShardedFit(len(events), base, state, fns,
                        {"DL": 1e-7, "DT": 1e-7, "lifetime": 1e-5, "response": 1e-9})
     loss, grads = f.gradient()
-    # the oracle's per-event gradients, summed
+    # the oracle's per-event gradients for the same dL/dM the library saw (the GPU frame less
+    # the FP32 target), summed
     ref = {k: 0.0 for k in fit.GLOBALS}
     mag = {k: 0.0 for k in fit.GLOBALS}
     dR = np.zeros(R.shape, np.complex128)
-    ref_loss = 0.0
+    ref_loss, loss_bound = 0.0, 0.0
     for e, (d, t) in enumerate(zip(events, targets)):
         prm = dataclasses.replace(fit.event_params(base, e), DL_cm2_s=4.0, DT_cm2_s=8.8,
                                   lifetime_us=10000.0)
-        grid = O.rasterize(g, prm, d)
-        G = O.convolve(g, R, grid) - t
+        plane.set_params(prm)
+        M = plane.run(wcsim.DeviceDepos.from_host(d)).cpu().numpy()
+        G = (M - t.astype(np.float32)).astype(np.float64)       # the FP32 difference the fit forms
         ref_loss += 0.5 * float((G * G).sum())
-        dS, dRe = O.convolve_adjoint(g, R, grid, G)
+        # two runs of a frame differ in the order of the FP32 atomic sums: L = 1/2 |G|^2 moves
+        # by about G . dG, |dG| <= 1e-5 |M| (the forward's tolerance)
+        loss_bound += 2.0 * np.linalg.norm(G) * 1e-5 * np.linalg.norm(M)
+        dS, dRe = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G)
         gr = O.depo_grads(g, prm, d, dS)
         terms = global_terms(prm, d, gr)
         for k in fit.GLOBALS:
             ref[k] += gr[k]
             mag[k] += float(np.abs(terms[k]).sum())
         dR += dRe
-    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    assert abs(loss - ref_loss) <= loss_bound, (loss, ref_loss, loss_bound)
     for k in fit.GLOBALS:
         assert abs(grads[k] - ref[k]) <= TERM_REL * mag[k], (k, grads[k], ref[k])
     got = grads["response"].cpu().numpy().astype(np.complex128)

@@ -4,9 +4,11 @@ Each case draws a geometry (wires, impacts per pitch, ticks: sizes whose factors
 5 and 7, with ragged tails against every tile size; pitch, tick and origins), drift
 parameters (speed, D_L, D_T, lifetime, n_sigma, fluctuation mode, renormalisation, seed,
 plane id), a response kind and spectrum padding, and a few hundred depos on tracks that
-cross the plane's borders.  The forward frame must match the oracle at the forward's
-tolerance (relative L2 <= 1e-5, max |err| <= 1e-4 x peak); where the adjoint applies
-(n_fw = 32 M), so must the depo and response gradients.
+cross the plane's borders; odd seeds take the fused forward.  The forward frame must match
+the oracle at the forward's tolerance (relative L2 <= 1e-5, max |err| <= 1e-4 x peak), and
+so must the depo and response gradients of the backward on every plane (one warp per time
+frequency for n_fw = 32 M, the block-level adjoint otherwise), the three global gradients
+to 1e-5 x the sum of their terms' magnitudes.
 """
 import dataclasses
 
@@ -16,11 +18,12 @@ import pytest
 from oracle import oracle as O
 from paper_2104_08265_gb300 import synth as S
 
+from gradcheck import assert_globals_close
+
 pytestmark = pytest.mark.gpu
 
 REL_L2 = 1e-5
 MAX_PEAK = 1e-4
-ADJOINT_M = (4, 8, 15, 16, 20, 24, 25, 30)
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +60,7 @@ def draw_case(seed):
     wires = smooth_sizes(1, 300)
     ticks = smooth_sizes(16, 3000)
     n_w = int(rng.choice(wires))
-    if seed % 3 == 0:                                   # the adjoint's wire sizes
+    if seed % 3 == 0:                                   # the one-warp wire kernels' sizes
         n_w = int(32 * rng.choice([4, 8, 15]))
     g = S.Geometry(n_wires=n_w, n_imp=int(rng.integers(1, 13)), n_ticks=int(rng.choice(ticks)),
                    pitch_mm=float(rng.uniform(2.0, 5.0)), p0_mm=float(rng.uniform(-50, 50)),
@@ -88,13 +91,12 @@ def test_random_plane_matches_oracle(W, seed):
         n_ft = smooth_sizes(g.n_ticks + 1, 2 * g.n_ticks)[0]
     R = S.make_response(g, kind, n_fw=n_fw, n_ft=n_ft)
     pl = W.Plane(g, prm, torch.from_numpy(np.ascontiguousarray(R, np.complex64)).cuda())
+    pl.set_forward(seed % 2 == 1)                       # both forward variants
     dd = W.DeviceDepos.from_host(d)
     what = "seed %d: %s %s" % (seed, g, prm)
     M = pl.run(dd)
     assert pl.check_flags() == 0
     close(M.cpu().numpy(), O.run(g, prm, R, d), what + " forward")
-    if R.shape[1] % 32 or R.shape[1] // 32 not in ADJOINT_M:
-        return
     G = torch.from_numpy(np.random.default_rng(seed).normal(size=(g.n_wires, g.n_ticks))
                          .astype(np.float32)).cuda()
     got = pl.backward(dd, G, want_resp=True)
@@ -104,3 +106,4 @@ def test_random_plane_matches_oracle(W, seed):
     for k in ("q", "p", "t", "sigma_L", "sigma_T"):
         close(got[k].cpu().numpy(), ref[k], what + " d" + k)
     close(got["response"].cpu().numpy(), dR, what + " dR")
+    assert_globals_close(got, ref, mean, d, what)
