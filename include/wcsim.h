@@ -199,8 +199,11 @@ wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
  * wcsim_run or wcsim_run_adc on the same depo arrays (same pointers and count) with the same
  * parameters and fluctuate = 0, instead of recomputing the mean-path grid and its spectra.
  * The caller promises not to change the depo arrays between the two calls (as autograd keeps
- * a forward's activations for its backward).  Any other compute call on the plane drops the
- * spectra.  enable = 0 (the default): the backward always recomputes.  Host-only. */
+ * a forward's activations for its backward): the arrays are recognised by their pointers and
+ * count only, so arrays freed and reallocated at the same addresses with other contents would
+ * be taken for the forward's.  Any other compute call on the plane drops the spectra.
+ * enable = 0 (the default): the backward always recomputes.  Calling it (with either value)
+ * also drops any kept spectra.  Host-only. */
 wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* plane, int32_t enable);
 
 /* Forward variant of wcsim_run / wcsim_run_adc.  fused = 0 (the default): the flow of Sec.

@@ -153,11 +153,18 @@ def _stream_handle(stream) -> int:
     return int(s.cuda_stream)
 
 
+_DEPO_SERIAL = [0]
+
+
 class DeviceDepos:
-    """Depos resident on the GPU (torch tensors); keeps the tensors alive for the C struct."""
+    """Depos resident on the GPU (torch tensors); keeps the tensors alive for the C struct.
+    Each instance has a serial number, so that a plane can tell two depo sets apart even when
+    the caching allocator gives the second the first one's addresses."""
 
     def __init__(self, p, t, td, q, ids):
         self.p, self.t, self.td, self.q, self.id = p, t, td, q, ids
+        _DEPO_SERIAL[0] += 1
+        self.serial = _DEPO_SERIAL[0]
         n = int(p.shape[0])
         for a in (p, t, td, q, ids):
             assert int(a.shape[0]) == n and a.is_cuda and a.is_contiguous()
@@ -249,6 +256,7 @@ class Plane:
         out = self._wave(out)
         check(lib().wcsim_run(self._h, ctypes.byref(depos.c), out.data_ptr(),
                               _stream_handle(stream)))
+        self._last_run_serial = depos.serial
         return out
 
     def set_digitizer(self, gain: float, pedestal: float, bits: int):
@@ -314,6 +322,10 @@ class Plane:
         global DL, DT, lifetime and (if asked) the response spectrum."""
         out, c = self._grads(len(depos))
         dR = self._resp_buffer(want_resp)
+        if getattr(self, "_reuse", False) and getattr(self, "_last_run_serial", None) != depos.serial:
+            # not the depo set of the last run (the library compares pointers only): drop the
+            # kept spectra so that the backward recomputes them
+            check(lib().wcsim_plane_set_reuse_forward(self._h, 1))
         check(lib().wcsim_run_backward(self._h, ctypes.byref(depos.c),
                                        grad_wave.contiguous().data_ptr(), ctypes.byref(c),
                                        dR.data_ptr() if dR is not None else None,
@@ -367,8 +379,12 @@ class Plane:
     def set_reuse_forward(self, enable: bool = True):
         """Let backward() reuse the spectra of the preceding mean-path run() on the same depos
         and parameters (the depos must not change in between); see
-        wcsim_plane_set_reuse_forward."""
+        wcsim_plane_set_reuse_forward.  The library recognises the depos by their device
+        pointers and count only; this binding also requires the same DeviceDepos object (its
+        serial), so tensors freed and reallocated at the same addresses are not mistaken for
+        the forward's."""
         check(lib().wcsim_plane_set_reuse_forward(self._h, 1 if enable else 0))
+        self._reuse = bool(enable)
 
     def set_forward(self, fused: bool = True):
         """Forward variant of run(): the rasterization fused into the time-axis transform

@@ -252,3 +252,63 @@ def test_autograd_backward_uses_its_own_forward_parameters(W):
     assert float(torch.linalg.vector_norm(q.grad - q0.grad) / torch.linalg.vector_norm(q0.grad)) < 1e-5
     for a_, b_ in zip(x, x0):
         assert float(a_.grad) == pytest.approx(float(b_.grad), rel=1e-4)
+
+
+def test_autograd_drift_time_gradient_and_sigma_sink(W):
+    """WcsimFn gives the drift time a gradient (dL/dt + dL/dsigma_L sigma_L / (2 t_d) +
+    dL/dsigma_T sigma_T / (2 t_d) - dL/dQ Q / lifetime, the chain rule pinned on CPU against
+    finite differences) and hands the per-depo sigma_L / sigma_T gradients out through its
+    sink; both against the oracle's per-depo gradients."""
+    import torch
+    from paper_2104_08265_gb300.autograd import WcsimFn
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=0, DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=800.0)
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    dd = W.DeviceDepos.from_host(d)
+    td = dd.td.clone().requires_grad_(True)
+    t64 = lambda x: torch.tensor(x, dtype=torch.float64, device="cuda")
+    sink = {}
+    M = WcsimFn.apply(pl, dd.q, dd.p, dd.t, td, dd.id, t64(6.0), t64(10.0), t64(800.0), None, sink)
+    G = torch.from_numpy(np.random.default_rng(93).normal(size=(g.n_wires, g.n_ticks))
+                         .astype(np.float32)).cuda()
+    (M * G).sum().backward()
+    dS, _ = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G.cpu().numpy().astype(np.float64))
+    ref = O.depo_grads(g, prm, d, dS)
+    tdh = np.asarray(d.td, np.float64)
+    live = tdh > 0
+    f_l = np.where(live, np.sqrt(2e-4 * 6.0 * np.where(live, tdh, 1)) / (2 * np.where(live, tdh, 1)), 0)
+    f_t = np.where(live, np.sqrt(2e-4 * 10.0 * np.where(live, tdh, 1)) / (2 * np.where(live, tdh, 1)), 0)
+    ref_td = (ref["t"] + ref["sigma_L"] * f_l + ref["sigma_T"] * f_t
+              - ref["q"] * np.asarray(d.q, np.float64) / 800.0)
+    assert_close(td.grad.cpu().numpy(), ref_td, what="dL/dt_d")
+    assert_close(sink["sigma_L"].cpu().numpy(), ref["sigma_L"], what="sink sigma_L")
+    assert_close(sink["sigma_T"].cpu().numpy(), ref["sigma_T"], what="sink sigma_T")
+    pl.close()
+
+
+def test_reuse_is_dropped_for_other_depos_at_the_same_addresses(W):
+    """The forward's depo tensors are freed and a new depo set with other charges lands at
+    the same addresses (the caching allocator reuses them): the backward of the new set must
+    not take the first set's spectra."""
+    import torch
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=0)
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    pl.set_reuse_forward(True)
+    a = W.DeviceDepos.from_host(d)
+    pl.run(a)
+    ptrs = (a.p.data_ptr(), a.q.data_ptr())
+    del a
+    d2 = dataclasses.replace(d, q=(d.q * 0.25).astype(np.float32))
+    b = W.DeviceDepos.from_host(d2)
+    G = torch.from_numpy(np.random.default_rng(94).normal(size=(g.n_wires, g.n_ticks))
+                         .astype(np.float32)).cuda()
+    got = pl.backward(b, G)
+    ref, _ = _oracle_backward(g, prm, R, d2, G.cpu().numpy().astype(np.float64))
+    _grads_close(got, ref, "reallocated depos", prm, d2)
+    print("same addresses reused:", ptrs == (b.p.data_ptr(), b.q.data_ptr()))
+    pl.close()

@@ -510,6 +510,39 @@ def test_depo_grads_match_central_finite_differences():
     assert checked >= 30
 
 
+def test_drift_time_chain_rule_matches_central_finite_differences():
+    """t_d enters through t_a = t + t_d, sigma = sqrt(2 D t_d) and Q' = Q exp(-t_d / tau):
+    dL/dt_d = dL/dt + dL/dsigma_L sigma_L / (2 t_d) + dL/dsigma_T sigma_T / (2 t_d)
+    - dL/dQ Q / tau (the chain rule the autograd wrapper applies), against FD in t_d with
+    the window frozen."""
+    import dataclasses
+    g = S.Geometry(n_wires=12, n_imp=10, n_ticks=128, pitch_mm=3.0)
+    rng = np.random.default_rng(29)
+    R = S.make_response(g, "induction").astype(np.complex128)
+    G = rng.normal(size=(g.n_wires, g.n_ticks))
+    prm = S.DriftParams(DL_cm2_s=6.0, DT_cm2_s=10.0, lifetime_us=800.0)
+    checked = 0
+    for trial in range(12):
+        p = rng.uniform(8, 28); t = rng.uniform(5, 20); td = rng.uniform(20, 40); q = 5000.0
+        d = one(p, t, td, q)
+        w0 = O.windows(g, prm, d)[0]
+        dS, _ = O.convolve_adjoint(g, R, O.rasterize(g, prm, d), G)
+        gr = O.depo_grads(g, prm, d, dS)
+        sL = math.sqrt(2 * prm.DL_cm2_s * 1e-4 * td)
+        sT = math.sqrt(2 * prm.DT_cm2_s * 1e-4 * td)
+        ana = (gr["t"][0] + gr["sigma_L"][0] * sL / (2 * td) + gr["sigma_T"][0] * sT / (2 * td)
+               - gr["q"][0] * q / prm.lifetime_us)
+        h = 1e-6 * td
+        dp_, dm_ = one(p, t, td + h, q), one(p, t, td - h, q)
+        if not (np.array_equal(O.windows(g, prm, dp_)[0], w0) and
+                np.array_equal(O.windows(g, prm, dm_)[0], w0)):
+            continue
+        num = (_loss(g, prm, R, dp_, G) - _loss(g, prm, R, dm_, G)) / (2 * h)
+        assert abs(num - ana) <= 2e-5 * max(abs(num), abs(ana)) + 1e-9, (num, ana)
+        checked += 1
+    assert checked >= 8
+
+
 def test_depo_sigma_grads_individually():
     """Per-depo sigma grads via the D derivative of a single depo: dL/dD = dsigma sigma/(2D)."""
     g = S.Geometry(n_wires=12, n_imp=10, n_ticks=128, pitch_mm=3.0)
