@@ -96,6 +96,7 @@ struct wcsim_plane {
     wcsim_depos fwd_depos = {};
     wcsim_drift_params fwd_prm = {};
     bool wire_block = false;    // autotuned: use the block-level wire pass even if the warp one fits
+    bool adj_block = false;     // use the block-level wire adjoint even if the warp one fits
     int32_t kd = 32;            // rasterization tile: depos per CTA and lanes per depo (the
     int32_t kg = 8;             // autotuner may change them)
     // forward with rasterization fused into the time-axis transform: depo binning scratch,
@@ -551,6 +552,8 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     pl->fused_fits = fused_supported(pl->pt);
     // forward variant; WCSIM_FORWARD=fused|plain overrides the default (plain)
     if (const char* v = getenv("WCSIM_FORWARD")) pl->fused = strcmp(v, "fused") == 0;
+    // wire adjoint; WCSIM_ADJOINT_KERNEL=block forces the block-level engine
+    if (const char* v = getenv("WCSIM_ADJOINT_KERNEL")) pl->adj_block = strcmp(v, "block") == 0;
     WC_TRY(cudaMemsetAsync(pl->flags, 0, sizeof(int), s), "flag reset");
     WC_TRY(launch_make_hermitian(d, (const float2*)resp_c64, pl->H,
                                  (float)(1.0 / ((double)n_fw * (double)n_ft)), s),
@@ -717,7 +720,7 @@ static wcsim_status convolve_adjoint(wcsim_plane* pl, const float* grad_wave, co
     if ((e = launch_rows_r2c(dG, pl->pt, grad_wave, pl->mt, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
     markb(pl, 4, s);
     const float inv_n = (float)(1.0 / ((double)d.n_fw * (double)d.n_ft));
-    if (pl->tw_warp)
+    if (pl->tw_warp && !pl->adj_block)
         e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, pl->g2d,
                                      (float2*)grad_resp_c64, inv_n, s);
     else
