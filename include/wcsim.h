@@ -220,8 +220,8 @@ wcsim_status wcsim_plane_set_forward(wcsim_plane* plane, int32_t fused);
 
 /* Rasterization tile of this plane (the autotuner's first choice, settable by hand):
  * depos_per_block depos per CTA of 256 threads, each rasterized by lanes_per_depo lanes.
- * Supported: (32, 8), (64, 8), (128, 8), (64, 16), (128, 16), (64, 32), (128, 32),
- * (256, 32); WCSIM_EINVAL otherwise.  Results are unchanged up to summation order.
+ * Supported: (32, 8), (64, 8), (128, 8), (256, 8), (64, 16), (128, 16), (256, 16),
+ * (64, 32), (128, 32), (256, 32); WCSIM_EINVAL otherwise.  Results are unchanged up to summation order.
  * Host-only. */
 wcsim_status wcsim_plane_set_raster_tile(wcsim_plane* plane, int32_t depos_per_block,
                                          int32_t lanes_per_depo);

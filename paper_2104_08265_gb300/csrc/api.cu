@@ -877,8 +877,8 @@ wcsim_status wcsim_plane_autotune(wcsim_plane* pl, const wcsim_depos* depos, voi
     wcsim_tune_report rep{};
     // 1. rasterization tile: depos per CTA, lanes per depo
     {
-        const int tiles[][2] = {{32, 8}, {64, 8}, {128, 8}, {64, 16}, {128, 16}, {64, 32},
-                                {128, 32}, {256, 32}};
+        const int tiles[][2] = {{32, 8}, {64, 8}, {128, 8}, {256, 8}, {64, 16}, {128, 16},
+                                {256, 16}, {64, 32}, {128, 32}, {256, 32}};
         float best = 1e30f;
         for (const auto& t : tiles) {
             pl->kd = t[0];

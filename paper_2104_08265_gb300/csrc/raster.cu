@@ -63,8 +63,8 @@ __device__ __forceinline__ float binomial_bin(const RasterConsts& c, const Decis
 // With G = 8 the four groups of a warp work on four depos side by side (a patch of ~17 rows x
 // 3 four-tick groups, ~47 items, fills six rounds of 8 lanes); with G = 32 a warp takes one
 // depo at a time (two rounds, but no groups diverging inside the warp).
-#define WCSIM_RASTER_TILES(X) X(32, 8) X(64, 8) X(128, 8) X(64, 16) X(128, 16) X(64, 32) \
-    X(128, 32) X(256, 32)
+#define WCSIM_RASTER_TILES(X) X(32, 8) X(64, 8) X(128, 8) X(256, 8) X(64, 16) X(128, 16) \
+    X(256, 16) X(64, 32) X(128, 32) X(256, 32)
 
 // The depos [blk * KD, blk * KD + KD) of one event, by one CTA of kWarps warps, G lanes per
 // depo.  BIN: the exact binomial fluctuation (an instance of its own, so that the other

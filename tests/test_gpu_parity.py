@@ -347,7 +347,8 @@ def test_autotune_picks_variants_without_changing_results(W):
     assert_close(got, O.run(g, prm, R, d), what="after autotune %s" % rep)
 
 
-RASTER_TILES = [(32, 8), (64, 8), (128, 8), (64, 16), (128, 16), (64, 32), (128, 32), (256, 32)]
+RASTER_TILES = [(32, 8), (64, 8), (128, 8), (256, 8), (64, 16), (128, 16), (256, 16), (64, 32),
+                (128, 32), (256, 32)]
 
 
 @pytest.mark.parametrize("fluct", [0, 1, 2])
