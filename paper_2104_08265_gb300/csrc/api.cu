@@ -82,11 +82,13 @@ struct wcsim_plane {
     float adc_gain = 0.0f, adc_pedestal = 0.0f;   // digitizer (adc_max 0: none set)
     int32_t adc_max = 0;
     int* flags = nullptr;       // device flag word
+    int* queue = nullptr;       // work-queue counter of batched rasterizations
     // scratch of batched runs: bcap events' grids, time-axis and wire-summed spectra
     float* bgrid = nullptr;
     float2* bshat = nullptr;
     float2* bmt = nullptr;
     int32_t bcap = 0;
+    int32_t bclean = 0;         // leading batch grid slots known to be all zero
     int device = 0;
     bool grid_clean = false;    // the plane's grid is all zero (consume-and-clear state)
     // wcsim_plane_set_reuse_forward: shat holds the mean-path spectra of the last run on
@@ -230,6 +232,7 @@ void plane_free(wcsim_plane* pl)
     cudaFree(pl->g2d);
     cudaFree(pl->noise_amp);
     cudaFree(pl->flags);
+    cudaFree(pl->queue);
     cudaFree(pl->bgrid);
     cudaFree(pl->bshat);
     cudaFree(pl->bmt);
@@ -410,6 +413,7 @@ wcsim_status reserve_batch(wcsim_plane* pl, int32_t n)
     if (!e) e = cudaMalloc(&pl->bmt, (size_t)n * ev_mt_elems(d) * sizeof(float2));
     if (e) return cuda_fail(e, "batch scratch allocation");
     pl->bcap = n;
+    pl->bclean = 0;
     return WCSIM_OK;
 }
 
@@ -422,18 +426,31 @@ void with_noise(const wcsim_plane* pl, ConvDims& d)
     d.plane_id = pl->prm.plane_id;
 }
 
-wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_depos* depos,
-                       float* const* waves, cudaStream_t s)
+// Batch scratch of plane pl for its k events (global batch indices idx[]), with their grid
+// slots reset where they are not known to be clean.  On success the grids are ready for
+// rasterization and pl->bclean holds the slots that will be clean after the run.
+wcsim_status prepare_group(wcsim_plane* pl, int k, int32_t* clean_after, cudaStream_t s)
 {
     wcsim_status st = reserve_batch(pl, k);
     if (st) return st;
     const ConvDims& d0 = pl->dims;
-    ConvDims d = d0;
-    d.ev_grid = (int64_t)ev_grid_elems(d0);
-    d.ev_shat = (int64_t)ev_shat_elems(d0);
-    d.ev_mt = (int64_t)ev_mt_elems(d0);
-    cudaError_t e = cudaMemsetAsync(pl->bgrid, 0, (size_t)k * ev_grid_elems(d0) * sizeof(float), s);
-    if (e) return cuda_fail(e, "batch grid reset");
+    // the time-axis transform clears each grid as it reads it (consume and clear), so a grid
+    // slot needs a reset only before its first use after an allocation or a failed run
+    if (pl->bclean < k) {
+        cudaError_t e = cudaMemsetAsync(pl->bgrid, 0, (size_t)k * ev_grid_elems(d0) * sizeof(float), s);
+        if (e) return cuda_fail(e, "batch grid reset");
+    }
+    *clean_after = pl->bclean > k ? pl->bclean : k;
+    pl->bclean = 0;                     // until the run has been enqueued in full
+    return WCSIM_OK;
+}
+
+// The per-plane rasterization of events idx[0..k) (when the batch's queue launch does not
+// apply) into their grid slots.
+wcsim_status rasterize_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_depos* depos,
+                             cudaStream_t s)
+{
+    const ConvDims& d0 = pl->dims;
     RasterConsts c = make_consts(pl);
     BatchEvents ev;
     ev.n = k;
@@ -447,9 +464,25 @@ wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_d
         ev.key1[i] = (uint32_t)(seed >> 32);
         ev.block_start[i + 1] = ev.block_start[i] + rasterize_blocks(dp->n, c.depos_per_block);
     }
-    if ((e = launch_rasterize_batch(c, ev, pl->flags, s))) return cuda_fail(e, "batch rasterize launch");
+    cudaError_t e = launch_rasterize_batch(c, ev, pl->flags, s);
+    return e ? cuda_fail(e, "batch rasterize launch") : WCSIM_OK;
+}
+
+// Eq. 2 for the k events of plane pl whose grids are rasterized: one launch per stage over
+// the k events.
+wcsim_status convolve_group(wcsim_plane* pl, int k, const int32_t* idx, float* const* waves,
+                            int32_t clean_after, cudaStream_t s)
+{
+    const ConvDims& d0 = pl->dims;
+    ConvDims d = d0;
+    d.ev_grid = (int64_t)ev_grid_elems(d0);
+    d.ev_shat = (int64_t)ev_shat_elems(d0);
+    d.ev_mt = (int64_t)ev_mt_elems(d0);
+    d.clear_input = 1;
+    cudaError_t e;
     if ((e = launch_rows_r2c_batch(d, pl->pt, pl->bgrid, pl->bshat, k, s)))
         return cuda_fail(e, "batch rows_r2c launch");
+    d.clear_input = 0;
     if (pl->tw_warp && !pl->wire_block) {
         if ((e = launch_wire_warp(d, pl->tw_warp, pl->bshat, pl->H, pl->bmt, pl->flags, s, k)))
             return cuda_fail(e, "batch wire launch");
@@ -466,6 +499,7 @@ wcsim_status run_group(wcsim_plane* pl, int k, const int32_t* idx, const wcsim_d
     }
     with_noise(pl, d);
     if ((e = launch_rows_c2r_batch(d, pl->pt, pl->bmt, w, k, s))) return cuda_fail(e, "batch rows_c2r launch");
+    pl->bclean = clean_after;
     return WCSIM_OK;
 }
 
@@ -546,6 +580,7 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     WC_TRY(cudaMalloc(&pl->shat, n_rows * cols * sizeof(float2)), "spectrum allocation");
     WC_TRY(cudaMalloc(&pl->mt, (size_t)d.n_w * cols * sizeof(float2)), "spectrum allocation");
     WC_TRY(cudaMalloc(&pl->flags, sizeof(int)), "flag allocation");
+    WC_TRY(cudaMalloc(&pl->queue, sizeof(int)), "queue counter allocation");
     WC_TRY(cudaMalloc(&pl->fs.cnt, (size_t)(d.n_w + 1) * sizeof(int32_t)), "bin count allocation");
     WC_TRY(cudaMalloc(&pl->fs.off, (size_t)(d.n_w + 2) * sizeof(int32_t)), "bin offset allocation");
     WC_TRY(cudaMemsetAsync(pl->fs.cnt, 0, (size_t)(d.n_w + 1) * sizeof(int32_t), s), "bin count reset");
@@ -825,18 +860,62 @@ wcsim_status wcsim_batch_run(int32_t n_events, wcsim_plane* const* planes,
     DeviceGuard dg(planes[0]->device);
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
-    // group events by plane, in order of first appearance
-    bool done[kMaxBatch] = {};
-    int32_t idx[kMaxBatch];
+    // group events by plane, in order of first appearance; slot[e]: event e's grid slot in
+    // its plane's batch scratch
+    int32_t slot[kMaxBatch], first[kMaxBatch], count[kMaxBatch];
+    int32_t members[kMaxBatch][kMaxBatch], clean_after[kMaxBatch];
+    int n_groups = 0;
     for (int i = 0; i < n_events; ++i) {
-        if (done[i]) continue;
-        int k = 0;
-        for (int j = i; j < n_events; ++j)
-            if (!done[j] && planes[j] == planes[i]) {
-                idx[k++] = j;
-                done[j] = true;
-            }
-        wcsim_status st = run_group(planes[i], k, idx, depos, waves, s);
+        int g = 0;
+        while (g < n_groups && planes[first[g]] != planes[i]) ++g;
+        if (g == n_groups) {
+            first[g] = i;
+            count[g] = 0;
+            ++n_groups;
+        }
+        slot[i] = count[g];
+        members[g][count[g]++] = i;
+    }
+    for (int g = 0; g < n_groups; ++g) {
+        wcsim_status st = prepare_group(planes[first[g]], count[g], &clean_after[g], s);
+        if (st) return st;
+    }
+    // one persistent rasterization over every event of the batch (a work queue of (event,
+    // depo block) items) when the planes share the rasterization tile and the kind of
+    // fluctuation draw; otherwise one launch per plane
+    bool queue = true;
+    const RasterConsts c0 = make_consts(planes[0]);
+    for (int i = 1; i < n_events && queue; ++i) {
+        const wcsim_plane* p = planes[i];
+        queue = p->kd == planes[0]->kd && p->kg == planes[0]->kg &&
+                (p->prm.fluctuate == 2) == (c0.fluctuate == 2);
+    }
+    if (queue) {
+        QueueEvents q;
+        q.n = n_events;
+        q.block_start[0] = 0;
+        for (int i = 0; i < n_events; ++i) {
+            wcsim_plane* p = planes[i];
+            q.c[i] = make_consts(p);
+            const uint64_t seed = p->prm.seed + (uint64_t)i;         // per-event stream
+            q.c[i].key0 = (uint32_t)seed;
+            q.c[i].key1 = (uint32_t)(seed >> 32);
+            q.d[i] = depo_arrays(&depos[i]);
+            q.grid[i] = p->bgrid + (size_t)slot[i] * ev_grid_elems(p->dims);
+            q.flags[i] = p->flags;
+            q.block_start[i + 1] = q.block_start[i] + rasterize_blocks(depos[i].n, c0.depos_per_block);
+        }
+        cudaError_t e = launch_rasterize_queue(q, planes[0]->queue, s);
+        if (e) return cuda_fail(e, "batch rasterize launch");
+    } else {
+        for (int g = 0; g < n_groups; ++g) {
+            wcsim_status st = rasterize_group(planes[first[g]], count[g], members[g], depos, s);
+            if (st) return st;
+        }
+    }
+    for (int g = 0; g < n_groups; ++g) {
+        wcsim_status st = convolve_group(planes[first[g]], count[g], members[g], waves,
+                                         clean_after[g], s);
         if (st) return st;
     }
     return WCSIM_OK;

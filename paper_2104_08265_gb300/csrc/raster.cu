@@ -222,6 +222,28 @@ k_rasterize_batch(RasterConsts c, BatchEvents ev, int* flags)
                                 (int64_t)blockIdx.x - ev.block_start[e]);
 }
 
+// Every event of a batch over a work queue: each CTA pops (event, depo block) items until the
+// queue is empty (events of different planes carry their own constants).
+template <int KD, int G, bool BIN>
+__global__ void __launch_bounds__(kWarps * 32)
+k_rasterize_queue(QueueEvents q, int* queue)
+{
+    __shared__ int s_item;
+    const int total = q.block_start[q.n];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();                   // every thread has the item before s_item is reused
+        if (item >= total) break;
+        int e = 0;
+        while (e + 1 < q.n && q.block_start[e + 1] <= item) ++e;
+        rasterize_block<KD, G, BIN>(q.c[e], q.d[e], q.grid[e], q.flags[e],
+                                    (int64_t)item - q.block_start[e]);
+        __syncthreads();                   // the block's shared tiles are reused by the next item
+    }
+}
+
 // Sum over the G lanes of a lane group (mask: the group's lanes), in every lane of it.
 template <int G>
 __device__ __forceinline__ float group_sum(float v, unsigned mask)
@@ -532,6 +554,29 @@ cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev,
             k_rasterize_batch<KD, G, true><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags);       \
         else                                                                                   \
             k_rasterize_batch<KD, G, false><<<blocks, kWarps * 32, 0, s>>>(c, ev, flags);      \
+    }
+    WCSIM_RASTER_TILES(WCSIM_TILE_CASE)
+#undef WCSIM_TILE_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rasterize_queue(const QueueEvents& q, int* queue, cudaStream_t s)
+{
+    const int total = q.block_start[q.n];
+    if (q.n <= 0 || total <= 0) return cudaSuccess;
+    const RasterConsts& c = q.c[0];
+    if (!raster_tile_supported(c.depos_per_block, c.lanes_per_depo)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), s);
+    if (e) return e;
+#define WCSIM_TILE_CASE(KD, G)                                                                 \
+    if (c.depos_per_block == KD && c.lanes_per_depo == G) {                                    \
+        auto k = (c.fluctuate == 2) ? k_rasterize_queue<KD, G, true>                           \
+                                    : k_rasterize_queue<KD, G, false>;                         \
+        int per_sm = 0;                                                                        \
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, 0)))   \
+            return e;                                                                          \
+        const int resident = (per_sm > 0 ? per_sm : 1) * sm_count();                           \
+        k<<<total < resident ? total : resident, kWarps * 32, 0, s>>>(q, queue);               \
     }
     WCSIM_RASTER_TILES(WCSIM_TILE_CASE)
 #undef WCSIM_TILE_CASE

@@ -55,6 +55,17 @@ struct BatchEvents {
     uint32_t key0[kMaxBatch], key1[kMaxBatch];
 };
 
+// Every event of a batch, whatever its plane, for one persistent rasterization over a work
+// queue of (event, depo block) items; passed by value.
+struct QueueEvents {
+    int32_t n;
+    int32_t block_start[kMaxBatch + 1];  // first item of each event (prefix sum)
+    RasterConsts c[kMaxBatch];           // the event's plane constants and fluctuation key
+    DepoArrays d[kMaxBatch];
+    float* grid[kMaxBatch];
+    int* flags[kMaxBatch];               // the event's plane's flag word
+};
+
 struct WavePtrs {
     float* p[kMaxBatch];
     int32_t ev[kMaxBatch];     // event index within the caller's batch (noise key offset)
@@ -68,6 +79,10 @@ cudaError_t launch_windows(const RasterConsts& c, const DepoArrays& d, int32_t* 
 cudaError_t launch_rasterize_batch(const RasterConsts& c, const BatchEvents& ev, int* flags,
                                    cudaStream_t s);
 int rasterize_blocks(int64_t n_depos, int depos_per_block);
+// Rasterize every event of q in one persistent launch: CTAs pop (event, block) items from
+// *queue (zeroed here on the stream first) until all q.block_start[q.n] are done.  All events
+// use the tile (depos_per_block, lanes_per_depo) and fluctuation mode of q.c[0].
+cudaError_t launch_rasterize_queue(const QueueEvents& q, int* queue, cudaStream_t s);
 // Whether the rasterizers have an instance for this tile (depos per CTA, lanes per depo).
 bool raster_tile_supported(int depos_per_block, int lanes_per_depo);
 // Adjoint of drift + rasterization (mean path, windows fixed): dgrid -> per-depo and global

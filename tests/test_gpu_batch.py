@@ -89,3 +89,41 @@ def test_batch_limits(W):
     L = W.lib()
     assert L.wcsim_batch_run(W.MAX_BATCH + 1, None, None, None, None) == W.ESHAPE
     assert L.wcsim_batch_run(0, None, None, None, None) == W.OK
+
+
+def test_batch_per_plane_rasterization_fallback_and_repeated_runs(W):
+    """Planes with different rasterization tiles (or an exact-binomial plane among others)
+    cannot share the one queued rasterization: each plane's events are rasterized in their
+    own launch.  Repeated runs with other depos must start from clean grids (each grid is
+    cleared as its transform reads it)."""
+    specs, prm, planes, events = small_batch(W)
+    planes["B"].set_raster_tile(128, 16)
+    dev = [W.DeviceDepos.from_host(d) for _, d in events]
+    b = W.Batch([planes[k] for k, _ in events], dev)
+    for rep in range(3):
+        got = [w.cpu().numpy() for w in b.run()]
+        for e, (k, d) in enumerate(events):
+            pl = planes[k]
+            pl.set_params(dataclasses.replace(prm, seed=prm.seed + e))
+            ref = pl.run(dev[e]).cpu().numpy()
+            pl.set_params(prm)
+            r, m = rel(got[e], ref)
+            assert r <= 1e-5 and m <= 1e-4, (rep, e, k, r, m)
+        # next round: other charges in place (same arrays, same batch)
+        for dv in dev:
+            dv.q.mul_(0.5)
+    # an exact-binomial plane among normal-approximation ones
+    g, kind = specs["C"]
+    import torch
+    binp = W.Plane(g, dataclasses.replace(prm, fluctuate=2),
+                   torch.from_numpy(S.make_response(g, kind)).cuda())
+    mixed = [planes["A"], binp, planes["A"]]
+    dsets = [dev[0], dev[3], dev[2]]
+    got = [w.cpu().numpy() for w in W.Batch(mixed, dsets).run()]
+    for e, (pl, dv) in enumerate(zip(mixed, dsets)):
+        p0 = pl.params
+        pl.set_params(dataclasses.replace(p0, seed=p0.seed + e))
+        ref = pl.run(dv).cpu().numpy()
+        pl.set_params(p0)
+        r, m = rel(got[e], ref)
+        assert r <= 1e-5 and m <= 1e-4, ("mixed", e, r, m)
