@@ -220,13 +220,14 @@ def write_traffic(reps):
             b = sum(float(r[c].replace(",", "")) * scale[units[c]] for c in cols)
             acc.setdefault(kernel_base(r[ki]), []).append(b)
     rec = {"_about": "DRAM bytes (read + write) per launch, mean over the captured launches, "
-                     "from ncu --set full captures of the 960-wire x 6000-tick plane with 100k "
-                     "depos; valid only while the CUDA sources hash to source_sha256.",
+                     "from ncu --set full captures (one kernel and one launch per capture) of the "
+                     "960-wire x 6000-tick plane with 100k depos; valid only while the CUDA "
+                     "sources hash to source_sha256.",
            "capture": ("CMD='python bench.py --steps 1 --warmup 1 --no-autotune --no-batch "
                        "--no-event --no-cpu-baseline --no-cufft --no-e2e --no-noise --soak-s 0'; "
-                       "for K in <each kernel>; do ncu --metrics dram__bytes_read.sum,"
-                       "dram__bytes_write.sum --clock-control none -k regex:$K -s 1 -c 1 -o $K "
-                       "$CMD; done; then python bench.py --write-traffic <the reports>"),
+                       "for K in <each kernel>; do $CMD && ncu --set full --import-source no "
+                       "--clock-control none -k regex:$K -s 1 -c 1 -o prof_$K $CMD; done; then "
+                       "python bench.py --write-traffic <the reports>"),
            "reports": [os.path.basename(r) for r in reps],
            "source_sha256": source_hash(),
            "bytes_per_launch": {k: float(np.mean(v)) for k, v in sorted(acc.items())}}
