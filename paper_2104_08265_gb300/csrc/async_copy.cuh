@@ -62,6 +62,30 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Tensor store: the box of the 5-D tensor map at `map` (a kernel parameter) whose first
+// element has coordinates (c0 .. c4) <- shared memory at src (128-byte aligned, the box in
+// dense order).  Completion is tracked by bulk groups (bulk_commit / bulk_wait_read).
+__device__ __forceinline__ void tma_store_5d(const void* map, const void* src, int c0, int c1,
+                                             int c2, int c3, int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];"
+        ::"l"(map), "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit()
+{
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Wait until every committed bulk group of this thread has finished reading shared memory
+// (the source may then be reused or released).
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;

@@ -13,8 +13,10 @@
 // brings both rows of the next pair into a two-stage shared buffer while the previous pair
 // is transformed.  The inverse kernel stages its Hermitian input (each element read once,
 // its mirror written from the same load) and writes 4 ticks per 16-byte store.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "async_copy.cuh"
 #include "fft_engine.cuh"
@@ -133,6 +135,79 @@ __device__ __forceinline__ void store_pair_spectra(const ConvDims& d, const floa
     }
 }
 
+// Shared offset (complex values) of row 1's flat half spectrum: 4 nkb rounded up to 128 bytes.
+__host__ __device__ inline int flat_row1(int nkb) { return (kBlockCols * nkb + 15) & ~15; }
+
+// The first 128-byte aligned complex slot at or after p (a TMA box in shared memory starts
+// on a 128-byte boundary): at most kFlatSlack slots further.
+constexpr int kFlatSlack = 15;
+__device__ __forceinline__ float2* align128(float2* p)
+{
+    const uint32_t a = smem_u32(p);
+    return p + (((128u - (a & 127u)) & 127u) >> 3);
+}
+
+// Separate the pair's half spectra as store_pair_spectra does, into flat shared rows for the
+// TMA box stores: row 0's X0[k] at f[k], row 1's X1[k] at f[o1 + k], zeros for nh <= k < nk.
+// NI > 0: f may alias z; every thread first reads its NI frequencies k = tid + i T (NI T >= nh)
+// into registers, the block synchronises, then writes.  NI = 0: f and z are distinct buffers.
+// Ends with a proxy fence and a block barrier (the async proxy may then read f).
+template <int NI, int T>
+__device__ __forceinline__ void separate_flat(const float2* z, int N, int nh, int nk, int o1,
+                                              float2* f)
+{
+    auto sep = [&](int k, float2& x0, float2& x1) {
+        const float2 a = z[pad16(k)];
+        const float2 b = z[k == 0 ? 0 : pad16(N - k)];
+        x0 = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        x1 = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+    };
+    if constexpr (NI > 0) {
+        float2 a0[NI], a1[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int k = threadIdx.x + i * T;
+            if (k < nh) sep(k, a0[i], a1[i]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int k = threadIdx.x + i * T;
+            if (k < nh) {
+                f[k] = a0[i];
+                f[o1 + k] = a1[i];
+            }
+        }
+    } else {
+        for (int k = threadIdx.x; k < nh; k += T) {
+            float2 x0, x1;
+            sep(k, x0, x1);
+            f[k] = x0;
+            f[o1 + k] = x1;
+        }
+    }
+    for (int k = nh + threadIdx.x; k < nk; k += T) f[k] = f[o1 + k] = make_float2(0.f, 0.f);
+    fence_proxy_async_smem();
+    __syncthreads();
+}
+
+// One thread stores the flat rows f (row 0) and f + o1 (row 1, if has1) of rows r0, r0 + 1 of
+// event ev through the tensor map, bk frequency blocks per box, and waits until the copies
+// have read shared memory.  Boxes past nkb are clipped by the copy.
+__device__ __forceinline__ void tma_store_pair(const ConvDims& d, const CUtensorMap* map,
+                                               const float2* f, int o1, int bk, int64_t r0,
+                                               bool has1, int ev)
+{
+    const int w0 = (int)(r0 / d.n_imp), j0 = (int)(r0 % d.n_imp);
+    const int w1 = (int)((r0 + 1) / d.n_imp), j1 = (int)((r0 + 1) % d.n_imp);
+    for (int kb = 0; kb < d.nkb; kb += bk) {
+        tma_store_5d(map, f + kBlockCols * kb, 0, w0, kb, j0, ev);
+        if (has1) tma_store_5d(map, f + o1 + kBlockCols * kb, 0, w1, kb, j1, ev);
+    }
+    bulk_commit();
+    bulk_wait_read();
+}
+
 __host__ __device__ inline size_t staged_smem(int n_t, int n)
 {
     return 2 * 2 * (size_t)n_t * sizeof(float) + 2 * (size_t)padded_len(n) * sizeof(float2) +
@@ -196,10 +271,12 @@ k_rows_r2c_staged(ConvDims d, FftPlan p, const float* __restrict__ grid, float2*
 // pf_ahead > 0: CTA b first asks L2 for the rows of pair b + pf_ahead (the CTA that will
 // most likely take over its slot once it retires), so that pair's first pass reads L2.
 // FIX: compile-time plan variant (fixed_plan_of(p)).
+// bk > 0: the half spectra leave through TMA box stores of bk frequency blocks (map: the
+// blocked spectra, events along its last dimension); bk = 0: plain stores.
 template <int FIX>
 __global__ void __launch_bounds__(kDirectThreads, FIX == kPlanRuntime ? 2 : 3)
 k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __restrict__ shat,
-                  int pf_ahead)
+                  int pf_ahead, const __grid_constant__ CUtensorMap map, int bk)
 {
     extern __shared__ __align__(128) unsigned char smraw[];
     const int N = p.n;
@@ -227,6 +304,20 @@ k_rows_r2c_direct(ConvDims d, FftPlan p, float* __restrict__ grid, float2* __res
         return;
     }
     const float2* z = run_row_plan<false, FIX, kDirectThreads>(p, X, Y);
+    if (bk > 0) {
+        const int o1 = flat_row1(d.nkb);
+        if constexpr (FIX == kPlan6000) {
+            constexpr int NI = (6000 / 2 + 1 + kDirectThreads - 1) / kDirectThreads;
+            float2* f = align128(X);
+            separate_flat<NI, kDirectThreads>(z, N, d.nh, kBlockCols * d.nkb, o1, f);
+            if (threadIdx.x == 0) tma_store_pair(d, &map, f, o1, bk, r0, has1, blockIdx.y);
+        } else {
+            float2* f = align128((z == X) ? Y : X);
+            separate_flat<0, kDirectThreads>(z, N, d.nh, kBlockCols * d.nkb, o1, f);
+            if (threadIdx.x == 0) tma_store_pair(d, &map, f, o1, bk, r0, has1, blockIdx.y);
+        }
+        return;
+    }
     store_pair_spectra(d, z, N, r0, has1, shat);
 }
 
@@ -274,6 +365,23 @@ int r2c_prefetch_ahead(const ConvDims& d, const float* grid, K k, size_t smem)
     return per_sm * sm_count();
 }
 
+// The TMA store setup of the direct R2C kernel for n_ev events of spectra at shat: the map
+// and its box size, or bk = 0 (plain stores) when disabled, unmappable, or when the flat rows
+// plus the clipped tail of the last box, from a 128-byte aligned start, do not fit one
+// padded_len(n) buffer.
+int r2c_store_map(const ConvDims& d, const FftPlan& pt, int fix, const float2* shat, int n_ev,
+                  CUtensorMap* map)
+{
+    memset(map, 0, sizeof(*map));
+    if (!d.spectra_tma) return 0;
+    const int bk = blocked_box_kb(d.nkb);
+    const int64_t span = (int64_t)((d.nkb + bk - 1) / bk) * bk * kBlockCols;
+    if (kFlatSlack + flat_row1(d.nkb) + span > (int64_t)padded_len(pt.n)) return 0;
+    (void)fix;   // both plan variants write the flat rows into one padded_len(n) buffer
+    if (!blocked_spectra_map(shat, d.n_w, d.nkb, d.n_imp, n_ev, d.ev_shat, map)) return 0;
+    return bk;
+}
+
 DeviceOnce g_attr;
 cudaError_t attrs()
 {
@@ -307,8 +415,10 @@ cudaError_t launch_rows_r2c(const ConvDims& d, const FftPlan& pt, const float* g
         const int fix = fixed_plan_of(pt);
         auto k = fix == kPlan6000 ? k_rows_r2c_direct<kPlan6000> : k_rows_r2c_direct<kPlanRuntime>;
         const size_t sm = row_plan_smem(fix, pt.n);
+        CUtensorMap map;
+        const int bk = r2c_store_map(d, pt, fix, shat, 1, &map);
         k<<<(unsigned)n_pairs, kDirectThreads, sm, s>>>(d, pt, const_cast<float*>(grid), shat,
-                                                        r2c_prefetch_ahead(d, grid, k, sm));
+                                                        r2c_prefetch_ahead(d, grid, k, sm), map, bk);
     }
     return cudaGetLastError();
 }
@@ -344,8 +454,10 @@ cudaError_t launch_rows_r2c_batch(const ConvDims& d, const FftPlan& pt, const fl
     const int fix = fixed_plan_of(pt);
     auto k = fix == kPlan6000 ? k_rows_r2c_direct<kPlan6000> : k_rows_r2c_direct<kPlanRuntime>;
     const size_t sm = row_plan_smem(fix, pt.n);
+    CUtensorMap map;
+    const int bk = r2c_store_map(d, pt, fix, shat, n_ev, &map);
     k<<<g, kDirectThreads, sm, s>>>(d, pt, const_cast<float*>(grid), shat,
-                                    r2c_prefetch_ahead(d, grid, k, sm));
+                                    r2c_prefetch_ahead(d, grid, k, sm), map, bk);
     return cudaGetLastError();
 }
 

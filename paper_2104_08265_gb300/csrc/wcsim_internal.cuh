@@ -6,6 +6,8 @@
 
 #include "../../include/wcsim.h"
 
+struct CUtensorMap_st;     // the driver's tensor map (cuda.h), by pointer only here
+
 namespace wcsim {
 
 // ------------------------------------------------------------------ depo rasterization
@@ -139,6 +141,7 @@ struct ConvDims {
     int32_t nkb;               // ceil(nh / kBlockCols)
     int32_t rows_variant;      // time-axis forward kernel: 0 direct loads, 1 bulk-staged
     int32_t clear_input;       // time-axis forward: write zeros over the rows it has read
+    int32_t spectra_tma = 1;   // time-axis forward: half spectra leave by TMA box stores
     // Batched runs: event e's grid, time-axis spectra and wire-summed spectra start
     // e * ev_grid, e * ev_shat and e * ev_mt elements after the first event's.
     int64_t ev_grid, ev_shat, ev_mt;
@@ -201,6 +204,15 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
 cudaError_t launch_wire_adjoint_block(const ConvDims& d, const FftPlan& pw, const float2* gt,
                                       float2* shat, const float2* H, float2* dR, float inv_n,
                                       cudaStream_t s);
+// TMA view of a blocked spectrum array [n_ev][n_j][nkb][n_w][4] complex (ev_stride complex
+// values from one event to the next): a 5-D FP32 tensor map whose box is one row's half
+// spectrum over blocked_box_kb(nkb) frequency blocks (4 complex values per block, dense in
+// shared memory).  False when the driver offers no encoder or the layout cannot be mapped
+// (base not 16-byte aligned); *out is then unspecified.
+constexpr int kMapBoxKb = 256;          // the TMA limit on a box dimension
+int blocked_box_kb(int nkb);
+bool blocked_spectra_map(const float2* base, int n_w, int nkb, int n_j, int n_ev,
+                         int64_t ev_stride, ::CUtensorMap_st* out);
 // Inverse time-axis FFT of every grid row from blocked spectra [n_imp][nkb][n_w][4].
 cudaError_t launch_rows_c2r_grid(const ConvDims& d, const FftPlan& pt, const float2* shat,
                                  float* grid, cudaStream_t s);

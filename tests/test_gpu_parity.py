@@ -183,15 +183,20 @@ def test_convolve_matches_oracle(W, case):
     assert_close(wave.cpu().numpy(), ref, what=str(case))
 
 
-@pytest.mark.parametrize("variant", [("", ""), ("staged", ""), ("", "block"), ("staged", "block")])
+@pytest.mark.parametrize("variant", [("", "", ""), ("staged", "", ""), ("", "block", ""),
+                                     ("staged", "block", ""), ("", "", "plain")])
 def test_kernel_variants_match_oracle(W, variant, monkeypatch):
-    """Every time-axis / wire-axis kernel variant on the 960 x 6000 plane."""
+    """Every time-axis / wire-axis kernel variant on the 960 x 6000 plane (the direct
+    time-axis kernel with TMA box stores of its half spectra, the default, and with plain
+    stores)."""
     import torch
-    rows, wire = variant
+    rows, wire, store = variant
     if rows:
         monkeypatch.setenv("WCSIM_ROWS_KERNEL", rows)
     if wire:
         monkeypatch.setenv("WCSIM_WIRE_KERNEL", wire)
+    if store:
+        monkeypatch.setenv("WCSIM_SPECTRA_STORE", store)
     rng = np.random.default_rng(41)
     g = S.Geometry(n_wires=960, n_imp=10, n_ticks=6000, pitch_mm=4.7)
     grid = np.zeros((g.n_rows, g.n_ticks), np.float32)
