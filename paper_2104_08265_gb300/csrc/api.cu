@@ -552,9 +552,9 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     // Kernel variant of the time-axis forward FFT; WCSIM_ROWS_KERNEL=staged|direct overrides.
     d.rows_variant = 0;
     if (const char* v = getenv("WCSIM_ROWS_KERNEL")) d.rows_variant = (strcmp(v, "staged") == 0) ? 1 : 0;
-    // Half spectra of the time-axis forward leave by TMA box stores; WCSIM_SPECTRA_STORE=plain
-    // selects per-thread stores.
-    if (const char* v = getenv("WCSIM_SPECTRA_STORE")) d.spectra_tma = strcmp(v, "plain") != 0;
+    // The time-axis kernels move blocked half spectra by TMA box copies; WCSIM_SPECTRA_TMA=0
+    // selects per-thread loads and stores.
+    if (const char* v = getenv("WCSIM_SPECTRA_TMA")) d.spectra_tma = strcmp(v, "0") != 0;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n_rows = (size_t)d.n_w * d.n_imp;
 #define WC_TRY(call, what)                                  \

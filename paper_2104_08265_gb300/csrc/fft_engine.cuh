@@ -481,6 +481,32 @@ __device__ __forceinline__ float2* run_plan(const FftPlan& p, const FirstLd& fir
 }
 
 // ------------------------------------------------------------------ compile-time plans
+// Apply the twiddles w^(r k), r = 1 .. R - 1, of a Stockham pass with stride NS to v[1 ..],
+// t = the pass's table + k (entry (r - 1) NS = w^(r k)).  Radix 15 loads only the entries of
+// r = 1, 5 and 10 and forms the rest as products of them (w^(3k) = w^(5k) conj(w^(2k)) and so
+// on, each at most three roundings away from correctly rounded table values), so a butterfly
+// reads 3 table entries instead of 14; other radices read every entry.
+template <int R, int NS, bool INV>
+__device__ __forceinline__ void apply_twiddles(float2* v, const float2* __restrict__ t)
+{
+    if constexpr (R == 15) {
+        const float2 a = __ldg(t), b = __ldg(t + 4 * NS), c = __ldg(t + 9 * NS);
+        const float2 na = make_float2(a.x, -a.y);                  // conj: w^(-k)
+        const float2 a2 = cmul(a, a), na2 = make_float2(a2.x, -a2.y);
+        const float2 a3 = cmul(b, na2), a4 = cmul(b, na);
+        float2 w[15];
+        w[1] = a;            w[2] = a2;            w[3] = a3;            w[4] = a4;
+        w[5] = b;            w[6] = cmul(b, a);    w[7] = cmul(b, a2);   w[8] = cmul(c, na2);
+        w[9] = cmul(c, na);  w[10] = c;            w[11] = cmul(c, a);   w[12] = cmul(c, a2);
+        w[13] = cmul(c, a3); w[14] = cmul(c, a4);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], w[r]);
+    } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], __ldg(t + (r - 1) * NS));
+    }
+}
+
 // One Stockham pass (single sequence) whose length N, radix R and stride NS are template
 // parameters, so that every divisor, stride and padded offset is a constant.  Same
 // arithmetic and twiddle table layout as pass_r.
@@ -500,11 +526,7 @@ __device__ __forceinline__ void pass_fixed(const Ld& ld, const St& st, const flo
             for (int r = 0; r < R; ++r) v[r] = ld(0, j + r * NB);
         }
         if constexpr (NS > 1) {
-            if (k > 0) {
-                const float2* t = tw + k;
-#pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = twiddle<INV>(v[r], __ldg(t + (r - 1) * NS));
-            }
+            if (k > 0) apply_twiddles<R, NS, INV>(v, tw + k);
         }
         dft<R, INV>(v);
         const int o = q * NS * R + k;
@@ -569,11 +591,7 @@ __device__ __forceinline__ void pass_fixed_inplace(const Ld& ld, float2* buf,
         if (j < NB) {
             const int q = j / NS, k = j - q * NS;
             if constexpr (NS > 1) {
-                if (k > 0) {
-                    const float2* t = tw + k;
-#pragma unroll
-                    for (int r = 1; r < R; ++r) v[i][r] = twiddle<INV>(v[i][r], __ldg(t + (r - 1) * NS));
-                }
+                if (k > 0) apply_twiddles<R, NS, INV>(v[i], tw + k);
             }
             dft<R, INV>(v[i]);
             const int o = q * NS * R + k;

@@ -39,7 +39,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
 
 }  // namespace
 
-int blocked_box_kb(int nkb) { return nkb < kMapBoxKb ? nkb : kMapBoxKb; }
+int blocked_box_kb(int nkb)
+{
+    if (nkb <= kMapBoxKb) return nkb;
+    const int nbox = (nkb + kMapBoxKb - 1) / kMapBoxKb;
+    return (((nkb + nbox - 1) / nbox) + 3) & ~3;    // balanced boxes, 128-byte multiples
+}
 
 bool blocked_spectra_map(const float2* base, int n_w, int nkb, int n_j, int n_ev,
                          int64_t ev_stride, ::CUtensorMap_st* out)

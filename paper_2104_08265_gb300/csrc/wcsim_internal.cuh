@@ -141,7 +141,7 @@ struct ConvDims {
     int32_t nkb;               // ceil(nh / kBlockCols)
     int32_t rows_variant;      // time-axis forward kernel: 0 direct loads, 1 bulk-staged
     int32_t clear_input;       // time-axis forward: write zeros over the rows it has read
-    int32_t spectra_tma = 1;   // time-axis forward: half spectra leave by TMA box stores
+    int32_t spectra_tma = 1;   // time-axis kernels: blocked half spectra by TMA box copies
     // Batched runs: event e's grid, time-axis spectra and wire-summed spectra start
     // e * ev_grid, e * ev_shat and e * ev_mt elements after the first event's.
     int64_t ev_grid, ev_shat, ev_mt;
@@ -210,6 +210,9 @@ cudaError_t launch_wire_adjoint_block(const ConvDims& d, const FftPlan& pw, cons
 // shared memory).  False when the driver offers no encoder or the layout cannot be mapped
 // (base not 16-byte aligned); *out is then unspecified.
 constexpr int kMapBoxKb = 256;          // the TMA limit on a box dimension
+// Frequency blocks per box: nkb itself up to the limit, else the fewest boxes of equal size,
+// rounded up to a multiple of 4 blocks (so that every box starts on a 128-byte boundary of a
+// dense shared buffer); the last box may reach past nkb (clipped by the copy).
 int blocked_box_kb(int nkb);
 bool blocked_spectra_map(const float2* base, int n_w, int nkb, int n_j, int n_ev,
                          int64_t ev_stride, ::CUtensorMap_st* out);

@@ -49,9 +49,16 @@ def plane_for(W, g, prm, R):
 
 
 @pytest.mark.parametrize("shape", [(128, 10, 1024, 128, 1024), (250, 4, 1000, 256, 1024),
-                                   (960, 10, 6000, 960, 6000)])
-def test_convolve_adjoint_matches_oracle(W, shape):
+                                   (960, 10, 6000, 960, 6000), (960, 10, 6000, 960, 6000, "0"),
+                                   (33, 3, 13500, 64, 13500)])
+def test_convolve_adjoint_matches_oracle(W, shape, monkeypatch):
+    """The adjoint of Eq. 2 against the oracle's, the time-axis kernels moving half spectra
+    by TMA box copies (the default) and, with a trailing "0", by per-thread loads and stores;
+    the last shape takes the runtime 13500-point plan with an odd wire count."""
     import torch
+    if len(shape) > 5:
+        monkeypatch.setenv("WCSIM_SPECTRA_TMA", shape[5])
+        shape = shape[:5]
     n_w, n_imp, n_t, n_fw, n_ft = shape
     rng = np.random.default_rng(n_w + n_t)
     g = S.Geometry(n_wires=n_w, n_imp=n_imp, n_ticks=n_t, pitch_mm=3.0)

@@ -184,10 +184,10 @@ def test_convolve_matches_oracle(W, case):
 
 
 @pytest.mark.parametrize("variant", [("", "", ""), ("staged", "", ""), ("", "block", ""),
-                                     ("staged", "block", ""), ("", "", "plain")])
+                                     ("staged", "block", ""), ("", "", "0")])
 def test_kernel_variants_match_oracle(W, variant, monkeypatch):
-    """Every time-axis / wire-axis kernel variant on the 960 x 6000 plane (the direct
-    time-axis kernel with TMA box stores of its half spectra, the default, and with plain
+    """Every time-axis / wire-axis kernel variant on the 960 x 6000 plane (the time-axis
+    kernels moving half spectra by TMA box copies, the default, and by per-thread loads and
     stores)."""
     import torch
     rows, wire, store = variant
@@ -196,7 +196,7 @@ def test_kernel_variants_match_oracle(W, variant, monkeypatch):
     if wire:
         monkeypatch.setenv("WCSIM_WIRE_KERNEL", wire)
     if store:
-        monkeypatch.setenv("WCSIM_SPECTRA_STORE", store)
+        monkeypatch.setenv("WCSIM_SPECTRA_TMA", store)
     rng = np.random.default_rng(41)
     g = S.Geometry(n_wires=960, n_imp=10, n_ticks=6000, pitch_mm=4.7)
     grid = np.zeros((g.n_rows, g.n_ticks), np.float32)
