@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "fft_engine.cuh"
 #include "warp_fft.cuh"
 #include "wcsim_internal.cuh"
@@ -46,6 +48,9 @@ k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __res
     load_wire_twiddles<M>(tw2, s_twf, nullptr);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb = blockIdx.x, c = warp, kt0 = kb * kBlockCols;
+    // impacts j0 <= j < j1 of this CTA (grid y splits the impacts; every part transforms G)
+    const int j0 = (int)((int64_t)blockIdx.y * d.n_imp / gridDim.y);
+    const int j1 = (int)((int64_t)(blockIdx.y + 1) * d.n_imp / gridDim.y);
     float2* tr = s_tr + warp * TR;
     float2* gcol = s_g + c * tile_ld(N);
 
@@ -59,14 +64,14 @@ k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __res
         }
     }
     __syncthreads();
-    store_tile_cols(s_g, N, tile_ld(N), g2d + (int64_t)kb * N * kBlockCols);
-    if (dR == nullptr || kt0 >= d.nh) return;            // uniform per CTA
+    if (blockIdx.y == 0) store_tile_cols(s_g, N, tile_ld(N), g2d + (int64_t)kb * N * kBlockCols);
+    if (dR == nullptr || kt0 >= d.nh || j0 >= j1) return;   // uniform per CTA
     const bool vec = (d.n_ft % 2) == 0 && (reinterpret_cast<uintptr_t>(dR) & 15) == 0;
     // S_j's column is loaded one impact ahead: the loads of S_{j+1} are in flight while the
     // rows of dL/dR_j are written
     float2 v[M];
-    load_col<M>(shat + (int64_t)kb * d.n_w * kBlockCols, c, d.n_w, lane, v);
-    for (int j = 0; j < d.n_imp; ++j) {
+    load_col<M>(shat + ((int64_t)j0 * d.nkb + kb) * d.n_w * kBlockCols, c, d.n_w, lane, v);
+    for (int j = j0; j < j1; ++j) {
         float2 u[32];
         __syncthreads();                                  // s_tr is read out
         warp_fft_fwd<M>(v, s_twf, tr, lane, u);
@@ -79,7 +84,7 @@ k_wire_adjoint_a(ConvDims d, const float2* __restrict__ tw2, const float2* __res
             }
         }
         __syncthreads();
-        if (j + 1 < d.n_imp)
+        if (j + 1 < j1)
             load_col<M>(shat + ((int64_t)(j + 1) * d.nkb + kb) * d.n_w * kBlockCols, c, d.n_w, lane, v);
         float2* dRj = dR + (int64_t)j * N * d.n_ft;
         // direct values (kw, kt0 + cc), kt < nh: pairs of columns as 16-byte stores
@@ -123,6 +128,8 @@ k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __res
     load_wire_twiddles<M>(tw2, nullptr, s_twi);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kb = blockIdx.x, c = warp;
+    const int j0 = (int)((int64_t)blockIdx.y * d.n_imp / gridDim.y);
+    const int j1 = (int)((int64_t)(blockIdx.y + 1) * d.n_imp / gridDim.y);
     float2* tr = s_tr + warp * TR;
 
     float2 g[32];
@@ -131,7 +138,7 @@ k_wire_adjoint_b(ConvDims d, const float2* __restrict__ tw2, const float2* __res
 #pragma unroll
         for (int k1 = 0; k1 < 32; ++k1) g[k1] = __ldg(gc + (int64_t)(lane + M * k1) * kBlockCols);
     }
-    for (int j = 0; j < d.n_imp; ++j) {
+    for (int j = j0; j < j1; ++j) {
         const int64_t blk = (int64_t)j * d.nkb + kb;
         float2 u[32];
         if (lane < M) {
@@ -181,6 +188,22 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
 
 #define WCSIM_ADJ_M(X) X(4) X(8) X(15) X(16) X(20) X(24) X(25) X(30)
 
+// Impact groups per frequency block for the one-warp adjoint on `slots` resident CTAs: the s
+// in 1 .. 4 that minimises the transform work, (n_imp + s) / (n_imp + 1) (every group also
+// transforms G), divided by the fill of the last wave of nkb s CTAs.
+int adjoint_split(int nkb, int n_imp, int slots)
+{
+    int best = 1;
+    double best_cost = 1e300;
+    for (int sp = 1; sp <= 4 && sp <= n_imp; ++sp) {
+        const double waves = (double)nkb * sp / slots;
+        const double fill = waves / std::ceil(waves);
+        const double cost = (double)(n_imp + sp) / (n_imp + 1) / fill;
+        if (cost < best_cost - 1e-9) { best = sp; best_cost = cost; }
+    }
+    return best;
+}
+
 DeviceOnce g_attr;
 
 }  // namespace
@@ -189,6 +212,9 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
                                      float2* shat, const float2* H, float2* g2d, float2* dR,
                                      float inv_n, cudaStream_t s)
 {
+    // impacts split over grid y: more, shorter CTAs for the same per-CTA footprint
+    const int split = d.adj_split > 0 ? (d.adj_split > d.n_imp ? d.n_imp : d.adj_split)
+                                      : adjoint_split(d.nkb, d.n_imp, 3 * sm_count());
     switch (d.n_fw / 32) {
 #define WCSIM_CASE(MM)                                                                           \
     case MM: {                                                                                   \
@@ -201,8 +227,9 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
             if (e) return e;                                                                    \
             attr_set.mark();                                                                    \
         }                                                                                       \
-        k_wire_adjoint_a<MM><<<d.nkb, kWarps * 32, smem_a, s>>>(d, tw2, gt, shat, g2d, dR, inv_n); \
-        k_wire_adjoint_b<MM><<<d.nkb, kWarps * 32, 0, s>>>(d, tw2, g2d, shat, H);               \
+        const dim3 grid(d.nkb, split), grid_a(d.nkb, dR ? split : 1);                           \
+        k_wire_adjoint_a<MM><<<grid_a, kWarps * 32, smem_a, s>>>(d, tw2, gt, shat, g2d, dR, inv_n); \
+        k_wire_adjoint_b<MM><<<grid, kWarps * 32, 0, s>>>(d, tw2, g2d, shat, H);                \
         break;                                                                                   \
     }
         WCSIM_ADJ_M(WCSIM_CASE)

@@ -555,6 +555,8 @@ wcsim_status wcsim_plane_create(const wcsim_geometry* geom, const void* resp_c64
     // The time-axis kernels move blocked half spectra by TMA box copies; WCSIM_SPECTRA_TMA=0
     // selects per-thread loads and stores.
     if (const char* v = getenv("WCSIM_SPECTRA_TMA")) d.spectra_tma = strcmp(v, "0") != 0;
+    // Impact groups of the one-warp wire adjoint (CTAs per frequency block); WCSIM_ADJ_SPLIT.
+    if (const char* v = getenv("WCSIM_ADJ_SPLIT")) d.adj_split = atoi(v);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n_rows = (size_t)d.n_w * d.n_imp;
 #define WC_TRY(call, what)                                  \

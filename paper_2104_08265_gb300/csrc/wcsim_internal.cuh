@@ -142,6 +142,8 @@ struct ConvDims {
     int32_t rows_variant;      // time-axis forward kernel: 0 direct loads, 1 bulk-staged
     int32_t clear_input;       // time-axis forward: write zeros over the rows it has read
     int32_t spectra_tma = 1;   // time-axis kernels: blocked half spectra by TMA box copies
+    int32_t adj_split = 0;     // one-warp wire adjoint: CTAs per frequency block (0: chosen
+                               // from the wave fill, adjoint_split)
     // Batched runs: event e's grid, time-axis spectra and wire-summed spectra start
     // e * ev_grid, e * ev_shat and e * ev_mt elements after the first event's.
     int64_t ev_grid, ev_shat, ev_mt;
