@@ -140,23 +140,28 @@ def stage_bytes(g, n_depos, mean_bins, fused=False):
     return out
 
 
-def backward_stage_bytes(g, n_depos, mean_bins, reused=False):
+def backward_stage_bytes(g, n_depos, mean_bins, reused=False, kept2d=False):
     """Algorithmic bytes per launch of each backward stage (wcsim_run_backward with dL/dR,
-    n_fw = n_wires, n_ft = n_ticks): S recomputed, S and G transformed, the wire adjoint
-    (reads S^, G^ and H; writes dL/dR in full [n_imp][n_fw][n_ft] and dL/dS^), the inverse
-    time FFT of dL/dS and the per-depo gather.  reused: the backward took the forward's S^
-    (wcsim_plane_set_reuse_forward), so S is neither recomputed nor transformed."""
+    n_fw = n_wires, n_ft = n_ticks): S recomputed, S and G transformed, the wire adjoint, the
+    inverse time FFT of dL/dS and the per-depo gather.  The wire adjoint reads S^ (or, kept2d,
+    the forward's 2D spectra of S), G^ and H, writes dL/dR in full [n_imp][n_fw][n_ft] and
+    dL/dS^, and passes G's 2D spectrum from part A to part B (written and read once).
+    reused: the backward took the forward's S^ (wcsim_plane_set_reuse_forward), so S is
+    neither recomputed nor transformed."""
     rows = g.n_rows
     nh = g.n_ticks // 2 + 1
-    spec = rows * nh * 8                    # S^ or dL/dS^, all impact positions
-    wspec = g.n_wires * nh * 8              # one plane-wide half spectrum (G^, M~)
+    spec = rows * nh * 8                    # S^, its 2D spectrum or dL/dS^, all impacts
+    wspec = g.n_wires * nh * 8              # one plane-wide half spectrum (G^, its 2D one)
+    dR = g.n_imp * g.n_wires * g.n_ticks * 8
     return {
         "bwd_zero": 0,                          # the preceding wcsim_run left the grid clear
         "bwd_rasterize": 0 if reused else n_depos * (32 + 4 * mean_bins),
         "bwd_r2c_S": 0 if reused else rows * g.n_ticks * 4 + spec,
         "bwd_r2c_G": g.n_wires * g.n_ticks * 4 + wspec,
-        "bwd_wire_adjoint": (spec + wspec + g.n_imp * g.n_wires * g.n_ticks * 8   # part A
-                             + spec + g.n_imp * g.n_wires * nh * 8 + spec),          # part B
+        # part A: G^ in, G's 2D spectrum out, S (or its 2D spectra) in, dL/dR out;
+        # part B: G's 2D spectrum and H in, dL/dS^ out
+        "bwd_wire_adjoint": (wspec + wspec + spec + dR) + (wspec + spec + spec)
+                            + (wspec if kept2d else 0),   # the row kernel reads G's again
         "bwd_c2r_dS": spec + rows * g.n_ticks * 4,
         "bwd_depo_adjoint": n_depos * (32 + 20 + 4 * mean_bins),
     }
@@ -674,8 +679,9 @@ def run_gpu(args):
         plane.set_params(tgt)
         m_target = plane.run(dd).clone()
         plane.set_params(dataclasses.replace(prm, fluctuate=0))
-        # the backward takes the spectra its forward just computed (same depos, mean path)
-        plane.set_reuse_forward(True)
+        # the backward takes the spectra its forward just computed (same depos, mean path),
+        # and dL/dR from the 2D spectra of S the forward's wire pass kept
+        plane.set_reuse_forward(True, keep_wire_spectra=True)
         G = torch.empty_like(wave)
 
         def fb_step():
@@ -785,7 +791,7 @@ def run_gpu(args):
         return
     hbm, peak_kind = peaks()
     sb = stage_bytes(g, len(d), mean_bins, fused=fused)
-    bsb = backward_stage_bytes(g, len(d), mean_bins, reused=True)
+    bsb = backward_stage_bytes(g, len(d), mean_bins, reused=True, kept2d=True)
     avg = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     stages = {k: {"ms": avg[k], "GB/s": sb[k] / (avg[k] * 1e-3) / 1e9 if avg[k] > 0 else None,
                   "alg_bytes": sb[k]} for k in avg}
@@ -815,6 +821,9 @@ def run_gpu(args):
         "backward_stages": ({k: {"ms": v, "alg_bytes": bsb[k],
                                  "GB/s": bsb[k] / (v * 1e-3) / 1e9 if v > 0 else None}
                              for k, v in bwd_stages.items()} if bwd_stages else None),
+        "fit_step": ("wcsim_run (mean path) then wcsim_run_backward with dL/dR, the backward "
+                     "taking the forward's spectra and the 2D spectra of S its wire pass kept "
+                     "(wcsim_plane_set_reuse_forward mode 2)") if bwd_stages else None,
         "mean_bins_per_depo": mean_bins,
         "wall_s_timed_loop": wall,
         "cufft_comparison": cufft,

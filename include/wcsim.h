@@ -202,8 +202,15 @@ wcsim_status wcsim_run_backward(wcsim_plane* plane, const wcsim_depos* depos,
  * a forward's activations for its backward): the arrays are recognised by their pointers and
  * count only, so arrays freed and reallocated at the same addresses with other contents would
  * be taken for the forward's.  Any other compute call on the plane drops the spectra.
- * enable = 0 (the default): the backward always recomputes.  Calling it (with either value)
- * also drops any kept spectra.  Host-only. */
+ * enable = 2: as 1, and such a forward's wire pass also writes the 2D spectra of S (the wire
+ * FFT of every impact's time-axis spectra, n_imp * n_fw * 4 ceil((n_ft / 2 + 1) / 4) complex
+ * values, allocated here) when the plane runs the one-warp wire pass (n_fw = 32 M; otherwise
+ * 2 acts as 1); a backward that wants dL/dR then reads them instead of transforming the
+ * spectra of S again, which moves the cost of those transforms into one extra write in the
+ * forward.  enable = 0 (the default): the backward always recomputes.  Calling it (with any
+ * value) drops any kept spectra, and a value other than 2 frees the 2D spectra's buffer
+ * (synchronising the device).  WCSIM_EINVAL for other values, WCSIM_ENOMEM if the buffer
+ * cannot be allocated.  Host-only. */
 wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* plane, int32_t enable);
 
 /* Forward variant of wcsim_run / wcsim_run_adc.  fused = 0 (the default): the flow of Sec.

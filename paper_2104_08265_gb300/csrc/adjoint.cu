@@ -186,6 +186,63 @@ k_rows_c2r_grid(ConvDims d, FftPlan p, const float2* __restrict__ shat, float* _
     store_real_pair(z, o0, o1, d.n_t, has1, vec);
 }
 
+// dL/dR_j(kw, kt) = conj(S_j^(kw, kt)) G^(kw, kt) / n and its Hermitian mirror (-kw, -kt)
+// (as part A writes them), from the 2D spectra of S kept by the forward's wire pass (s2d,
+// time-frequency major [n_imp][4 nkb][n_fw]) and G's 2D spectrum (g2d, blocked
+// [nkb][n_fw][4]).  A CTA takes a tile of 32 time frequencies x 32 wire frequencies and
+// loops over the impacts: each warp reads 4 columns of the tile (consecutive lanes on
+// consecutive wire frequencies), the products pass through a padded shared tile, and each
+// warp then writes 4 rows of dL/dR_j (32 consecutive time frequencies, 256 bytes) and the
+// 4 mirrored rows (reversed, also contiguous): whole lines out, where part A writes 32-byte
+// pieces 48 KB apart.  G^'s tile is read once for all impacts.
+constexpr int kDrTile = 32;
+
+__global__ void __launch_bounds__(256)
+k_dr_tiles(ConvDims d, const float2* __restrict__ s2d, const float2* __restrict__ g2d,
+           float2* __restrict__ dR, float inv_n)
+{
+    __shared__ float2 t[kDrTile][kDrTile + 1];        // [kt][kw], padded
+    const int N = d.n_fw, ncol = kBlockCols * d.nkb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kt0 = blockIdx.x * kDrTile, kw0 = blockIdx.y * kDrTile;
+    const int kw = kw0 + lane;
+    // this thread's 4 elements: time frequencies kt0 + 4 warp + i, wire frequency kw
+    float2 g[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int kt = kt0 + 4 * warp + i;
+        g[i] = (kt < d.nh && kw < N)
+                   ? __ldg(g2d + ((int64_t)(kt >> 2) * N + kw) * kBlockCols + (kt & 3))
+                   : make_float2(0.f, 0.f);
+    }
+    for (int j = 0; j < d.n_imp; ++j) {
+        float2 u[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int kt = kt0 + 4 * warp + i;
+            u[i] = (kt < d.nh && kw < N) ? __ldcs(s2d + ((int64_t)j * ncol + kt) * N + kw)
+                                         : make_float2(0.f, 0.f);
+        }
+        __syncthreads();                                // the previous impact's tile is read
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            t[4 * warp + i][lane] = make_float2(inv_n * (u[i].x * g[i].x + u[i].y * g[i].y),
+                                                inv_n * (u[i].x * g[i].y - u[i].y * g[i].x));
+        __syncthreads();
+        float2* dRj = dR + (int64_t)j * N * d.n_ft;
+        const int kt = kt0 + lane;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * warp + i, w = kw0 + r;       // row kw = w, column kt
+            if (w >= N) break;
+            const float2 v = t[lane][r];
+            if (kt < d.nh) __stcs(dRj + (int64_t)w * d.n_ft + kt, v);
+            if (kt >= 1 && kt < d.nh && d.n_ft - kt >= d.nh)
+                __stcs(dRj + (int64_t)((N - w) % N) * d.n_ft + (d.n_ft - kt), make_float2(v.x, -v.y));
+        }
+    }
+}
+
 #define WCSIM_ADJ_M(X) X(4) X(8) X(15) X(16) X(20) X(24) X(25) X(30)
 
 // Impact groups per frequency block for the one-warp adjoint on `slots` resident CTAs: the s
@@ -236,6 +293,15 @@ cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const
 #undef WCSIM_CASE
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dr_rows(const ConvDims& d, const float2* s2d, const float2* g2d, float2* dR,
+                           float inv_n, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((d.nh + kDrTile - 1) / kDrTile),
+                    (unsigned)((d.n_fw + kDrTile - 1) / kDrTile));
+    k_dr_tiles<<<grid, 256, 0, s>>>(d, s2d, g2d, dR, inv_n);
     return cudaGetLastError();
 }
 

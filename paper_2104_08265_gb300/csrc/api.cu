@@ -95,6 +95,12 @@ struct wcsim_plane {
     // (fwd_depos, fwd_prm) while fwd_valid
     bool reuse_fwd = false;
     bool fwd_valid = false;
+    // mode 2 (one-warp wire pass only): the forward's wire pass also writes the 2D spectra of
+    // S to s2d (row-major [n_imp][n_fw][4 nkb]); keep_s2d is set for the duration of such a
+    // forward, s2d_valid says the last one wrote them (read together with fwd_valid)
+    float2* s2d = nullptr;
+    bool keep_s2d = false;
+    bool s2d_valid = false;
     wcsim_depos fwd_depos = {};
     wcsim_drift_params fwd_prm = {};
     bool wire_block = false;    // autotuned: use the block-level wire pass even if the warp one fits
@@ -230,6 +236,7 @@ void plane_free(wcsim_plane* pl)
     cudaFree(pl->shat);
     cudaFree(pl->mt);
     cudaFree(pl->g2d);
+    cudaFree(pl->s2d);
     cudaFree(pl->noise_amp);
     cudaFree(pl->flags);
     cudaFree(pl->queue);
@@ -305,7 +312,8 @@ wcsim_status convolve_stages(wcsim_plane* pl, R2C r2c, float* wave, cudaStream_t
     int t = tl_record(pl, s);
     tl_span(pl, 2, b, t);
     if (pl->tw_warp && !pl->wire_block)
-        e = launch_wire_warp(d, pl->tw_warp, pl->shat, pl->H, pl->mt, pl->flags, s);
+        e = launch_wire_warp(d, pl->tw_warp, pl->shat, pl->H, pl->mt, pl->flags, s, 1,
+                             pl->keep_s2d ? pl->s2d : nullptr);
     else
         e = launch_wire_pass(d, pl->pw, pl->shat, pl->H, pl->mt, pl->flags, s);
     if (e) return cuda_fail(e, "wire_pass launch");
@@ -315,6 +323,13 @@ wcsim_status convolve_stages(wcsim_plane* pl, R2C r2c, float* wave, cudaStream_t
     if ((e = launch_rows_c2r(d, pl->pt, pl->mt, wave, s))) return cuda_fail(e, "rows_c2r launch");
     tl_span(pl, 4, t, tl_record(pl, s));
     return WCSIM_OK;
+}
+
+// A forward that will keep the 2D spectra of S for the backward (set_reuse_forward mode 2):
+// mean path, one-warp wire pass, buffer allocated.
+bool keeps_s2d(const wcsim_plane* pl)
+{
+    return pl->s2d && pl->reuse_fwd && pl->prm.fluctuate == 0 && pl->tw_warp && !pl->wire_block;
 }
 
 wcsim_status do_convolve(wcsim_plane* pl, const float* grid, float* wave, cudaStream_t s)
@@ -378,11 +393,15 @@ wcsim_status fused_forward(wcsim_plane* pl, const wcsim_depos* depos, void* out,
     auto r2c = [&](cudaStream_t strm) {
         return launch_rows_r2c_fused(d, pt, c, fs, shat, strm);
     };
+    pl->keep_s2d = keeps_s2d(pl);
     st = convolve_stages(pl, r2c, static_cast<float*>(out), s);
+    const bool kept = pl->keep_s2d;
+    pl->keep_s2d = false;
     if (st) return st;
     pl->fwd_valid = false;
     if (pl->reuse_fwd && pl->prm.fluctuate == 0) {
         pl->fwd_valid = true;           // shat: the mean-path spectra of these depos
+        pl->s2d_valid = kept;
         pl->fwd_depos = *depos;
         pl->fwd_prm = pl->prm;
     }
@@ -703,13 +722,17 @@ static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* o
         pl->dims.adc_pedestal = pl->adc_pedestal;
         pl->dims.adc_max = pl->adc_max;
     }
+    pl->keep_s2d = keeps_s2d(pl);
     st = do_convolve(pl, pl->grid, static_cast<float*>(out), s);
+    const bool kept = pl->keep_s2d;
+    pl->keep_s2d = false;
     pl->dims.clear_input = 0;
     pl->dims.noise_amp = nullptr;
     pl->dims.adc_max = 0;
     if (st == WCSIM_OK && pl->dims.rows_variant == 0) pl->grid_clean = true;
     if (st == WCSIM_OK && pl->reuse_fwd && pl->prm.fluctuate == 0) {
         pl->fwd_valid = true;           // shat: the mean-path spectra of these depos
+        pl->s2d_valid = kept;
         pl->fwd_depos = *depos;
         pl->fwd_prm = pl->prm;
     }
@@ -740,9 +763,11 @@ wcsim_status wcsim_plane_set_digitizer(wcsim_plane* pl, float gain, float pedest
 
 // have_shat: the plane's spectra already hold the time-axis FFT of `grid` (a forward on the
 // same grid just computed them), so that transform is skipped
+// have_s2d: the forward also kept the 2D spectra of S (reuse mode 2): dL/dR streams from them
+// (part A only transforms G) and the spectra of the grid are not needed at all
 static wcsim_status convolve_adjoint(wcsim_plane* pl, const float* grad_wave, const float* grid,
                                      float* dgrid, void* grad_resp_c64, void* stream,
-                                     bool have_shat)
+                                     bool have_shat, bool have_s2d = false)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
     if (!grad_wave || !grid || !dgrid) return fail(WCSIM_EINVAL, "grad_wave, grid or dgrid is NULL");
@@ -760,7 +785,12 @@ static wcsim_status convolve_adjoint(wcsim_plane* pl, const float* grad_wave, co
     if ((e = launch_rows_r2c(dG, pl->pt, grad_wave, pl->mt, pl->flags, s))) return cuda_fail(e, "rows_r2c launch");
     markb(pl, 4, s);
     const float inv_n = (float)(1.0 / ((double)d.n_fw * (double)d.n_ft));
-    if (pl->tw_warp && !pl->adj_block)
+    const bool warp = pl->tw_warp && !pl->adj_block;
+    if (warp && have_s2d && grad_resp_c64) {
+        if (!(e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, pl->g2d,
+                                           nullptr, inv_n, s)))
+            e = launch_dr_rows(d, pl->s2d, pl->g2d, (float2*)grad_resp_c64, inv_n, s);
+    } else if (warp)
         e = launch_wire_adjoint_warp(d, pl->tw_warp, pl->mt, pl->shat, pl->H, pl->g2d,
                                      (float2*)grad_resp_c64, inv_n, s);
     else
@@ -832,7 +862,8 @@ wcsim_status wcsim_run_backward(wcsim_plane* pl, const wcsim_depos* depos, const
             return cuda_fail(e, "rasterize launch");
     }
     markb(pl, 2, s);
-    if ((st = convolve_adjoint(pl, grad_wave, pl->grid, pl->grid, grad_resp_c64, stream, reuse)))
+    if ((st = convolve_adjoint(pl, grad_wave, pl->grid, pl->grid, grad_resp_c64, stream, reuse,
+                               reuse && pl->s2d_valid)))
         return st;
     return wcsim_rasterize_adjoint(pl, depos, pl->grid, grads, stream);
 }
@@ -1169,8 +1200,25 @@ wcsim_status wcsim_plane_set_forward(wcsim_plane* pl, int32_t fused)
 wcsim_status wcsim_plane_set_reuse_forward(wcsim_plane* pl, int32_t enable)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
-    pl->reuse_fwd = enable != 0;
+    if (enable < 0 || enable > 2) return fail(WCSIM_EINVAL, "enable must be 0, 1 or 2 (got %d)", enable);
     pl->fwd_valid = false;
+    pl->s2d_valid = false;
+    if (enable == 2 && pl->tw_warp && !pl->s2d) {
+        DeviceGuard dg(pl->device);
+        if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
+        const ConvDims& d = pl->dims;
+        const size_t n = (size_t)d.n_imp * d.n_fw * kBlockCols * d.nkb;
+        cudaError_t e = cudaMalloc(&pl->s2d, n * sizeof(float2));
+        if (e) {
+            pl->s2d = nullptr;
+            return cuda_fail(e, "2D spectra allocation");
+        }
+    } else if (enable != 2 && pl->s2d) {
+        DeviceGuard dg(pl->device);
+        cudaFree(pl->s2d);              // synchronising: no work of the plane is in flight after
+        pl->s2d = nullptr;
+    }
+    pl->reuse_fwd = enable != 0;
     return WCSIM_OK;
 }
 

@@ -35,10 +35,15 @@ constexpr int kCols = 2;
 template <int M, int CW>
 constexpr size_t warp_smem() { return (size_t)32 * M * CW * sizeof(float2) + 16; }
 
-template <int M, int CW>
+// S2D: the 2D spectra of S (the wire FFT of every Shat_j column, before the product with H_j)
+// are also written to s2d, time-frequency major [n_imp][4 nkb][n_fw] (the layout of H): each
+// warp stores its column from registers, consecutive lanes on consecutive wire frequencies,
+// for an adjoint that takes dL/dR from them (wcsim_plane_set_reuse_forward mode 2).
+template <int M, int CW, bool S2D>
 __global__ void __launch_bounds__(CW * 32, CW == 4 ? 3 : 5)
 k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict__ shat,
-            const float2* __restrict__ H, float2* __restrict__ mt, int* flags)
+            const float2* __restrict__ H, float2* __restrict__ mt, int* flags,
+            float2* __restrict__ s2d)
 {
     static_assert(CW == 2 || CW == 4, "columns per CTA");
     constexpr int N = 32 * M;
@@ -83,12 +88,20 @@ k_wire_warp(ConvDims d, const float2* __restrict__ tw2, const float2* __restrict
             landed = mbar_wait(bar, j & 1, d.wait_ns);   // H_j's tile, copied while S_j loads
             warp_fft_fwd<M>(v, s_twf, tr, lane, u);
         }
-        if (landed && lane < M) {
+        if (lane < M) {
+            if (landed) {
 #pragma unroll
-            for (int k1 = 0; k1 < 32; ++k1) {
-                const float2 h = s_h[warp * N + lane + M * k1];
-                acc[k1].x += h.x * u[k1].x - h.y * u[k1].y;
-                acc[k1].y += h.x * u[k1].y + h.y * u[k1].x;
+                for (int k1 = 0; k1 < 32; ++k1) {
+                    const float2 h = s_h[warp * N + lane + M * k1];
+                    acc[k1].x += h.x * u[k1].x - h.y * u[k1].y;
+                    acc[k1].y += h.x * u[k1].y + h.y * u[k1].x;
+                }
+            }
+            if constexpr (S2D) {
+                // S_j's 2D spectrum in column 4 kb + c: lane k2 < M holds kw = k2 + M k1
+                float2* col = s2d + ((int64_t)j * kBlockCols * d.nkb + kb * kBlockCols + c) * N;
+#pragma unroll
+                for (int k1 = 0; k1 < 32; ++k1) __stcs(col + lane + M * k1, u[k1]);
             }
         }
         // every warp is done with s_h (and its transpose tile)
@@ -165,22 +178,31 @@ cudaError_t wire_warp_twiddles(int n_fw, float2** dev)
 }
 
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
-                             const float2* H, float2* mt, int* flags, cudaStream_t s, int n_ev)
+                             const float2* H, float2* mt, int* flags, cudaStream_t s, int n_ev,
+                             float2* s2d)
 {
     const dim3 grid((unsigned)n_ev, (unsigned)(d.nkb * (kBlockCols / kCols)));
+    if (s2d && n_ev != 1) return cudaErrorInvalidValue;
     switch (d.n_fw / 32) {
 #define WCSIM_CASE(MM)                                                                         \
     case MM: {                                                                                 \
         static DeviceOnce attr_set;                                                            \
         if (attr_set.pending()) {                                                              \
-            cudaError_t e = cudaFuncSetAttribute(k_wire_warp<MM, kCols>,                       \
+            cudaError_t e = cudaFuncSetAttribute(k_wire_warp<MM, kCols, false>,                \
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                                  (int)warp_smem<MM, kCols>());                 \
+            if (!e) e = cudaFuncSetAttribute(k_wire_warp<MM, kCols, true>,                     \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                             (int)warp_smem<MM, kCols>());                 \
             if (e) return e;                                                                   \
             attr_set.mark();                                                                   \
         }                                                                                      \
-        k_wire_warp<MM, kCols><<<grid, kCols * 32, warp_smem<MM, kCols>(), s>>>(d, tw2, shat, H, \
-                                                                                mt, flags);    \
+        if (s2d)                                                                               \
+            k_wire_warp<MM, kCols, true><<<grid, kCols * 32, warp_smem<MM, kCols>(), s>>>(     \
+                d, tw2, shat, H, mt, flags, s2d);                                              \
+        else                                                                                   \
+            k_wire_warp<MM, kCols, false><<<grid, kCols * 32, warp_smem<MM, kCols>(), s>>>(    \
+                d, tw2, shat, H, mt, flags, nullptr);                                          \
         break;                                                                                 \
     }
         WCSIM_WARP_M(WCSIM_CASE)

@@ -191,9 +191,11 @@ bool wire_warp_supported(int n_fw);
 // Twiddles of the warp kernel: [2][n_fw], exp(-2 pi i a b / n_fw) at a * 32 + b (a < M,
 // b < 32) and at b * M + a, FP64 rounded to FP32.  Device allocation owned by the caller.
 cudaError_t wire_warp_twiddles(int n_fw, float2** dev);
+// s2d (n_ev = 1 only): also write the 2D spectra of S (every Shat_j column's wire FFT,
+// before the product with H_j), time-frequency major [n_imp][4 nkb][n_fw] complex.
 cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2* shat,
                              const float2* H, float2* mt, int* flags, cudaStream_t s,
-                             int n_ev = 1);
+                             int n_ev = 1, float2* s2d = nullptr);
 // Adjoint of the wire pass (n_fw = 32 M): reads the time-axis spectra of the forward grid
 // (shat) and of G (gt, blocked [nkb][n_w][4]); overwrites shat with the time-axis spectra
 // of dL/dS and, if dR is not null, writes dL/dR_j (full [n_imp][n_fw][n_ft] layout).  g2d
@@ -201,6 +203,11 @@ cudaError_t launch_wire_warp(const ConvDims& d, const float2* tw2, const float2*
 cudaError_t launch_wire_adjoint_warp(const ConvDims& d, const float2* tw2, const float2* gt,
                                      float2* shat, const float2* H, float2* g2d, float2* dR,
                                      float inv_n, cudaStream_t s);
+// dL/dR_j from the forward's kept 2D spectra of S (s2d, [n_imp][4 nkb][n_fw], see
+// launch_wire_warp) and G's 2D spectrum (g2d, blocked [nkb][n_fw][4]; part A with dR null
+// writes it): the full [n_imp][n_fw][n_ft] layout, Hermitian mirror included.
+cudaError_t launch_dr_rows(const ConvDims& d, const float2* s2d, const float2* g2d, float2* dR,
+                           float inv_n, cudaStream_t s);
 // The same adjoint for any wire FFT size, block-level engine (plan pw): gt, shat, dR as above;
 // no 2D spectrum of G is kept.
 cudaError_t launch_wire_adjoint_block(const ConvDims& d, const FftPlan& pw, const float2* gt,

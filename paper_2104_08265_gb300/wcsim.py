@@ -325,7 +325,7 @@ class Plane:
         if getattr(self, "_reuse", False) and getattr(self, "_last_run_serial", None) != depos.serial:
             # not the depo set of the last run (the library compares pointers only): drop the
             # kept spectra so that the backward recomputes them
-            check(lib().wcsim_plane_set_reuse_forward(self._h, 1))
+            check(lib().wcsim_plane_set_reuse_forward(self._h, getattr(self, "_reuse_mode", 1)))
         check(lib().wcsim_run_backward(self._h, ctypes.byref(depos.c),
                                        grad_wave.contiguous().data_ptr(), ctypes.byref(c),
                                        dR.data_ptr() if dR is not None else None,
@@ -376,15 +376,18 @@ class Plane:
         """Limit (ns) of the device-side waits for bulk copies; see wcsim_plane_set_wait_limit."""
         check(lib().wcsim_plane_set_wait_limit(self._h, ctypes.c_uint64(int(ns))))
 
-    def set_reuse_forward(self, enable: bool = True):
+    def set_reuse_forward(self, enable: bool = True, keep_wire_spectra: bool = False):
         """Let backward() reuse the spectra of the preceding mean-path run() on the same depos
         and parameters (the depos must not change in between); see
-        wcsim_plane_set_reuse_forward.  The library recognises the depos by their device
-        pointers and count only; this binding also requires the same DeviceDepos object (its
-        serial), so tensors freed and reallocated at the same addresses are not mistaken for
-        the forward's."""
-        check(lib().wcsim_plane_set_reuse_forward(self._h, 1 if enable else 0))
+        wcsim_plane_set_reuse_forward.  keep_wire_spectra: the forward also keeps the 2D
+        spectra of S, from which a backward with want_resp=True takes dL/dR (mode 2).  The
+        library recognises the depos by their device pointers and count only; this binding
+        also requires the same DeviceDepos object (its serial), so tensors freed and
+        reallocated at the same addresses are not mistaken for the forward's."""
+        mode = (2 if keep_wire_spectra else 1) if enable else 0
+        check(lib().wcsim_plane_set_reuse_forward(self._h, mode))
         self._reuse = bool(enable)
+        self._reuse_mode = mode
 
     def set_forward(self, fused: bool = True):
         """Forward variant of run(): the rasterization fused into the time-axis transform

@@ -158,9 +158,11 @@ def test_autograd_function_gradients_and_a_fit_step(W):
     assert float(loss2) < float(loss.detach())
 
 
-def test_backward_reusing_the_forward_spectra_matches_oracle(W):
+@pytest.mark.parametrize("keep2d", [False, True])
+def test_backward_reusing_the_forward_spectra_matches_oracle(W, keep2d):
     """set_reuse_forward: the backward after a mean-path run on the same depos takes the
-    run's spectra; gradients as the oracle's and as the recomputing backward's."""
+    run's spectra (keep2d: and the 2D spectra of S its wire pass kept, from which dL/dR
+    streams); gradients as the oracle's and as the recomputing backward's."""
     import torch
     wl = S.make_workload("fit960-100k")
     g, prm, kind, d = wl.planes[0]
@@ -170,7 +172,7 @@ def test_backward_reusing_the_forward_spectra_matches_oracle(W):
     G = torch.from_numpy(np.random.default_rng(91).normal(size=(g.n_wires, g.n_ticks))
                          .astype(np.float32)).cuda()
     plain = pl.backward(dd, G, want_resp=True)
-    pl.set_reuse_forward(True)
+    pl.set_reuse_forward(True, keep_wire_spectra=keep2d)
     pl.run(dd)
     got = pl.backward(dd, G, want_resp=True)
     ref, rdR = _oracle_backward(g, prm, R, d, G.cpu().numpy().astype(np.float64))
@@ -319,3 +321,32 @@ def test_reuse_is_dropped_for_other_depos_at_the_same_addresses(W):
     _grads_close(got, ref, "reallocated depos", prm, d2)
     print("same addresses reused:", ptrs == (b.p.data_ptr(), b.q.data_ptr()))
     pl.close()
+
+
+@pytest.mark.parametrize("n_w,n_fw", [(128, 128), (20, 24)])
+def test_kept_wire_spectra_across_runs_and_sizes(W, n_w, n_fw):
+    """Mode 2 over repeated fit steps with changing parameters and response (each backward's
+    dL/dR the oracle's for its own forward), a backward without dL/dR in between, and a wire
+    axis the one-warp pass does not take (n_fw = 24: mode 2 acts as mode 1)."""
+    import torch
+    g = S.Geometry(n_wires=n_w, n_imp=10, n_ticks=1000, pitch_mm=3.0)
+    prm = S.DriftParams(fluctuate=0)
+    rng = np.random.default_rng(n_w + n_fw)
+    d = S.track_depos(rng, 3, 400, g.n_wires * g.pitch_mm, 0.6 * g.n_ticks * g.tick_us)
+    dd = W.DeviceDepos.from_host(d)
+    R = S.make_response(g, "induction", n_fw=n_fw, n_ft=1024)
+    pl = plane_for(W, g, prm, R)
+    pl.set_reuse_forward(True, keep_wire_spectra=True)
+    Gh = rng.normal(size=(g.n_wires, g.n_ticks))
+    G = torch.from_numpy(Gh.astype(np.float32)).cuda()
+    for step in range(3):
+        prm_s = dataclasses.replace(prm, DT_cm2_s=prm.DT_cm2_s * (1.0 + 0.2 * step))
+        R_s = (R * (1.0 + 0.1 * step)).astype(np.complex64)
+        pl.set_params(prm_s)
+        pl.set_response(torch.from_numpy(R_s).cuda())
+        pl.run(dd)
+        got = pl.backward(dd, G, want_resp=(step != 1))
+        ref, rdR = _oracle_backward(g, prm_s, R_s, d, Gh)
+        _grads_close(got, ref, "kept 2D spectra, step %d" % step, prm_s, d)
+        if step != 1:
+            assert_close(got["response"].cpu().numpy(), rdR, what="kept 2D spectra dR %d" % step)
