@@ -51,14 +51,18 @@ class FitState:
 
 def gpu_event_gradient(plane, depos, target) -> Callable:
     """The per-event backward on the GPU: run event e on `plane` (wcsim_run with the state's
-    parameters and response), then wcsim_run_backward with dL/dM = M - T.  Returns a
-    callable (state, params_e) -> (loss, {DL, DT, lifetime, response})."""
+    parameters and response), then wcsim_run_backward with dL/dM = M - T.  The backward takes
+    the forward's spectra (wcsim_plane_set_reuse_forward; the run is on the mean path when
+    params_e has fluctuate = 0), and, when the response is fitted, dL/dR from the 2D spectra
+    the forward kept.  Returns a callable (state, params_e) -> (loss, {DL, DT, lifetime,
+    response})."""
 
     def fn(state: FitState, params_e: DriftParams):
         plane.set_params(dataclasses.replace(params_e, DL_cm2_s=state.DL, DT_cm2_s=state.DT,
                                              lifetime_us=state.lifetime))
         if state.response is not None:
             plane.set_response(state.response)
+        plane.set_reuse_forward(True, keep_wire_spectra=state.response is not None)
         M = plane.run(depos)
         G = (M - target).contiguous()
         g = plane.backward(depos, G, want_resp=state.response is not None)
