@@ -694,13 +694,19 @@ def run_gpu(args):
         torch.cuda.synchronize()
         fs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         fe = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        plane.set_timing(True)
-        bwd_stage_ms = {k: [] for k in wcsim.BWD_STAGES}
         for i in range(args.steps):
             flush.zero_()
             fs[i].record(stream)
             fb_step()
             fe[i].record(stream)
+        torch.cuda.synchronize()
+        # the stage breakdown in a loop of its own: the library's stage events are not part
+        # of the timed steps
+        plane.set_timing(True)
+        bwd_stage_ms = {k: [] for k in wcsim.BWD_STAGES}
+        for i in range(args.steps):
+            flush.zero_()
+            fb_step()
             torch.cuda.synchronize()
             for k, v in plane.stage_times(backward=True).items():
                 if k in bwd_stage_ms:
