@@ -289,9 +289,9 @@ __global__ void __launch_bounds__(kWarps * 32, 3)
 k_depo_adjoint(RasterConsts c, DepoArrays d, const float* __restrict__ dgrid, DepoGrads g,
                int* flags)
 {
-    // a half warp per depo (as in the forward); patch tiles of at most kTile rows x kTile
-    // ticks
-    constexpr int G = 16, NG = kWarps * 32 / G, kTile = 32;
+    // 8 lanes per depo (as the forward's default tile; 16 lanes took 84 against 74 us on the
+    // 960 x 6000 plane); patch tiles of at most kTile rows x kTile ticks
+    constexpr int G = 8, NG = kWarps * 32 / G, kTile = 32;
     __shared__ Decision s_dec[kDepos];
     // wp, dwp/dmu, dwp/dsig per row; wt, dwt/dmu, dwt/dsig per tick laid out on 4-tick
     // groups (slot p is tick 4 q_lo + p, zero outside the window)
