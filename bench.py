@@ -683,10 +683,11 @@ def run_gpu(args):
         # and dL/dR from the 2D spectra of S the forward's wire pass kept
         plane.set_reuse_forward(True, keep_wire_spectra=True)
         G = torch.empty_like(wave)
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
 
         def fb_step():
-            plane.run(dd, out=wave)
-            torch.sub(wave, m_target, out=G)
+            # G = M - M_target and the loss straight from the inverse time FFT
+            plane.run_residual(dd, m_target, out=G, loss=loss)
             plane.backward(dd, G, want_resp=True)
 
         for _ in range(args.warmup):
@@ -827,7 +828,8 @@ def run_gpu(args):
         "backward_stages": ({k: {"ms": v, "alg_bytes": bsb[k],
                                  "GB/s": bsb[k] / (v * 1e-3) / 1e9 if v > 0 else None}
                              for k, v in bwd_stages.items()} if bwd_stages else None),
-        "fit_step": ("wcsim_run (mean path) then wcsim_run_backward with dL/dR, the backward "
+        "fit_step": ("wcsim_run_residual (mean path: G = M - M_target and the loss) then "
+                     "wcsim_run_backward with dL/dR, the backward "
                      "taking the forward's spectra and the 2D spectra of S its wire pass kept "
                      "(wcsim_plane_set_reuse_forward mode 2)") if bwd_stages else None,
         "mean_bins_per_depo": mean_bins,

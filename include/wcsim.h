@@ -140,6 +140,16 @@ wcsim_status wcsim_run(wcsim_plane* plane, const wcsim_depos* depos, float* wave
 wcsim_status wcsim_run_adc(wcsim_plane* plane, const wcsim_depos* depos, uint16_t* adc,
                            void* stream);
 
+/* wcsim_run for a fit: `residual` (DEVICE float32 [n_wires][n_ticks]) receives M - target,
+ * each value one FP32 subtraction of the frame wcsim_run would write from `target` (DEVICE
+ * float32, same layout, read only), the dL/dM of L = 1/2 |M - target|^2 that
+ * wcsim_run_backward takes; if `loss` (DEVICE double) is not NULL it is set to L (squares
+ * summed in FP32 within each warp's share of two wires, those sums in FP64).  residual and target
+ * must not overlap.  A forward like wcsim_run for wcsim_plane_set_reuse_forward.
+ * WCSIM_EINVAL if target or residual is NULL. */
+wcsim_status wcsim_run_residual(wcsim_plane* plane, const wcsim_depos* depos, const float* target,
+                                float* residual, double* loss, void* stream);
+
 /* Digitizer of wcsim_run_adc: gain (ADC counts per unit of M), pedestal (counts), bits in
  * 1..16.  WCSIM_EINVAL for bits out of range or a non-finite gain or pedestal. */
 wcsim_status wcsim_plane_set_digitizer(wcsim_plane* plane, float gain, float pedestal,

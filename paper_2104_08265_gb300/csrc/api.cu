@@ -678,8 +678,10 @@ wcsim_status wcsim_convolve(wcsim_plane* pl, const float* grid, float* wave, voi
 
 // wcsim_run and wcsim_run_adc: rasterize into the plane's grid, then convolve (with the
 // plane's noise); adc: the inverse time FFT writes the plane's ADC codes to out.
+// target (not with adc): out receives M - target, and loss (if not null) 1/2 sum of squares.
 static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* out, bool adc,
-                              void* stream)
+                              void* stream, const float* target = nullptr,
+                              double* loss = nullptr)
 {
     if (!pl) return fail(WCSIM_EINVAL, "plane is NULL");
     wcsim_status st = check_depos(depos);
@@ -690,8 +692,11 @@ static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* o
     if (!dg.ok) return fail(WCSIM_ECUDA, "cannot select the plane's device");
     cudaStream_t s = (cudaStream_t)stream;
     const ConvDims& d = pl->dims;
-    mark(pl, 0, s);
     cudaError_t e = cudaSuccess;
+    if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(double), s))) return cuda_fail(e, "loss reset");
+    mark(pl, 0, s);
+    pl->dims.target = target;
+    pl->dims.loss = target ? loss : nullptr;
     if (fused_applies(pl, depos)) {
         with_noise(pl, pl->dims);
         if (adc) {
@@ -702,16 +707,26 @@ static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* o
         st = fused_forward(pl, depos, out, s);
         pl->dims.noise_amp = nullptr;
         pl->dims.adc_max = 0;
+        pl->dims.target = nullptr;
+        pl->dims.loss = nullptr;
         return st;
     }
     if (!pl->grid_clean) {
         e = cudaMemsetAsync(pl->grid, 0, (size_t)d.n_w * d.n_imp * d.n_t * sizeof(float), s);
-        if (e) return cuda_fail(e, "grid reset");
+        if (e) {
+            pl->dims.target = nullptr;
+            pl->dims.loss = nullptr;
+            return cuda_fail(e, "grid reset");
+        }
     }
     pl->grid_clean = false;
     mark(pl, 1, s);
     e = launch_rasterize(make_consts(pl), depo_arrays(depos), pl->grid, pl->flags, s);
-    if (e) return cuda_fail(e, "rasterize launch");
+    if (e) {
+        pl->dims.target = nullptr;
+        pl->dims.loss = nullptr;
+        return cuda_fail(e, "rasterize launch");
+    }
     mark(pl, 2, s);
     // the time-axis transform reads the plane's own grid once: it clears it as it goes
     // (the direct kernel; the staged one reads through bulk copies and leaves it as is)
@@ -729,6 +744,8 @@ static wcsim_status run_frame(wcsim_plane* pl, const wcsim_depos* depos, void* o
     pl->dims.clear_input = 0;
     pl->dims.noise_amp = nullptr;
     pl->dims.adc_max = 0;
+    pl->dims.target = nullptr;
+    pl->dims.loss = nullptr;
     if (st == WCSIM_OK && pl->dims.rows_variant == 0) pl->grid_clean = true;
     if (st == WCSIM_OK && pl->reuse_fwd && pl->prm.fluctuate == 0) {
         pl->fwd_valid = true;           // shat: the mean-path spectra of these depos
@@ -747,6 +764,13 @@ wcsim_status wcsim_run(wcsim_plane* pl, const wcsim_depos* depos, float* wave, v
 wcsim_status wcsim_run_adc(wcsim_plane* pl, const wcsim_depos* depos, uint16_t* adc, void* stream)
 {
     return run_frame(pl, depos, adc, true, stream);
+}
+
+wcsim_status wcsim_run_residual(wcsim_plane* pl, const wcsim_depos* depos, const float* target,
+                                float* residual, double* loss, void* stream)
+{
+    if (!target) return fail(WCSIM_EINVAL, "target is NULL");
+    return run_frame(pl, depos, residual, false, stream, target, loss);
 }
 
 wcsim_status wcsim_plane_set_digitizer(wcsim_plane* pl, float gain, float pedestal, int32_t bits)

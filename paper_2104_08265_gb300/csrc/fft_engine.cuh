@@ -423,6 +423,50 @@ __device__ __forceinline__ void store_real_pair(const float2* z, float* __restri
     }
 }
 
+// store_real_pair for a residual: o = M - target (one FP32 subtraction of the value
+// store_real_pair would write) for rows 0 (.x, target t0) and 1 (.y, t1); returns this
+// thread's FP32 sum of the squared residuals it wrote.  vec: rows and targets 16-byte
+// aligned, n_t a multiple of 4.
+__device__ __forceinline__ float store_residual_pair(const float2* z, float* __restrict__ o0,
+                                                    float* __restrict__ o1,
+                                                    const float* __restrict__ t0,
+                                                    const float* __restrict__ t1, int n_t,
+                                                    bool has1, bool vec)
+{
+    float ss = 0.0f;
+    if (vec) {
+        for (int q = threadIdx.x; q < (n_t >> 2); q += blockDim.x) {
+            const int i = pad16(4 * q);
+            const float2 a = z[i], b = z[i + 1], c = z[i + 2], e = z[i + 3];
+            const float4 ta = __ldg(reinterpret_cast<const float4*>(t0) + q);
+            const float4 r0 = make_float4(__fsub_rn(a.x, ta.x), __fsub_rn(b.x, ta.y),
+                                          __fsub_rn(c.x, ta.z), __fsub_rn(e.x, ta.w));
+            reinterpret_cast<float4*>(o0)[q] = r0;
+            ss += r0.x * r0.x + r0.y * r0.y + r0.z * r0.z + r0.w * r0.w;
+            if (has1) {
+                const float4 tb = __ldg(reinterpret_cast<const float4*>(t1) + q);
+                const float4 r1 = make_float4(__fsub_rn(a.y, tb.x), __fsub_rn(b.y, tb.y),
+                                              __fsub_rn(c.y, tb.z), __fsub_rn(e.y, tb.w));
+                reinterpret_cast<float4*>(o1)[q] = r1;
+                ss += r1.x * r1.x + r1.y * r1.y + r1.z * r1.z + r1.w * r1.w;
+            }
+        }
+    } else {
+        for (int t = threadIdx.x; t < n_t; t += blockDim.x) {
+            const float2 v = z[pad16(t)];
+            const float r0 = __fsub_rn(v.x, t0[t]);
+            o0[t] = r0;
+            ss += r0 * r0;
+            if (has1) {
+                const float r1 = __fsub_rn(v.y, t1[t]);
+                o1[t] = r1;
+                ss += r1 * r1;
+            }
+        }
+    }
+    return ss;
+}
+
 // ADC code of waveform value m: clamp(floor(fl(fl(g m) + p) + 1/2), 0, top), each step one
 // correctly rounded FP32 operation.
 __device__ __forceinline__ uint16_t adc_code(float m, float g, float p, float top)

@@ -346,6 +346,18 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
         return;
     }
     float* o0 = wave + (int64_t)w0 * d.n_t;
+    if (d.target) {                            // residual M - target, and 1/2 sum of squares
+        const float* t0 = d.target + (int64_t)w0 * d.n_t;
+        const bool vec = ((d.n_t & 3) == 0) &&
+                         (((reinterpret_cast<uintptr_t>(wave) | reinterpret_cast<uintptr_t>(d.target)) & 15) == 0);
+        float ss = store_residual_pair(z, o0, o0 + d.n_t, t0, t0 + d.n_t, d.n_t, has1, vec);
+        if (d.loss) {                          // one FP64 addition per warp (no static
+#pragma unroll                                         // shared memory: see attrs())
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(d.loss, 0.5 * (double)ss);
+        }
+        return;
+    }
     const bool vec = ((d.n_t & 3) == 0) && ((reinterpret_cast<uintptr_t>(wave) & 15) == 0);
     store_real_pair(z, o0, o0 + d.n_t, d.n_t, has1, vec);
 }
@@ -382,6 +394,8 @@ int r2c_store_map(const ConvDims& d, const FftPlan& pt, int fix, const float2* s
     return bk;
 }
 
+// The row kernels declare no static shared memory: the dynamic limit set here is the whole
+// per-block opt-in limit, which a static array would push over (the attribute call fails).
 DeviceOnce g_attr;
 cudaError_t attrs()
 {

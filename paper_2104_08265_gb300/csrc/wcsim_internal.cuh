@@ -160,6 +160,11 @@ struct ConvDims {
     // clamp(floor(fl(fl(adc_gain M) + adc_pedestal) + 1/2), 0, adc_max)
     float adc_gain = 0.0f, adc_pedestal = 0.0f;
     int32_t adc_max = 0;
+    // target != null (single runs): the inverse time FFT writes M - target (the same
+    // [n_w][n_t] layout) instead of M and, with loss, adds 1/2 sum (M - target)^2 to *loss
+    // (FP32 within a warp, FP64 across warps)
+    const float* target = nullptr;
+    double* loss = nullptr;
 };
 
 

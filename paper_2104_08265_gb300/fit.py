@@ -50,8 +50,9 @@ class FitState:
 
 
 def gpu_event_gradient(plane, depos, target) -> Callable:
-    """The per-event backward on the GPU: run event e on `plane` (wcsim_run with the state's
-    parameters and response), then wcsim_run_backward with dL/dM = M - T.  The backward takes
+    """The per-event backward on the GPU: run event e on `plane` (wcsim_run_residual with the
+    state's parameters and response: M - T and the loss), then wcsim_run_backward with
+    dL/dM = M - T.  The backward takes
     the forward's spectra (wcsim_plane_set_reuse_forward; the run is on the mean path when
     params_e has fluctuate = 0), and, when the response is fitted, dL/dR from the 2D spectra
     the forward kept.  Returns a callable (state, params_e) -> (loss, {DL, DT, lifetime,
@@ -63,10 +64,9 @@ def gpu_event_gradient(plane, depos, target) -> Callable:
         if state.response is not None:
             plane.set_response(state.response)
         plane.set_reuse_forward(True, keep_wire_spectra=state.response is not None)
-        M = plane.run(depos)
-        G = (M - target).contiguous()
+        G, loss_t = plane.run_residual(depos, target)      # M - T and 1/2 |M - T|^2
         g = plane.backward(depos, G, want_resp=state.response is not None)
-        loss = 0.5 * float(torch.sum(G.double() * G.double()))
+        loss = float(loss_t)
         return loss, {"DL": float(g["DL"]), "DT": float(g["DT"]),
                       "lifetime": float(g["lifetime"]), "response": g["response"]}
 

@@ -106,6 +106,7 @@ def lib() -> ctypes.CDLL:
         "wcsim_plane_set_wait_limit": [vp, ctypes.c_uint64],
         "wcsim_plane_set_noise": [vp, vp, i32, ctypes.c_uint64, vp],
         "wcsim_run_adc": [vp, P(CDepos), vp, vp],
+        "wcsim_run_residual": [vp, P(CDepos), vp, vp, vp, vp],
         "wcsim_plane_set_digitizer": [vp, ctypes.c_float, ctypes.c_float, i32],
         "wcsim_plane_set_reuse_forward": [vp, i32],
         "wcsim_plane_set_forward": [vp, i32],
@@ -258,6 +259,22 @@ class Plane:
                               _stream_handle(stream)))
         self._last_run_serial = depos.serial
         return out
+
+    def run_residual(self, depos: DeviceDepos, target, out=None, loss=None, stream=None):
+        """M - target for the frame M of run() (float32 [n_wires, n_ticks] on the GPU) and,
+        in `loss` (a float64 tensor of one element, made if None), L = 1/2 |M - target|^2;
+        see wcsim_run_residual.  Returns (residual, loss)."""
+        import torch
+        out = self._wave(out)
+        target = target.contiguous()
+        if target.shape != out.shape or target.dtype != torch.float32 or not target.is_cuda:
+            raise ValueError("target must be a float32 CUDA tensor of shape %s" % (tuple(out.shape),))
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        check(lib().wcsim_run_residual(self._h, ctypes.byref(depos.c), target.data_ptr(),
+                                       out.data_ptr(), loss.data_ptr(), _stream_handle(stream)))
+        self._last_run_serial = depos.serial
+        return out, loss
 
     def set_digitizer(self, gain: float, pedestal: float, bits: int):
         """ADC settings of run_adc; see wcsim_plane_set_digitizer."""

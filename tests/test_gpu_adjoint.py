@@ -350,3 +350,31 @@ def test_kept_wire_spectra_across_runs_and_sizes(W, n_w, n_fw):
         _grads_close(got, ref, "kept 2D spectra, step %d" % step, prm_s, d)
         if step != 1:
             assert_close(got["response"].cpu().numpy(), rdR, what="kept 2D spectra dR %d" % step)
+
+
+def test_run_residual_matches_run_and_oracle(W):
+    """wcsim_run_residual: M - T and L = 1/2 |M - T|^2 in one forward, against run() and
+    the oracle's frame; then a backward from the residual, its dL/dR the oracle's."""
+    import torch
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=0)
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    dd = W.DeviceDepos.from_host(d)
+    T = torch.from_numpy(np.random.default_rng(95).normal(size=(g.n_wires, g.n_ticks))
+                         .astype(np.float32)).cuda()
+    M = pl.run(dd).clone()
+    res, loss = pl.run_residual(dd, T)
+    ref = O.run(g, prm, R, d) - T.cpu().numpy().astype(np.float64)
+    assert_close(res.cpu().numpy(), ref, what="residual vs oracle")
+    assert_close(res.cpu().numpy(), (M - T).cpu().numpy(), rel=1e-6, peak=1e-6,
+                 what="residual vs run")
+    r64 = res.double()
+    assert float(loss) == pytest.approx(0.5 * float((r64 * r64).sum()), rel=1e-5)
+    pl.set_reuse_forward(True, keep_wire_spectra=True)
+    res, loss = pl.run_residual(dd, T, out=res, loss=loss)
+    got = pl.backward(dd, res, want_resp=True)
+    refg, rdR = _oracle_backward(g, prm, R, d, res.cpu().numpy().astype(np.float64))
+    _grads_close(got, refg, "from the residual", prm, d)
+    assert_close(got["response"].cpu().numpy(), rdR, what="from the residual dR")
