@@ -59,24 +59,35 @@ static __device__ __forceinline__ float window_mass(float frac, float hw, float 
 }
 
 // One axis of the bin decision.  Every operation is an explicitly rounded IEEE operation
-// (no contraction), so that the result is a function of the inputs alone.
+// (no contraction), so that the result is a function of the inputs alone.  The window edges
+// i0 + floor(frac -+ hw) are sums of whole numbers below 2^53, exact in FP64 and formed here
+// in 64-bit integers instead (FP64 runs at a small fraction of the FP32 rate on this part):
+// floor of a float is floorf, and clamping it to +-2^42 (far beyond |i0| < 10^12 and the grid)
+// changes no clipped edge.
 static __device__ __forceinline__ bool axis_window(double x, float hw, int64_t n, int32_t& lo,
                                             int32_t& hi, int64_t& i0i, float& frac)
 {
-    if (!(x > -1e12 && x < 1e12)) return false;
-    double i0 = floor(x);
+    if (!(fabs(x) < 1e12)) return false;
+    const double i0 = floor(x);
     frac = __double2float_rn(__dsub_rn(x, i0));
-    float a = __fsub_rn(frac, hw);
-    float b = __fadd_rn(frac, hw);
-    double l = __dadd_rn(i0, floor((double)a));
-    double h = __dadd_rn(i0, floor((double)b));
-    if (l < 0.0) l = 0.0;
-    if (h > (double)(n - 1)) h = (double)(n - 1);
+    const float a = __fsub_rn(frac, hw);
+    const float b = __fadd_rn(frac, hw);
+    constexpr float kEdge = 4398046511104.0f;      // 2^42
+    i0i = (int64_t)i0;
+    int64_t l = i0i + (int64_t)fminf(fmaxf(floorf(a), -kEdge), kEdge);
+    int64_t h = i0i + (int64_t)fminf(fmaxf(floorf(b), -kEdge), kEdge);
+    if (l < 0) l = 0;
+    if (h > n - 1) h = n - 1;
     if (l > h) return false;
     lo = (int32_t)l;
     hi = (int32_t)h;
-    i0i = (int64_t)i0;
     return true;
+}
+
+// isfinite for a double by its exponent bits (integer operations, not the FP64 pipe).
+static __device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 
 // Drift (t_a = t + t_d, Q' = Q e^{-t_d/tau}, sigma = sqrt(2 D t_d)) and the window of bins
@@ -89,7 +100,10 @@ static __device__ __forceinline__ Decision decide(const RasterConsts& c, const D
     r.ok = 0;
     const double p = d.p[i], t = d.t[i], td = d.td[i];
     const float q = d.q[i];
-    if (!(td >= 0.0) || !isfinite(p) || !isfinite(t) || !isfinite(td) || !(q >= 0.0f) ||
+    // td >= 0 (or -0) and every input finite: sign and exponent bits, integer operations
+    const int64_t tdb = __double_as_longlong(td);
+    const bool td_neg = tdb < 0 && (tdb & 0x7fffffffffffffffll) != 0;
+    if (td_neg || !finite_bits(p) || !finite_bits(t) || !finite_bits(td) || !(q >= 0.0f) ||
         !isfinite(q)) {
         atomicOr(flags, kErrInvalidDepo);
         return r;
