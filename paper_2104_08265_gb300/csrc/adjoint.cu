@@ -215,14 +215,22 @@ k_dr_tiles(ConvDims d, const float2* __restrict__ s2d, const float2* __restrict_
                    ? __ldg(g2d + ((int64_t)(kt >> 2) * N + kw) * kBlockCols + (kt & 3))
                    : make_float2(0.f, 0.f);
     }
-    for (int j = 0; j < d.n_imp; ++j) {
-        float2 u[4];
+    // this thread's 4 values of S_j^, loaded one impact ahead
+    auto load_s = [&](int j, float2 (&u)[4]) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int kt = kt0 + 4 * warp + i;
             u[i] = (kt < d.nh && kw < N) ? __ldcs(s2d + ((int64_t)j * ncol + kt) * N + kw)
                                          : make_float2(0.f, 0.f);
         }
+    };
+    float2 un[4];
+    load_s(0, un);
+    for (int j = 0; j < d.n_imp; ++j) {
+        float2 u[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) u[i] = un[i];
+        if (j + 1 < d.n_imp) load_s(j + 1, un);
         __syncthreads();                                // the previous impact's tile is read
 #pragma unroll
         for (int i = 0; i < 4; ++i)
