@@ -435,20 +435,38 @@ __device__ __forceinline__ float store_residual_pair(const float2* z, float* __r
 {
     float ss = 0.0f;
     if (vec) {
-        for (int q = threadIdx.x; q < (n_t >> 2); q += blockDim.x) {
-            const int i = pad16(4 * q);
-            const float2 a = z[i], b = z[i + 1], c = z[i + 2], e = z[i + 3];
-            const float4 ta = __ldg(reinterpret_cast<const float4*>(t0) + q);
-            const float4 r0 = make_float4(__fsub_rn(a.x, ta.x), __fsub_rn(b.x, ta.y),
-                                          __fsub_rn(c.x, ta.z), __fsub_rn(e.x, ta.w));
-            reinterpret_cast<float4*>(o0)[q] = r0;
-            ss += r0.x * r0.x + r0.y * r0.y + r0.z * r0.z + r0.w * r0.w;
-            if (has1) {
-                const float4 tb = __ldg(reinterpret_cast<const float4*>(t1) + q);
-                const float4 r1 = make_float4(__fsub_rn(a.y, tb.x), __fsub_rn(b.y, tb.y),
-                                              __fsub_rn(c.y, tb.z), __fsub_rn(e.y, tb.w));
-                reinterpret_cast<float4*>(o1)[q] = r1;
-                ss += r1.x * r1.x + r1.y * r1.y + r1.z * r1.z + r1.w * r1.w;
+        // the targets' 16-byte loads in batches of kU per row, issued before their use
+        constexpr int kU = 6;
+        const int nq = n_t >> 2;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int base = threadIdx.x; base < nq; base += kU * blockDim.x) {
+            float4 ta[kU], tb[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = base + u * blockDim.x;
+                ta[u] = tb[u] = zero;
+                if (q < nq) {
+                    ta[u] = __ldg(reinterpret_cast<const float4*>(t0) + q);
+                    if (has1) tb[u] = __ldg(reinterpret_cast<const float4*>(t1) + q);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = base + u * blockDim.x;
+                if (q < nq) {
+                    const int i = pad16(4 * q);
+                    const float2 a = z[i], b = z[i + 1], c = z[i + 2], e = z[i + 3];
+                    const float4 r0 = make_float4(__fsub_rn(a.x, ta[u].x), __fsub_rn(b.x, ta[u].y),
+                                                  __fsub_rn(c.x, ta[u].z), __fsub_rn(e.x, ta[u].w));
+                    reinterpret_cast<float4*>(o0)[q] = r0;
+                    ss += r0.x * r0.x + r0.y * r0.y + r0.z * r0.z + r0.w * r0.w;
+                    if (has1) {
+                        const float4 r1 = make_float4(__fsub_rn(a.y, tb[u].x), __fsub_rn(b.y, tb[u].y),
+                                                      __fsub_rn(c.y, tb[u].z), __fsub_rn(e.y, tb[u].w));
+                        reinterpret_cast<float4*>(o1)[q] = r1;
+                        ss += r1.x * r1.x + r1.y * r1.y + r1.z * r1.z + r1.w * r1.w;
+                    }
+                }
             }
         }
     } else {

@@ -333,6 +333,12 @@ k_rows_c2r(ConvDims d, FftPlan p, const float2* __restrict__ mt, WavePtrs waves)
     float2* Y = X + padded_len(N);
     const int w0 = 2 * blockIdx.x, w1 = w0 + 1;
     const bool has1 = w1 < d.n_w;
+    if (d.target && threadIdx.x == 0 && (d.n_t & 3) == 0 &&
+        (reinterpret_cast<uintptr_t>(d.target) & 15) == 0) {
+        // the target rows this CTA subtracts at the end: into L2 while it transforms
+        bulk_prefetch_l2(d.target + (int64_t)w0 * d.n_t,
+                         (uint32_t)((has1 ? 2 : 1) * d.n_t * sizeof(float)));
+    }
     stage_herm_pair(mt, mt, w0, has1 ? w1 : w0, has1, d.n_w, d.nh, N, X, d.noise_amp,
                     d.noise_seed + (uint64_t)waves.ev[blockIdx.y], d.plane_id);
     __syncthreads();
