@@ -378,3 +378,27 @@ def test_run_residual_matches_run_and_oracle(W):
     refg, rdR = _oracle_backward(g, prm, R, d, res.cpu().numpy().astype(np.float64))
     _grads_close(got, refg, "from the residual", prm, d)
     assert_close(got["response"].cpu().numpy(), rdR, what="from the residual dR")
+
+
+@pytest.mark.parametrize("case", ["noise", "padded"])
+def test_run_residual_with_noise_and_padded_spectra(W, case):
+    """The residual of a plane with Eq. 1's noise (M includes it) and of padded spectra
+    (n_ft > n_ticks, n_fw > n_wires: M is cropped before T is subtracted), against run()."""
+    import torch
+    g = S.Geometry(n_wires=40, n_imp=10, n_ticks=600, pitch_mm=3.0)
+    prm = S.DriftParams(fluctuate=1, seed=11)
+    rng = np.random.default_rng(96)
+    d = S.track_depos(rng, 2, 300, g.n_wires * g.pitch_mm, 0.5 * g.n_ticks * g.tick_us)
+    n_fw, n_ft = (64, 640) if case == "padded" else (None, None)
+    R = S.make_response(g, "induction", n_fw=n_fw, n_ft=n_ft)
+    pl = plane_for(W, g, prm, R)
+    if case == "noise":
+        nh = g.n_ticks // 2 + 1
+        pl.set_noise(np.full(nh, 3.0, np.float32), seed=4321)
+    dd = W.DeviceDepos.from_host(d)
+    T = torch.from_numpy(rng.normal(size=(g.n_wires, g.n_ticks)).astype(np.float32)).cuda()
+    M = pl.run(dd).clone()
+    res, loss = pl.run_residual(dd, T)
+    assert_close(res.cpu().numpy(), (M - T).cpu().numpy(), rel=1e-6, peak=1e-6, what=case)
+    r64 = res.double()
+    assert float(loss) == pytest.approx(0.5 * float((r64 * r64).sum()), rel=1e-5)
