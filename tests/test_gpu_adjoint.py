@@ -402,3 +402,25 @@ def test_run_residual_with_noise_and_padded_spectra(W, case):
     assert_close(res.cpu().numpy(), (M - T).cpu().numpy(), rel=1e-6, peak=1e-6, what=case)
     r64 = res.double()
     assert float(loss) == pytest.approx(0.5 * float((r64 * r64).sum()), rel=1e-5)
+
+
+def test_kept_wire_spectra_after_the_fused_forward(W):
+    """Mode 2 after the fused forward (rasterization inside the time-axis transform): the
+    wire pass keeps the 2D spectra all the same, and dL/dR and the depo gradients are the
+    oracle's."""
+    import torch
+    wl = S.make_workload("plane128-2k")
+    g, prm, kind, d = wl.planes[0]
+    prm = dataclasses.replace(prm, fluctuate=0)
+    R = S.make_response(g, kind)
+    pl = plane_for(W, g, prm, R)
+    pl.set_forward(True)
+    pl.set_reuse_forward(True, keep_wire_spectra=True)
+    dd = W.DeviceDepos.from_host(d)
+    T = torch.from_numpy(np.random.default_rng(97).normal(size=(g.n_wires, g.n_ticks))
+                         .astype(np.float32)).cuda()
+    res, loss = pl.run_residual(dd, T)
+    got = pl.backward(dd, res, want_resp=True)
+    ref, rdR = _oracle_backward(g, prm, R, d, res.cpu().numpy().astype(np.float64))
+    _grads_close(got, ref, "fused forward, kept spectra", prm, d)
+    assert_close(got["response"].cpu().numpy(), rdR, what="fused forward, kept spectra dR")
