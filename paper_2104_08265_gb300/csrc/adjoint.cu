@@ -8,7 +8,8 @@
 // layout of the forward warp kernel), each doing one wire FFT per impact position: part A
 // transforms G's column once and, per j, S_j's column, writing dL/dR_j at (kw, kt) and its
 // Hermitian mirror (-kw, -kt); part B forms conj(H_j) G^ and transforms it back, overwriting
-// S_j's column with the time-axis spectrum of dL/dS_j.
+// S_j's column with the time-axis spectrum of dL/dS_j.  When the forward kept the 2D spectra
+// of S, part A transforms G alone and dr_tiles forms dL/dR_j from the kept spectra.
 // rows_c2r_grid: the inverse time-axis FFT of those spectra for every grid row.
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -96,7 +96,7 @@ struct wcsim_plane {
     bool reuse_fwd = false;
     bool fwd_valid = false;
     // mode 2 (one-warp wire pass only): the forward's wire pass also writes the 2D spectra of
-    // S to s2d (row-major [n_imp][n_fw][4 nkb]); keep_s2d is set for the duration of such a
+    // S to s2d (time-frequency major [n_imp][4 nkb][n_fw]); keep_s2d is set for the duration of such a
     // forward, s2d_valid says the last one wrote them (read together with fwd_valid)
     float2* s2d = nullptr;
     bool keep_s2d = false;

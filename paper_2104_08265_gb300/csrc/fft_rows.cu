@@ -8,11 +8,14 @@
 // a pair with no nonzero value stores zero spectra at once, and otherwise every pass of the
 // plan runs in shared memory (in place, in one buffer, for the compile-time 6000-point plan;
 // between two buffers for runtime plans); the CTA also asks L2 for the rows of the CTA
-// expected to follow it on the SM.  rows_r2c (staged, chosen by the autotuner or
+// expected to follow it on the SM.  The two half spectra are separated into flat shared rows
+// and leave through TMA tensor box stores (per-thread stores with WCSIM_SPECTRA_TMA=0).
+// rows_r2c (staged, chosen by the autotuner or
 // WCSIM_ROWS_KERNEL) is persistent: one CTA per SM walks pairs of rows, and one bulk copy
 // brings both rows of the next pair into a two-stage shared buffer while the previous pair
 // is transformed.  The inverse kernel stages its Hermitian input (each element read once,
-// its mirror written from the same load) and writes 4 ticks per 16-byte store.
+// its mirror written from the same load) and writes 4 ticks per 16-byte store, or, given a
+// target frame, the residual M - target and its sum of squares.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>

@@ -13,7 +13,8 @@
 // is brought into shared memory by one bulk asynchronous copy on an mbarrier: the copy of
 // H_{j+1} is issued as soon as every warp has used H_j, so it lands while the warps load and
 // transform S_{j+1}.  Every wait is bounded in time; a wait that runs out raises the timeout
-// flag and the CTA leaves.  The result leaves through shared memory as 16-byte stores.
+// flag and the CTA leaves.  The result leaves through shared memory as 16-byte stores.  In
+// the S2D instance (fit steps) each warp also stores its S_j column's wire spectrum.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
