@@ -191,13 +191,39 @@ STAGE_KERNEL_FUSED = {"rows_r2c": "k_rows_r2c_fused", "wire_pass": "k_wire_warp"
                       "rows_c2r": "k_rows_c2r"}
 
 
+def code_only(text):
+    """C/C++ source without its comments and with runs of whitespace collapsed (string and
+    character literals kept as written), so that edits to comments leave it unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_hash():
+    """SHA-256 of the code (comments aside) of every CUDA source of the library."""
     import glob
     import hashlib
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2104_08265_gb300", "csrc")
     for f in sorted(glob.glob(os.path.join(src, "*.cu")) + glob.glob(os.path.join(src, "*.cuh"))):
-        h.update(open(f, "rb").read())
+        h.update(code_only(open(f, encoding="utf-8").read()).encode())
     return h.hexdigest()
 
 
@@ -226,7 +252,7 @@ def write_traffic(reps):
             acc.setdefault(kernel_base(r[ki]), []).append(b)
     rec = {"_about": "DRAM bytes (read + write) per launch, mean over the captured launches, "
                      "from ncu --set full captures (one kernel and one launch per capture) of the "
-                     "960-wire x 6000-tick plane with 100k depos; valid only while the CUDA "
+                     "960-wire x 6000-tick plane with 100k depos; valid only while the code (comments aside) of the CUDA "
                      "sources hash to source_sha256.",
            "capture": ("CMD='python bench.py --steps 1 --warmup 1 --no-autotune --no-batch "
                        "--no-event --no-cpu-baseline --no-cufft --no-e2e --no-noise --soak-s 0'; "
