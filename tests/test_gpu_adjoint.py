@@ -424,3 +424,25 @@ def test_kept_wire_spectra_after_the_fused_forward(W):
     ref, rdR = _oracle_backward(g, prm, R, d, res.cpu().numpy().astype(np.float64))
     _grads_close(got, ref, "fused forward, kept spectra", prm, d)
     assert_close(got["response"].cpu().numpy(), rdR, what="fused forward, kept spectra dR")
+
+
+@pytest.mark.parametrize("split", ["1", "2", "4"])
+def test_adjoint_impact_split_matches_oracle(W, split, monkeypatch):
+    """The one-warp wire adjoint with the impacts of a frequency block split over 1, 2 and 4
+    CTAs (WCSIM_ADJ_SPLIT; the automatic choice takes 3 on these planes): dL/dS and dL/dR
+    against the oracle."""
+    import torch
+    monkeypatch.setenv("WCSIM_ADJ_SPLIT", split)
+    g = S.Geometry(n_wires=128, n_imp=10, n_ticks=1024, pitch_mm=3.0)
+    rng = np.random.default_rng(98)
+    grid = np.zeros((g.n_rows, g.n_ticks), np.float32)
+    idx = rng.integers(0, grid.size, grid.size // 20)
+    grid.reshape(-1)[idx] = rng.normal(size=idx.size).astype(np.float32)
+    G = rng.normal(size=(g.n_wires, g.n_ticks)).astype(np.float32)
+    R = S.make_response(g, "induction")
+    pl = plane_for(W, g, S.DriftParams(), R)
+    dS, dR = pl.convolve_adjoint(torch.from_numpy(G).cuda(), torch.from_numpy(grid).cuda(),
+                                 want_resp=True)
+    rdS, rdR = O.convolve_adjoint(g, R, grid.astype(np.float64), G.astype(np.float64))
+    assert_close(dS.cpu().numpy(), rdS, what="dS split %s" % split)
+    assert_close(dR.cpu().numpy(), rdR, what="dR split %s" % split)
